@@ -1,0 +1,162 @@
+"""wRLS denoiser ORACLE: plain FP64 CPU implementation in ``wrls_oracle.c``.
+
+Test infrastructure only. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this package.
+It shares no code with the CUDA library and never imports it.
+
+``build()`` compiles ``wrls_oracle.c`` with gcc (``-O2 -ffp-contract=off -fopenmp``) into
+``oracle/_build/libwrls_oracle.so``; ``OracleStream`` runs frames through it.
+The constants in ``OracleParams`` defaults are the paper's where it gives one
+(lambda = 0.998 in Sec. 5.2, h = 0.75 in Sec. 5.3, alpha = 0.75 in Sec. 6, a 5x5 blend
+window in Sec. 5.3) and the readings of the C file's header elsewhere.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wrls_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libwrls_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, gcc) if missing or older than its source."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("h", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("eps", ctypes.c_double), ("p0_delta", ctypes.c_double),
+                ("sigma_s", ctypes.c_double), ("h_s", ctypes.c_double),
+                ("p_trace_max", ctypes.c_double),
+                ("radius", ctypes.c_int), ("weight_mode", ctypes.c_int),
+                ("clamp_mode", ctypes.c_int), ("blend_mode", ctypes.c_int),
+                ("feature_mode", ctypes.c_int), ("init_mode", ctypes.c_int)]
+
+
+@dataclasses.dataclass
+class OracleParams:
+    lambda_: float = 0.998     # Sec. 5.2 (Eq. 10)
+    h: float = 0.75            # Sec. 5.3 (Eq. 13)
+    alpha: float = 0.75        # Sec. 6 (Eq. 12)
+    eps: float = 1e-4
+    p0_delta: float = 1.0
+    sigma_s: float = 1.0
+    h_s: float = 0.75
+    p_trace_max: float = 0.0
+    radius: int = 2            # 5x5 window, Sec. 5.3
+    weight_mode: int = 0       # 0 wRLS, 1 RLS
+    clamp_mode: int = 0        # 0 3x3 clamp, 1 off
+    blend_mode: int = 0        # 0 p_i beta_k, 1 p_k beta_k
+    feature_mode: int = 0      # 0 p=[1,z], 1 p=[1]
+    init_mode: int = 0         # 0 beta = 0, 1 feature pass-through
+
+    def c(self) -> _Params:
+        return _Params(*dataclasses.astuple(self))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        fp = ctypes.POINTER(ctypes.c_float)
+        _lib.wrls_oracle_frame.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, dp, dp, dp, fp, fp, dp, dp, dp, dp, dp,
+                                           ctypes.POINTER(ctypes.c_ubyte)]
+        _lib.wrls_oracle_frame.restype = ctypes.c_int
+        _lib.wrls_oracle_blend.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
+                                           dp, dp, dp]
+        _lib.wrls_oracle_blend.restype = ctypes.c_int
+        _lib.wrls_oracle_set_threads.argtypes = [ctypes.c_int]
+        _lib.wrls_oracle_get_threads.restype = ctypes.c_int
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().wrls_oracle_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().wrls_oracle_get_threads())
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _fptr(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class OracleStream:
+    """Per-stream oracle state (beta [n,3,4], full P [n,4,4], z [n,3]) across frames."""
+
+    def __init__(self, width: int, height: int, params: Optional[OracleParams] = None):
+        self.W, self.H = int(width), int(height)
+        self.params = params or OracleParams()
+        n = self.W * self.H
+        self.beta = np.zeros((n, 3, 4))
+        self.P = np.zeros((n, 4, 4))
+        self.z = np.zeros((n, 3))
+        self.need_reset = True
+
+    def reset(self) -> None:
+        self.need_reset = True
+
+    def frame(self, radiance: np.ndarray, motion: np.ndarray):
+        """Run one frame. radiance (3,H,W) f32, motion (2,H,W) f32.
+        Returns (out (3,H,W) f64, w (H,W) f64, valid (H,W) bool)."""
+        W, H = self.W, self.H
+        rad = np.ascontiguousarray(radiance, dtype=np.float32)
+        mot = np.ascontiguousarray(motion, dtype=np.float32)
+        assert rad.shape == (3, H, W) and mot.shape == (2, H, W)
+        n = W * H
+        bn, Pn, zn = np.empty((n, 3, 4)), np.empty((n, 4, 4)), np.empty((n, 3))
+        out = np.empty((3, H, W))
+        w = np.empty((H, W))
+        valid = np.empty((H, W), dtype=np.uint8)
+        prm = self.params.c()
+        rc = lib().wrls_oracle_frame(ctypes.byref(prm), W, H, int(self.need_reset),
+                                     _dptr(self.beta), _dptr(self.P), _dptr(self.z),
+                                     _fptr(rad), _fptr(mot), _dptr(bn), _dptr(Pn), _dptr(zn),
+                                     _dptr(out), _dptr(w),
+                                     valid.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        if rc != 0:
+            raise ValueError("wrls_oracle_frame rejected its arguments")
+        self.beta, self.P, self.z = bn, Pn, zn
+        self.need_reset = False
+        return out, w, valid.astype(bool)
+
+    def z_planes(self) -> np.ndarray:
+        return self.z.reshape(self.H, self.W, 3).transpose(2, 0, 1)
+
+
+def blend(params: OracleParams, beta: np.ndarray, z: np.ndarray, width: int, height: int) -> np.ndarray:
+    """The blend step alone on an explicit state: beta [n,3,4], z [n,3] -> out (3,H,W)."""
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    out = np.empty((3, height, width))
+    prm = params.c()
+    rc = lib().wrls_oracle_blend(ctypes.byref(prm), int(width), int(height), _dptr(beta), _dptr(z),
+                                 _dptr(out))
+    if rc != 0:
+        raise ValueError("wrls_oracle_blend rejected its arguments")
+    return out
