@@ -69,9 +69,12 @@ class OracleParams:
 
 
 def lib():
+    """Load the oracle library (``WRLS_ORACLE_LIB`` selects another build of the same
+    source, which the mutation tests use to load deliberately broken copies)."""
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        override = os.environ.get("WRLS_ORACLE_LIB")
+        _lib = ctypes.CDLL(override if override else build())
         dp = ctypes.POINTER(ctypes.c_double)
         fp = ctypes.POINTER(ctypes.c_float)
         _lib.wrls_oracle_frame.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,

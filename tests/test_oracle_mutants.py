@@ -1,0 +1,53 @@
+"""The oracle pins must catch plausible mistakes: each mutant below is a copy of the
+oracle source with one planted error (a flipped sign, a dropped term, a swapped index or
+operand). Every mutant is compiled on the CPU and must fail at least one pin of
+test_oracle_pins.py. Nothing here touches the CUDA library."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "wrls_oracle.c")
+
+MUTANTS = {
+    "eq8_residual_sign": ("double e = missing ? 0.0 : I[c] - pred;",
+                          "double e = missing ? 0.0 : pred - I[c];"),
+    "eq14_lambda_times_w": ("prm->lambda / w + pPp", "prm->lambda * w + pPp"),
+    "eq11_no_forgetting": ("(P[a][b] - q[a] * pP[b]) / prm->lambda", "(P[a][b] - q[a] * pP[b])"),
+    "eq9_gain_without_denominator": ("beta[c][a] += q[a] * e;", "beta[c][a] += Pp[a] * e;"),
+    "eq12_alpha_swapped": ("prm->alpha * zc[c] + (1.0 - prm->alpha) * I[c]",
+                           "(1.0 - prm->alpha) * zc[c] + prm->alpha * I[c]"),
+    "eq13_max_instead_of_min": ("double m = na < nb ? na : nb;", "double m = na < nb ? nb : na;"),
+    "reprojection_sign": ("float qx = (float)x + mot[0 * n_pix + j];",
+                          "float qx = (float)x - mot[0 * n_pix + j];"),
+    "reprojection_axes_swapped": ("float qy = (float)y + mot[1 * n_pix + j];",
+                                  "float qy = (float)y + mot[0 * n_pix + j];"),
+    "bilinear_taps_transposed": ("(long)y0 * W + x1,\n                                     (long)y1 * W + x0",
+                                 "(long)y1 * W + x0,\n                                     (long)y0 * W + x1"),
+    "clamp_window_one_sided": ("for (int dy = -1; dy <= 1; ++dy)", "for (int dy = 0; dy <= 1; ++dy)"),
+    "blend_own_prediction": ("const double* pu = prm->blend_mode == 0 ? pi_ : pk;",
+                             "const double* pu = pk;"),
+    "blend_range_term_dropped": (" *\n                               exp(-(dz * dz) / (prm->h_s * prm->h_s));", ";"),
+    "blend_sigma_factor": ("(2.0 * prm->sigma_s * prm->sigma_s)", "(prm->sigma_s * prm->sigma_s)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, "mutant anchor not found: " + name
+    mutated = src.replace(old, new, 1)
+    c_path = tmp_path / "mutant.c"
+    so_path = tmp_path / "libmutant.so"
+    c_path.write_text(mutated)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                           "-o", str(so_path), str(c_path), "-lm"])
+    env = dict(os.environ, WRLS_ORACLE_LIB=str(so_path), OMP_NUM_THREADS="2")
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                          os.path.join(HERE, "test_oracle_pins.py")],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, "no pin caught mutant %s:\n%s" % (name, res.stdout[-2000:])
