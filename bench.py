@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the wRLS denoiser (libwrls.so through its C ABI).
+
+Workload: the 1920x1080, 120-frame camera pan (1.7 px/frame, heteroscedastic log-normal
+noise, 5% x50 fireflies) of ``synth.pan_1080p_120f``; FP32 state. One step = one pass over
+the 120 frames (every frame runs the whole path: reprojection, Eq. 12-14 update, 5x5
+blend). Inputs are generated on the device before timing and stay resident; the state
+ping-pong alone (2 x 207 MB) exceeds the 129 MB L2 every frame.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wrls|reference]
+
+N > 1 runs under torchrun: one independent replica per GPU (streams do not shard;
+no collective on the data path), value = all ranks' pixels / max-over-ranks time.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (rank 0 only),
+one step = one 1080p frame of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "denoised Mpix/s plain FP32 vs batched BF16-state at stated err; p99 frame latency"
+BYTES_UPDATE_F32 = 220   # per pixel: state read 100 + radiance 12 + motion 8 + state write 100
+BYTES_PATH_F32 = 232     # per pixel and frame for the whole path: + out 12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wrls", choices=["wrls", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--frames", type=int, default=0,
+                    help="use only the first N frames of the sequence (small profiling captures)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.device_id = device_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.device_id, "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [v for v in sm if mx and v >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def smi_device_id(torch, dev, local):
+    """nvidia-smi -i argument for this process's GPU: its UUID when nvidia-smi knows it."""
+    cands = []
+    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", "") or "")
+    if uuid:
+        cands.append(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis:
+        cands.append(vis.split(",")[local].strip())
+    cands.append(str(local))
+    for c in cands:
+        try:
+            r = subprocess.run(["nvidia-smi", "-i", c, "--query-gpu=index", "--format=csv,noheader"],
+                               capture_output=True, text=True, timeout=20)
+            if r.returncode == 0 and r.stdout.strip():
+                return c
+        except (OSError, subprocess.TimeoutExpired):
+            break
+    return str(local)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(spec, seconds: float, frames_ring: int = 4):
+    """The FP64 oracle, as it stands, on the host cores: Mpix/s on a bounded sample of the
+    workload (a ring of its first frames, run until `seconds` of work)."""
+    import oracle as O
+    from paper_2106_08034_gb300 import synth
+    sc = synth.Scene(spec)
+    ring = [sc.frame(t) for t in range(frames_ring)]
+    ring = [(f["radiance"].numpy(), f["motion"].numpy()) for f in ring]
+    st = O.OracleStream(spec.width, spec.height)
+    st.frame(*ring[0])              # warm-up frame (first-frame restart)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        st.frame(*ring[(n + 1) % frames_ring])
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds and n >= 2:
+            break
+    return n * spec.width * spec.height / dt / 1e6, n, dt, O.get_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2106_08034_gb300 import synth
+    import oracle as O
+    spec = synth.pan_1080p_120f()
+    sc = synth.Scene(spec)
+    ring = [sc.frame(t) for t in range(8)]
+    ring = [(f["radiance"].numpy(), f["motion"].numpy()) for f in ring]
+    st = O.OracleStream(spec.width, spec.height)
+    for i in range(args.warmup):
+        st.frame(*ring[i % 8])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        st.frame(*ring[(args.warmup + i) % 8])
+    dt = time.perf_counter() - t0
+    px = spec.width * spec.height
+    value = args.steps * px / dt / 1e6
+    cores = O.get_threads()
+    sample = "%d frames of the 1920x1080 pan workload (ring of its first 8 frames), FP64" % args.steps
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpix/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "pan_1080p_120f (1920x1080, 120 frames, pan 1.7 px/frame, 5% fireflies)",
+                   "step": "one 1920x1080 frame (bounded sample)", "implementation": "FP64 C oracle, OpenMP"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_wrls(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2106_08034_gb300 import build as B
+    from paper_2106_08034_gb300 import synth
+    from paper_2106_08034_gb300 import wrls as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    B.build()
+    W.lib()
+    dev = torch.device("cuda", local)
+
+    spec = synth.pan_1080p_120f(seed=1 + rank)
+    Wd, Hd, T = spec.width, spec.height, spec.frames
+    if args.frames > 0:
+        T = min(T, args.frames)
+    px = Wd * Hd
+    sc = synth.Scene(spec)
+    rad = torch.empty(T, 3, Hd, Wd, device=dev)
+    mot = torch.empty(T, 2, Hd, Wd, device=dev)
+    for t in range(T):
+        f = sc.frame(t, device=dev)
+        rad[t].copy_(f["radiance"])
+        mot[t].copy_(f["motion"])
+    del f
+    torch.cuda.synchronize()
+
+    cs = torch.cuda.Stream(device=dev)
+    p = W.wrls_params_default()
+    s = W.Stream(Wd, Hd, p, cuda_stream=cs)
+    out = torch.empty(3, Hd, Wd, device=dev)
+
+    def step():
+        for t in range(T):
+            W.wrls_denoise_frame(s.handle, rad[t], None, None, mot[t], out)
+
+    with torch.cuda.stream(cs):
+        for _ in range(args.warmup):
+            step()
+    cs.synchronize()
+    W.wrls_stream_enable_timing(s.handle, True)
+
+    clocks = ClockSampler(smi_device_id(torch, dev, local))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(cs)
+    for _ in range(args.steps):
+        step()
+    e1.record(cs)
+    e1.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    upd_ms, bl_ms, nfr = W.wrls_stream_kernel_times(s.handle)
+    W.wrls_stream_enable_timing(s.handle, False)
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    frames_total = args.steps * T * world
+    value = frames_total * px / (t_max / 1e3) / 1e6
+
+    # e2e: the same metric through the host-buffer entry point, copies in the timed region
+    e2e = None
+    if not args.no_e2e:
+        ring = 8
+        h_rad = [rad[t].cpu().pin_memory() for t in range(ring)]
+        h_mot = [mot[t].cpu().pin_memory() for t in range(ring)]
+        h_out = [torch.empty(3, Hd, Wd).pin_memory() for _ in range(ring)]
+        s2 = W.Stream(Wd, Hd, p, cuda_stream=cs)
+        e2e_steps = max(1, min(args.steps, 3))
+
+        def step_host():
+            for t in range(T):
+                k = t % ring
+                W.wrls_denoise_frame_host(s2.handle, h_rad[k], None, None, h_mot[k], h_out[k])
+        step_host()
+        cs.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0.record(cs)
+        for _ in range(e2e_steps):
+            step_host()
+        e1.record(cs)
+        e1.synchronize()
+        ms2 = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([ms2], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms2 = float(tt.item())
+        e2e = {"value": round(e2e_steps * T * world * px / (ms2 / 1e3) / 1e6, 2), "unit": "Mpix/s",
+               "h2d_bytes_per_step": T * px * 20, "d2h_bytes_per_step": T * px * 12,
+               "steps": e2e_steps}
+        s2.close()
+
+    peak, peak_kind = measured_peaks()
+    upd_per = upd_ms / max(nfr, 1)
+    bl_per = bl_ms / max(nfr, 1)
+    achieved = BYTES_UPDATE_F32 * px / (upd_per / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_update (reproject + Eq. 12-14 update)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "bytes_per_px": BYTES_UPDATE_F32,
+                "kernel_ms": {"update": round(upd_per, 5), "blend": round(bl_per, 5)},
+                "path": {"bytes_per_px": BYTES_PATH_F32,
+                         "achieved": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9, 1),
+                         "frac": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9 / peak, 4)}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, dt, cores = cpu_oracle_rate(spec, args.cpu_seconds)
+        cpu = {"value": round(rate, 4), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+               "sample": "%d frames of the 1920x1080 pan workload (%.1f s), FP64 C oracle" % (n, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "pan_1080p_120f: 1920x1080, 120 frames, pan 1.7 px/frame, "
+                                   "log-normal noise, 5% x50 fireflies",
+                       "step": "one pass over the 120 frames", "state": "f32",
+                       "l2": "inputs larger than L2: state ping-pong 2 x 207 MB per frame",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 2 * T * args.steps, "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_wrls(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * wrls.h -- C ABI of libwrls.so, a GB300 (sm_103a) implementation of the weighted
+ * recursive least squares (wRLS) temporal / spatio-temporal denoiser of
+ * Iglesias-Guitian, Mane, Moon, "Real-Time Denoising of Volumetric Path Tracing for
+ * Direct Volume Rendering", IEEE TVCG 2020 (Sec. 4-5).
+ *
+ * The problem (Sec. 4, Fig. 5): a renderer produces one noisy frame per time step; the
+ * denoiser keeps a persistent per-pixel state -- a linear model beta (Eq. 5), its inverse
+ * covariance P (Eq. 10-11) and a temporal feature z (Eq. 12) -- reprojects it along
+ * per-pixel motion (Table 2, pi(v_j) = j + v_j), updates it by wRLS against the new noisy
+ * radiance (Eq. 8, 9, 11, 13, 14) and outputs a colour blended from the predictions of a
+ * 5x5 neighbourhood of models (Sec. 5.3, "Spatio-temporal denoising using wRLS").
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a wrls_status; nothing throws across the ABI. On an error the
+ *    call has no effect on the stream's state and wrls_last_error() describes it.
+ *  - Image buffers are planar, channel-major, row-major, tightly packed:
+ *    element (c, y, x) of a C-channel W x H image is at index (c * H + y) * W + x.
+ *    All are binary32 (float).
+ *  - Device buffers are CUDA device pointers of the current device. The caller owns
+ *    every input and output buffer; the stream owns its state.
+ *  - Work is enqueued asynchronously on the stream's CUDA stream (see
+ *    wrls_stream_set_cuda_stream); an output is complete once that stream is
+ *    synchronised. The library never allocates per frame.
+ *  - A stream object may be used by one host thread at a time.
+ */
+#ifndef WRLS_H
+#define WRLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WRLS_OK = 0,
+    WRLS_ERR_INVALID_ARG = 1, /* a null/misaligned pointer, a bad size or parameter */
+    WRLS_ERR_OOM = 2,         /* device allocation failed at create time */
+    WRLS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    WRLS_ERR_STATE = 4,       /* the object is in a state that forbids the call */
+    WRLS_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+} wrls_status;
+
+/* Storage format of the per-pixel state (computation is always binary32). */
+typedef enum {
+    WRLS_STATE_F32 = 0,   /* 25 binary32 values per pixel (100 B) */
+    WRLS_STATE_BF16 = 1,  /* 25 bfloat16 values + one binary32 P scale (54 B) */
+    WRLS_STATE_F16 = 2    /* 25 binary16 values + one binary32 P scale (54 B) */
+} wrls_state_precision;
+
+/*
+ * Parameters. Fill with wrls_params_default() and change fields as needed;
+ * struct_size must stay sizeof(wrls_params) (ABI versioning).
+ */
+typedef struct wrls_params {
+    uint32_t struct_size;
+    float lambda;        /* forgetting factor, Sec. 5.2 (Eq. 10-11); default 0.998 */
+    float h;             /* wRLS bandwidth, Sec. 5.3 (Eq. 13); default 0.75 */
+    float alpha;         /* temporal-feature history weight, Eq. 12 (Sec. 6); default 0.75 */
+    float eps;           /* Eq. 13 epsilon; default 1e-4 */
+    float p0_delta;      /* P of a (re)started pixel = p0_delta * I; default 1 */
+    float sigma_s;       /* blend: spatial Gaussian std (pixels); default 1 */
+    float h_s;           /* blend: bandwidth on the Eq. 13 distance of features; default 0.75 */
+    float p_trace_max;   /* wind-up guard: P <- P0 when trace(P) > p_trace_max or a
+                            diagonal entry <= 0; 0 (default) = off */
+    int32_t radius;      /* blend window radius: 2 = 5x5 (Sec. 5.3, default); 0 = temporal only */
+    int32_t weight_mode; /* 0 = wRLS weight Eq. 13 (default); 1 = RLS, w = 1 (Eq. 10) */
+    int32_t clamp_mode;  /* 0 = clamp history to the 3x3 min/max of I~ (Eq. 12 Psi); 1 = off */
+    int32_t blend_mode;  /* 0 = neighbour k's model predicts pixel i: p_i . beta_k (default);
+                            1 = bilateral average of the neighbours' own predictions */
+    int32_t feature_mode;/* 0 = p = [1, z] (Sec. 5.1, d = 4, default); 1 = p = [1] (no feature) */
+    int32_t init_mode;   /* 0 = restarted pixels start from beta = 0 (default);
+                            1 = feature pass-through, beta_c = e_{c+1} (prediction = z_c) */
+    int32_t state_precision; /* wrls_state_precision; default WRLS_STATE_F32 */
+    int32_t n_features;  /* feature planes the caller may pass; the paper's predictor uses
+                            none of them (Sec. 4, 5.3); accepted and ignored */
+} wrls_params;
+
+typedef struct wrls_stream wrls_stream;
+
+/* Fill *p with the defaults above. */
+void wrls_params_default(wrls_params* p);
+
+/* Device bytes a stream of w x h pixels holds for its state (two copies: the
+ * reprojection of Sec. 5.3 reads frame t-1 while frame t is written). 0 on bad args.
+ * Used for admission by device memory. */
+size_t wrls_state_bytes(int width, int height, const wrls_params* p);
+
+/* Create a stream for w x h frames (1 <= w, h <= 16384). Allocates the state with
+ * cudaMalloc on the current device (WRLS_ERR_OOM on failure). The first frame after
+ * create (or after wrls_stream_reset) restarts every pixel. On success *out owns the
+ * stream; release it with wrls_stream_destroy. */
+wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls_stream** out);
+
+/* Set the CUDA stream (a cudaStream_t passed as void*) that later calls enqueue on.
+ * NULL selects the legacy default stream (the default after create). */
+wrls_status wrls_stream_set_cuda_stream(wrls_stream* s, void* cuda_stream);
+
+/*
+ * Denoise one frame (Sec. 5.3): reproject, Eq. 12 feature, Eq. 13 weight, Eq. 8/14/9/11
+ * update, 5x5 blend. All pointers are device pointers:
+ *   radiance  3 x H x W, noisy linear HDR colour I~(t); required. A pixel with a
+ *             non-finite channel is a missing sample (weight 0, it leaves its model
+ *             unchanged apart from the forgetting factor).
+ *   variance  H x W per-pixel variance, or NULL; not used by the paper's weight.
+ *   features  n_features x H x W G-buffer planes, or NULL; not used by the paper's
+ *             predictor.
+ *   motion    2 x H x W (v_x plane, then v_y plane) in pixels, backward: the previous
+ *             position of pixel j is j + v_j (Table 2). Non-finite or out-of-image
+ *             previous positions restart the pixel.
+ *   out       3 x H x W denoised colour; must not overlap any input.
+ * Pointers must be 4-byte aligned. Asynchronous on the stream's CUDA stream.
+ */
+wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const float* variance,
+                               const float* features, const float* motion, float* out);
+
+/*
+ * Same as wrls_denoise_frame with HOST buffers (pinned memory gives asynchronous copies):
+ * copies radiance and motion to device buffers the stream owns (allocated on the first
+ * call and kept until destroy), denoises, and copies the result back to `out`. Returns
+ * after enqueuing; `out` is valid once the stream's CUDA stream is synchronised.
+ * variance and features may be NULL (they are not used by the paper's method).
+ */
+wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const float* variance,
+                                    const float* features, const float* motion, float* out);
+
+/* The next frame restarts every pixel (frame-0 behaviour). */
+wrls_status wrls_stream_reset(wrls_stream* s);
+
+/* Synchronise the stream's pending work and free it. NULL is a no-op. */
+void wrls_stream_destroy(wrls_stream* s);
+
+/*
+ * Copy the current per-pixel state, decoded to binary32, into `dst` (device,
+ * 25 x H x W planar): planes 0-11 beta[c][a] (channel c, coefficient a, plane c*4+a),
+ * planes 12-21 the upper triangle of P row by row (00,01,02,03,11,12,13,22,23,33),
+ * planes 22-24 z. WRLS_ERR_STATE before the first frame.
+ */
+wrls_status wrls_stream_read_state(wrls_stream* s, float* dst);
+
+/* Frames denoised since create. */
+uint64_t wrls_stream_frames(const wrls_stream* s);
+
+/*
+ * Kernel tracing. With timing enabled, every frame records CUDA events on the stream's
+ * CUDA stream before and after each of its kernels (temporal update, spatial blend).
+ * wrls_stream_kernel_times synchronises the recorded events, adds their durations to
+ * *update_ms and *blend_ms (milliseconds, summed over frames), sets *frames to the number
+ * of frames summed, and clears the record. Up to 8192 frames are held; older ones are
+ * folded into the totals as the record fills. Enabling allocates the events; disabling
+ * frees them.
+ */
+wrls_status wrls_stream_enable_timing(wrls_stream* s, int enable);
+wrls_status wrls_stream_kernel_times(wrls_stream* s, double* update_ms, double* blend_ms,
+                                     uint64_t* frames);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* wrls_last_error(void);
+
+/*
+ * ---- Batched tick: all ready frames of many streams in one persistent launch ----
+ *
+ * One tick processes one frame of each of n streams (of any sizes) with a single
+ * persistent kernel launch that pulls (stream, tile) work items from a device work list;
+ * the launch is captured once in a CUDA graph per batch shape and replayed. Results are
+ * identical to calling wrls_denoise_frame on each stream alone.
+ */
+typedef struct {
+    wrls_stream* stream;
+    const float* radiance;  /* device, 3 x H x W */
+    const float* variance;  /* device or NULL (unused) */
+    const float* features;  /* device or NULL (unused) */
+    const float* motion;    /* device, 2 x H x W */
+    float* out;             /* device, 3 x H x W */
+} wrls_frame_io;
+
+typedef struct wrls_batch wrls_batch;
+
+/* Create a batch executor for up to max_streams frames per tick. */
+wrls_status wrls_batch_create(int max_streams, wrls_batch** out);
+
+/* Set the CUDA stream (cudaStream_t as void*) ticks run on; NULL = legacy default. */
+wrls_status wrls_batch_set_cuda_stream(wrls_batch* b, void* cuda_stream);
+
+/* Run one tick over n frames (1 <= n <= max_streams; each stream at most once, all
+ * streams of the same state precision and parameters). Asynchronous. */
+wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n);
+
+/* Synchronise and free. NULL is a no-op. */
+void wrls_batch_destroy(wrls_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WRLS_H */

@@ -1,0 +1,350 @@
+// C ABI of libwrls.so (declared in include/wrls.h): parameter handling, stream objects
+// owning the per-pixel state, and the per-frame entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "wrls_internal.h"
+
+namespace wrls {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+static size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_stride,
+                         size_t* scale_offset_bytes) {
+  const size_t p = round_up((size_t)W, 32);
+  const size_t ps = round_up(p * (size_t)H, 64);
+  const size_t elem = precision == 0 ? 4 : 2;
+  size_t bytes = ps * elem * kNState;
+  size_t scale_off = 0;
+  if (precision != 0) {
+    scale_off = round_up(bytes, 256);
+    bytes = scale_off + ps * sizeof(float);
+  }
+  if (pitch) *pitch = (int)p;
+  if (plane_stride) *plane_stride = ps;
+  if (scale_offset_bytes) *scale_offset_bytes = scale_off;
+  return round_up(bytes, 256);
+}
+
+bool make_kparams(const wrls_params& p, KParams* kp, const char** why) {
+  if (p.struct_size != sizeof(wrls_params)) { *why = "params.struct_size != sizeof(wrls_params)"; return false; }
+  if (!(p.lambda > 0.0f && p.lambda <= 1.0f)) { *why = "lambda must be in (0, 1]"; return false; }
+  if (!(p.h > 0.0f) || !(p.alpha >= 0.0f && p.alpha <= 1.0f) || !(p.eps > 0.0f) ||
+      !(p.p0_delta > 0.0f) || !(p.sigma_s > 0.0f) || !(p.h_s > 0.0f) || !(p.p_trace_max >= 0.0f)) {
+    *why = "h, eps, p0_delta, sigma_s, h_s must be > 0, alpha in [0,1], p_trace_max >= 0";
+    return false;
+  }
+  if (p.radius < 0 || p.radius > kMaxRadius) { *why = "radius must be in [0, 2]"; return false; }
+  if ((unsigned)p.weight_mode > 1u || (unsigned)p.clamp_mode > 1u || (unsigned)p.blend_mode > 1u ||
+      (unsigned)p.feature_mode > 1u || (unsigned)p.init_mode > 1u || (unsigned)p.state_precision > 2u ||
+      p.n_features < 0) {
+    *why = "a mode field is out of range";
+    return false;
+  }
+  const double log2e = 1.4426950408889634;
+  kp->lambda = p.lambda;
+  kp->inv_lambda = (float)(1.0 / (double)p.lambda);
+  kp->alpha = p.alpha;
+  kp->one_m_alpha = (float)(1.0 - (double)p.alpha);
+  kp->eps = p.eps;
+  kp->w_k = (float)(log2e / ((double)p.h * (double)p.h));
+  kp->p0_delta = p.p0_delta;
+  kp->p_trace_max = p.p_trace_max;
+  kp->range_k = (float)(log2e / ((double)p.h_s * (double)p.h_s));
+  for (int dy = -kMaxRadius; dy <= kMaxRadius; ++dy)
+    for (int dx = -kMaxRadius; dx <= kMaxRadius; ++dx)
+      kp->spatial[(dy + kMaxRadius) * (2 * kMaxRadius + 1) + dx + kMaxRadius] =
+          (float)(-(double)(dx * dx + dy * dy) / (2.0 * (double)p.sigma_s * (double)p.sigma_s) * log2e);
+  kp->radius = p.radius;
+  kp->weight_mode = p.weight_mode;
+  kp->clamp_mode = p.clamp_mode;
+  kp->blend_mode = p.blend_mode;
+  kp->feature_mode = p.feature_mode;
+  kp->init_mode = p.init_mode;
+  return true;
+}
+
+}  // namespace wrls
+
+using namespace wrls;
+
+#define WRLS_CHECK_CUDA(call, what)                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      set_error("%s: %s", what, cudaGetErrorString(e_));                                \
+      return WRLS_ERR_CUDA;                                                             \
+    }                                                                                   \
+  } while (0)
+
+static bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
+
+static bool dims_ok(int w, int h) { return w >= 1 && h >= 1 && w <= 16384 && h <= 16384; }
+
+// Add the durations of the recorded frames to the totals and clear the record.
+static wrls_status fold_timing(wrls_stream* s) {
+  for (int i = 0; i < s->t_pending; ++i) {
+    cudaEvent_t* ev = s->tev + 3 * i;
+    float a = 0.0f, b = 0.0f;
+    WRLS_CHECK_CUDA(cudaEventSynchronize(ev[2]), "kernel timing: event synchronize");
+    WRLS_CHECK_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]), "kernel timing: elapsed time");
+    WRLS_CHECK_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]), "kernel timing: elapsed time");
+    s->t_update_ms += a;
+    s->t_blend_ms += b;
+    s->t_frames++;
+  }
+  s->t_pending = 0;
+  return WRLS_OK;
+}
+
+static void free_timing(wrls_stream* s) {
+  if (!s->tev) return;
+  for (int i = 0; i < 3 * wrls_stream::kTimingCap; ++i)
+    if (s->tev[i]) cudaEventDestroy(s->tev[i]);
+  delete[] s->tev;
+  s->tev = nullptr;
+  s->t_pending = 0;
+}
+
+extern "C" {
+
+void wrls_params_default(wrls_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->struct_size = sizeof(wrls_params);
+  p->lambda = 0.998f;   // Sec. 5.2
+  p->h = 0.75f;         // Sec. 5.3
+  p->alpha = 0.75f;     // Sec. 6
+  p->eps = 1e-4f;
+  p->p0_delta = 1.0f;
+  p->sigma_s = 1.0f;
+  p->h_s = 0.75f;
+  p->p_trace_max = 0.0f;
+  p->radius = 2;        // 5x5, Sec. 5.3
+  p->weight_mode = 0;
+  p->clamp_mode = 0;
+  p->blend_mode = 0;
+  p->feature_mode = 0;
+  p->init_mode = 0;
+  p->state_precision = WRLS_STATE_F32;
+  p->n_features = 0;
+}
+
+size_t wrls_state_bytes(int width, int height, const wrls_params* p) {
+  if (!p || !dims_ok(width, height) || (unsigned)p->state_precision > 2u) return 0;
+  return 2 * state_copy_layout(width, height, p->state_precision, nullptr, nullptr, nullptr);
+}
+
+const char* wrls_last_error(void) { return g_err; }
+
+wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls_stream** out) {
+  if (!out) { set_error("wrls_stream_create: out is NULL"); return WRLS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!p) { set_error("wrls_stream_create: params is NULL"); return WRLS_ERR_INVALID_ARG; }
+  if (!dims_ok(width, height)) {
+    set_error("wrls_stream_create: width/height %d x %d outside [1, 16384]", width, height);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  KParams kp;
+  const char* why = "";
+  if (!make_kparams(*p, &kp, &why)) { set_error("wrls_stream_create: %s", why); return WRLS_ERR_INVALID_ARG; }
+  int pitch;
+  size_t ps, scale_off;
+  const size_t copy = state_copy_layout(width, height, p->state_precision, &pitch, &ps, &scale_off);
+  wrls_stream* s = new (std::nothrow) wrls_stream();
+  if (!s) { set_error("wrls_stream_create: host allocation failed"); return WRLS_ERR_OOM; }
+  s->W = width;
+  s->H = height;
+  s->prm = *p;
+  s->kp = kp;
+  cudaGetDevice(&s->device);
+  cudaError_t e = cudaMalloc(&s->mem, 2 * copy);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("wrls_stream_create: cudaMalloc(%zu) failed: %s", 2 * copy, cudaGetErrorString(e));
+    delete s;
+    return e == cudaErrorMemoryAllocation ? WRLS_ERR_OOM : WRLS_ERR_CUDA;
+  }
+  s->mem_bytes = 2 * copy;
+  for (int i = 0; i < 2; ++i) {
+    StateDesc& d = s->state[i];
+    d.base = (char*)s->mem + i * copy;
+    d.scale = p->state_precision ? (float*)((char*)d.base + scale_off) : nullptr;
+    d.precision = p->state_precision;
+    d.W = width;
+    d.H = height;
+    d.pitch = pitch;
+    d.plane_stride = ps;
+  }
+  *out = s;
+  return WRLS_OK;
+}
+
+wrls_status wrls_stream_set_cuda_stream(wrls_stream* s, void* cuda_stream) {
+  if (!s) { set_error("wrls_stream_set_cuda_stream: stream is NULL"); return WRLS_ERR_INVALID_ARG; }
+  s->cs = (cudaStream_t)cuda_stream;
+  return WRLS_OK;
+}
+
+wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const float* variance,
+                               const float* features, const float* motion, float* out) {
+  (void)variance;
+  (void)features;
+  if (!s || !radiance || !motion || !out) {
+    set_error("wrls_denoise_frame: stream, radiance, motion and out must be non-NULL");
+    return WRLS_ERR_INVALID_ARG;
+  }
+  if (!aligned4(radiance) || !aligned4(motion) || !aligned4(out)) {
+    set_error("wrls_denoise_frame: buffers must be 4-byte aligned");
+    return WRLS_ERR_INVALID_ARG;
+  }
+  const size_t n = (size_t)s->W * s->H;
+  const char* o = (const char*)out;
+  const char* r = (const char*)radiance;
+  const char* m = (const char*)motion;
+  if ((o < r + 3 * n * 4 && r < o + 3 * n * 4) || (o < m + 2 * n * 4 && m < o + 3 * n * 4)) {
+    set_error("wrls_denoise_frame: out overlaps an input");
+    return WRLS_ERR_INVALID_ARG;
+  }
+  const StateDesc& prev = s->state[s->cur];
+  const StateDesc& next = s->state[s->cur ^ 1];
+  cudaEvent_t* ev = nullptr;
+  if (s->tev) {
+    if (s->t_pending == wrls_stream::kTimingCap) {
+      wrls_status st = fold_timing(s);
+      if (st != WRLS_OK) return st;
+    }
+    ev = s->tev + 3 * s->t_pending;
+    WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
+  }
+  WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->cs),
+                  "wrls_denoise_frame: update kernel launch");
+  if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
+  WRLS_CHECK_CUDA(launch_blend(s->kp, next, out, s->cs), "wrls_denoise_frame: blend kernel launch");
+  if (ev) {
+    WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
+    s->t_pending++;
+  }
+  s->cur ^= 1;
+  s->need_reset = false;
+  s->has_frame = true;
+  s->frames++;
+  return WRLS_OK;
+}
+
+wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const float* variance,
+                                    const float* features, const float* motion, float* out) {
+  (void)variance;
+  (void)features;
+  if (!s || !radiance || !motion || !out) {
+    set_error("wrls_denoise_frame_host: stream, radiance, motion and out must be non-NULL");
+    return WRLS_ERR_INVALID_ARG;
+  }
+  const size_t n = (size_t)s->W * s->H;
+  if (!s->staging) {
+    cudaError_t e = cudaMalloc(&s->staging, 8 * n * sizeof(float));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      s->staging = nullptr;
+      set_error("wrls_denoise_frame_host: staging cudaMalloc failed: %s", cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? WRLS_ERR_OOM : WRLS_ERR_CUDA;
+    }
+  }
+  float* d_rad = s->staging;
+  float* d_mot = s->staging + 3 * n;
+  float* d_out = s->staging + 5 * n;
+  WRLS_CHECK_CUDA(cudaMemcpyAsync(d_rad, radiance, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s->cs),
+                  "wrls_denoise_frame_host: radiance copy");
+  WRLS_CHECK_CUDA(cudaMemcpyAsync(d_mot, motion, 2 * n * sizeof(float), cudaMemcpyHostToDevice, s->cs),
+                  "wrls_denoise_frame_host: motion copy");
+  wrls_status st = wrls_denoise_frame(s, d_rad, nullptr, nullptr, d_mot, d_out);
+  if (st != WRLS_OK) return st;
+  WRLS_CHECK_CUDA(cudaMemcpyAsync(out, d_out, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, s->cs),
+                  "wrls_denoise_frame_host: output copy");
+  return WRLS_OK;
+}
+
+wrls_status wrls_stream_reset(wrls_stream* s) {
+  if (!s) { set_error("wrls_stream_reset: stream is NULL"); return WRLS_ERR_INVALID_ARG; }
+  s->need_reset = true;
+  return WRLS_OK;
+}
+
+void wrls_stream_destroy(wrls_stream* s) {
+  if (!s) return;
+  int prev_dev = 0;
+  cudaGetDevice(&prev_dev);
+  if (prev_dev != s->device) cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->cs);
+  free_timing(s);
+  cudaFree(s->mem);
+  if (s->staging) cudaFree(s->staging);
+  cudaGetLastError();
+  if (prev_dev != s->device) cudaSetDevice(prev_dev);
+  delete s;
+}
+
+wrls_status wrls_stream_read_state(wrls_stream* s, float* dst) {
+  if (!s || !dst) { set_error("wrls_stream_read_state: NULL argument"); return WRLS_ERR_INVALID_ARG; }
+  if (!aligned4(dst)) { set_error("wrls_stream_read_state: dst must be 4-byte aligned"); return WRLS_ERR_INVALID_ARG; }
+  if (!s->has_frame) { set_error("wrls_stream_read_state: no frame denoised yet"); return WRLS_ERR_STATE; }
+  WRLS_CHECK_CUDA(launch_read_state(s->state[s->cur], dst, s->cs), "wrls_stream_read_state: launch");
+  return WRLS_OK;
+}
+
+uint64_t wrls_stream_frames(const wrls_stream* s) { return s ? s->frames : 0; }
+
+wrls_status wrls_stream_enable_timing(wrls_stream* s, int enable) {
+  if (!s) { set_error("wrls_stream_enable_timing: stream is NULL"); return WRLS_ERR_INVALID_ARG; }
+  if (!enable) {
+    cudaStreamSynchronize(s->cs);
+    free_timing(s);
+    return WRLS_OK;
+  }
+  if (s->tev) return WRLS_OK;
+  s->tev = new (std::nothrow) cudaEvent_t[3 * wrls_stream::kTimingCap]();
+  if (!s->tev) { set_error("wrls_stream_enable_timing: host allocation failed"); return WRLS_ERR_OOM; }
+  for (int i = 0; i < 3 * wrls_stream::kTimingCap; ++i) {
+    cudaError_t e = cudaEventCreate(&s->tev[i]);
+    if (e != cudaSuccess) {
+      free_timing(s);
+      set_error("wrls_stream_enable_timing: cudaEventCreate: %s", cudaGetErrorString(e));
+      return WRLS_ERR_CUDA;
+    }
+  }
+  s->t_update_ms = s->t_blend_ms = 0.0;
+  s->t_frames = 0;
+  return WRLS_OK;
+}
+
+wrls_status wrls_stream_kernel_times(wrls_stream* s, double* update_ms, double* blend_ms,
+                                     uint64_t* frames) {
+  if (!s || !update_ms || !blend_ms || !frames) {
+    set_error("wrls_stream_kernel_times: NULL argument");
+    return WRLS_ERR_INVALID_ARG;
+  }
+  if (!s->tev) { set_error("wrls_stream_kernel_times: timing is not enabled"); return WRLS_ERR_STATE; }
+  wrls_status st = fold_timing(s);
+  if (st != WRLS_OK) return st;
+  *update_ms = s->t_update_ms;
+  *blend_ms = s->t_blend_ms;
+  *frames = s->t_frames;
+  s->t_update_ms = s->t_blend_ms = 0.0;
+  s->t_frames = 0;
+  return WRLS_OK;
+}
+
+}  // extern "C"

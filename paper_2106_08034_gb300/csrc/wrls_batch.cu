@@ -1,0 +1,309 @@
+// Batched tick: one frame of each of n streams (of any sizes) denoised by a persistent
+// kernel pair that pulls (stream, tile) work items from a device work table.
+//
+// Per tick the host writes a table (header + one FrameWork per frame, with each frame's
+// first tile index) into one of two pinned host buffers and replays a CUDA graph captured
+// once per (buffer, state precision): copy table -> device, zero the two work counters,
+// persistent update kernel, persistent blend kernel. A CTA takes the next tile with an
+// atomicAdd on its counter until the counter passes the total; no CTA ever waits on
+// another. The tile bodies are those of the single-frame kernels, so every stream's
+// output and state are bitwise identical to denoising it alone.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "wrls_internal.h"
+#include "wrls_tiles.cuh"
+
+namespace wrls {
+
+struct FrameWork {
+  KParams kp;
+  void* prev_base;
+  float* prev_scale;
+  void* next_base;
+  float* next_scale;
+  size_t plane_stride;
+  const float* rad;
+  const float* mot;
+  float* out;
+  int pitch;
+  int W, H;
+  int reset;
+  int tiles_x;
+  int tile_begin;
+};
+
+struct BatchHeader {
+  int n;
+  int total_tiles;
+  int pad[2];
+};
+
+template <class SV> __device__ __forceinline__ SV make_view(void* base, float* scale, size_t ps, int pitch);
+template <> __device__ __forceinline__ StateF32 make_view<StateF32>(void* base, float*, size_t ps, int pitch) {
+  return StateF32{(float*)base, ps, pitch};
+}
+template <> __device__ __forceinline__ StateBF16 make_view<StateBF16>(void* base, float* scale, size_t ps, int pitch) {
+  return StateBF16{(__nv_bfloat16*)base, scale, ps, pitch};
+}
+template <> __device__ __forceinline__ StateF16 make_view<StateF16>(void* base, float* scale, size_t ps, int pitch) {
+  return StateF16{(__half*)base, scale, ps, pitch};
+}
+
+// Claim the next work item; returns its frame index in *frame and tile index in the frame.
+__device__ __forceinline__ int next_item(const BatchHeader* __restrict__ hdr,
+                                         const FrameWork* __restrict__ fw, int* counter,
+                                         int* s_item, int* s_frame, int* frame) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int t = atomicAdd(counter, 1);
+    int f = -1;
+    if (t < hdr->total_tiles) {
+      int lo = 0, hi = hdr->n - 1;  // last frame with tile_begin <= t
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (fw[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+      }
+      f = lo;
+    }
+    *s_item = t;
+    *s_frame = f;
+  }
+  __syncthreads();
+  *frame = *s_frame;
+  return *frame < 0 ? -1 : *s_item - fw[*frame].tile_begin;
+}
+
+template <class SV>
+__global__ void __launch_bounds__(kTileThreads)
+    k_batch_update(const BatchHeader* __restrict__ hdr, const FrameWork* __restrict__ fw, int* counters) {
+  __shared__ UpdateSmem sm;
+  __shared__ int s_item, s_frame;
+  for (;;) {
+    int f;
+    const int lt = next_item(hdr, fw, counters + 0, &s_item, &s_frame, &f);
+    if (lt < 0) break;
+    const FrameWork& w = fw[f];
+    const SV prev = make_view<SV>(w.prev_base, w.prev_scale, w.plane_stride, w.pitch);
+    const SV next = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
+    update_tile(sm, w.kp, w.W, w.H, w.reset != 0, prev, next, w.rad, w.mot,
+                (lt % w.tiles_x) * kTW, (lt / w.tiles_x) * kTH);
+  }
+}
+
+template <class SV>
+__global__ void __launch_bounds__(kTileThreads)
+    k_batch_blend(const BatchHeader* __restrict__ hdr, const FrameWork* __restrict__ fw, int* counters) {
+  __shared__ BlendSmem sm;
+  __shared__ int s_item, s_frame;
+  for (;;) {
+    int f;
+    const int lt = next_item(hdr, fw, counters + 1, &s_item, &s_frame, &f);
+    if (lt < 0) break;
+    const FrameWork& w = fw[f];
+    const SV cur = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
+    blend_tile(sm, w.kp, w.W, w.H, cur, w.out, (lt % w.tiles_x) * kTW, (lt / w.tiles_x) * kTH);
+  }
+}
+
+template <class SV>
+static cudaError_t persistent_grid(int* g_update, int* g_blend) {
+  int dev = 0, sms = 0, a = 0, b = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_update<SV>, kTileThreads, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_blend<SV>, kTileThreads, 0);
+  if (e != cudaSuccess) return e;
+  *g_update = sms * (a > 0 ? a : 1);
+  *g_blend = sms * (b > 0 ? b : 1);
+  return cudaSuccess;
+}
+
+template <class SV>
+static cudaError_t capture_tick(cudaStream_t cap, const void* h_table, void* d_table, size_t bytes,
+                                int* d_counters, cudaGraphExec_t* exec) {
+  int gu = 0, gb = 0;
+  cudaError_t e = persistent_grid<SV>(&gu, &gb);
+  if (e != cudaSuccess) return e;
+  const BatchHeader* hdr = (const BatchHeader*)d_table;
+  const FrameWork* fw = (const FrameWork*)((char*)d_table + sizeof(BatchHeader));
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaMemcpyAsync(d_table, h_table, bytes, cudaMemcpyHostToDevice, cap);
+  cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), cap);
+  k_batch_update<SV><<<gu, kTileThreads, 0, cap>>>(hdr, fw, d_counters);
+  k_batch_blend<SV><<<gb, kTileThreads, 0, cap>>>(hdr, fw, d_counters);
+  e = cudaStreamEndCapture(cap, &g);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+}  // namespace wrls
+
+using namespace wrls;
+
+struct wrls_batch {
+  int max_streams = 0;
+  cudaStream_t cs = nullptr;
+  cudaStream_t cap = nullptr;
+  size_t table_bytes = 0;
+  void* d_table = nullptr;
+  int* d_counters = nullptr;
+  void* h_table[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int slot = 0;
+  int device = 0;
+};
+
+static void batch_free(wrls_batch* b) {
+  for (int s = 0; s < 2; ++s) {
+    for (int p = 0; p < 3; ++p)
+      if (b->exec[s][p]) cudaGraphExecDestroy(b->exec[s][p]);
+    if (b->ev[s]) cudaEventDestroy(b->ev[s]);
+    if (b->h_table[s]) cudaFreeHost(b->h_table[s]);
+  }
+  if (b->d_table) cudaFree(b->d_table);
+  if (b->d_counters) cudaFree(b->d_counters);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaGetLastError();
+  delete b;
+}
+
+extern "C" {
+
+wrls_status wrls_batch_create(int max_streams, wrls_batch** out) {
+  if (!out) { set_error("wrls_batch_create: out is NULL"); return WRLS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (max_streams < 1 || max_streams > 4096) {
+    set_error("wrls_batch_create: max_streams %d outside [1, 4096]", max_streams);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  wrls_batch* b = new (std::nothrow) wrls_batch();
+  if (!b) { set_error("wrls_batch_create: host allocation failed"); return WRLS_ERR_OOM; }
+  b->max_streams = max_streams;
+  cudaGetDevice(&b->device);
+  b->table_bytes = sizeof(BatchHeader) + (size_t)max_streams * sizeof(FrameWork);
+  cudaError_t e = cudaMalloc(&b->d_table, b->table_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counters, 2 * sizeof(int));
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+    e = cudaMallocHost(&b->h_table[s], b->table_bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[s], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    set_error("wrls_batch_create: %s", cudaGetErrorString(e));
+    wrls_status st = e == cudaErrorMemoryAllocation ? WRLS_ERR_OOM : WRLS_ERR_CUDA;
+    batch_free(b);
+    return st;
+  }
+  *out = b;
+  return WRLS_OK;
+}
+
+wrls_status wrls_batch_set_cuda_stream(wrls_batch* b, void* cuda_stream) {
+  if (!b) { set_error("wrls_batch_set_cuda_stream: batch is NULL"); return WRLS_ERR_INVALID_ARG; }
+  b->cs = (cudaStream_t)cuda_stream;
+  return WRLS_OK;
+}
+
+wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
+  if (!b || !frames) { set_error("wrls_batch_tick: NULL argument"); return WRLS_ERR_INVALID_ARG; }
+  if (n < 1 || n > b->max_streams) {
+    set_error("wrls_batch_tick: n = %d outside [1, %d]", n, b->max_streams);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  const int prec = frames[0].stream ? frames[0].stream->prm.state_precision : -1;
+  for (int i = 0; i < n; ++i) {
+    const wrls_frame_io& io = frames[i];
+    if (!io.stream || !io.radiance || !io.motion || !io.out) {
+      set_error("wrls_batch_tick: frame %d has a NULL stream, radiance, motion or out", i);
+      return WRLS_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)io.radiance | (uintptr_t)io.motion | (uintptr_t)io.out) & 3u) {
+      set_error("wrls_batch_tick: frame %d buffers must be 4-byte aligned", i);
+      return WRLS_ERR_INVALID_ARG;
+    }
+    if (io.stream->prm.state_precision != prec) {
+      set_error("wrls_batch_tick: all streams of a tick must share one state precision");
+      return WRLS_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < i; ++k)
+      if (frames[k].stream == io.stream) {
+        set_error("wrls_batch_tick: stream of frame %d appears twice", i);
+        return WRLS_ERR_INVALID_ARG;
+      }
+  }
+  const int slot = b->slot;
+  cudaError_t e = cudaEventSynchronize(b->ev[slot]);  // the slot's previous copy has run
+  if (e != cudaSuccess) { set_error("wrls_batch_tick: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
+  BatchHeader* hdr = (BatchHeader*)b->h_table[slot];
+  FrameWork* fw = (FrameWork*)((char*)b->h_table[slot] + sizeof(BatchHeader));
+  int tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    wrls_stream* s = frames[i].stream;
+    const StateDesc& pv = s->state[s->cur];
+    const StateDesc& nx = s->state[s->cur ^ 1];
+    FrameWork& w = fw[i];
+    w.kp = s->kp;
+    w.prev_base = pv.base;
+    w.prev_scale = pv.scale;
+    w.next_base = nx.base;
+    w.next_scale = nx.scale;
+    w.plane_stride = pv.plane_stride;
+    w.rad = frames[i].radiance;
+    w.mot = frames[i].motion;
+    w.out = frames[i].out;
+    w.pitch = pv.pitch;
+    w.W = s->W;
+    w.H = s->H;
+    w.reset = s->need_reset ? 1 : 0;
+    w.tiles_x = (s->W + kTW - 1) / kTW;
+    w.tile_begin = tiles;
+    tiles += w.tiles_x * ((s->H + kTH - 1) / kTH);
+  }
+  hdr->n = n;
+  hdr->total_tiles = tiles;
+  if (!b->exec[slot][prec]) {
+    const size_t bytes = b->table_bytes;
+    switch (prec) {
+      case 0: e = capture_tick<StateF32>(b->cap, b->h_table[slot], b->d_table, bytes, b->d_counters, &b->exec[slot][prec]); break;
+      case 1: e = capture_tick<StateBF16>(b->cap, b->h_table[slot], b->d_table, bytes, b->d_counters, &b->exec[slot][prec]); break;
+      default: e = capture_tick<StateF16>(b->cap, b->h_table[slot], b->d_table, bytes, b->d_counters, &b->exec[slot][prec]); break;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->exec[slot][prec] = nullptr;
+      set_error("wrls_batch_tick: graph capture failed: %s", cudaGetErrorString(e));
+      return WRLS_ERR_CUDA;
+    }
+  }
+  e = cudaGraphLaunch(b->exec[slot][prec], b->cs);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], b->cs);
+  if (e != cudaSuccess) { set_error("wrls_batch_tick: graph launch: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
+  for (int i = 0; i < n; ++i) {
+    wrls_stream* s = frames[i].stream;
+    s->cur ^= 1;
+    s->need_reset = false;
+    s->has_frame = true;
+    s->frames++;
+  }
+  b->slot ^= 1;
+  return WRLS_OK;
+}
+
+void wrls_batch_destroy(wrls_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->cs);
+  for (int s = 0; s < 2; ++s)
+    if (b->ev[s]) cudaEventSynchronize(b->ev[s]);
+  batch_free(b);
+}
+
+}  // extern "C"

@@ -1,0 +1,249 @@
+// Device-side building blocks of the wRLS denoiser (Sec. 5.2-5.3 of Iglesias-Guitian,
+// Mane, Moon, IEEE TVCG 2020): kernel parameters, the per-pixel state storage formats,
+// and the per-pixel temporal update (reprojection, Eq. 12, Eq. 13, Eq. 8/14/9/11).
+//
+// State per pixel: beta[3][4] (one linear model per colour channel, Eq. 5), the
+// symmetric 4x4 inverse covariance P shared by the three channels (10 values), and the
+// temporal feature z[3] (Eq. 12): 25 values. Planes: 0-11 beta[c][a] (c*4+a),
+// 12-21 P upper triangle (00,01,02,03,11,12,13,22,23,33), 22-24 z.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wrls {
+
+constexpr int kNState = 25;
+constexpr int kBeta = 0;
+constexpr int kP = 12;
+constexpr int kZ = 22;
+constexpr int kMaxRadius = 2;
+constexpr int kMaxTaps = (2 * kMaxRadius + 1) * (2 * kMaxRadius + 1);
+
+// Everything a kernel needs from wrls_params, precomputed on the host.
+struct KParams {
+  float lambda;       // forgetting factor (Eq. 10-11)
+  float inv_lambda;
+  float alpha;        // Eq. 12
+  float one_m_alpha;
+  float eps;          // Eq. 13
+  float w_k;          // log2(e) / h^2: Eq. 13 exponent in base 2
+  float p0_delta;     // P of a restarted pixel
+  float p_trace_max;  // wind-up guard, 0 = off
+  float range_k;      // log2(e) / h_s^2: blend range exponent in base 2
+  float spatial[kMaxTaps];  // -(dx^2+dy^2) / (2 sigma_s^2) * log2(e), row-major offsets
+  int radius;
+  int weight_mode;
+  int clamp_mode;
+  int blend_mode;
+  int feature_mode;
+  int init_mode;
+};
+
+// 2^x on the SFU (PTX ex2.approx, max relative error about 2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---- state storage formats -------------------------------------------------------------
+// A view of one state copy: plane p of pixel (x, y) is at p * plane_stride + y * pitch + x.
+
+struct StateF32 {
+  float* base;
+  size_t plane_stride;
+  int pitch;
+  __device__ __forceinline__ void load(size_t idx, float v[kNState]) const {
+#pragma unroll
+    for (int p = 0; p < kNState; ++p) v[p] = __ldg(base + p * plane_stride + idx);
+  }
+  __device__ __forceinline__ void load_beta_z(size_t idx, float b[12], float z[3]) const {
+#pragma unroll
+    for (int p = 0; p < 12; ++p) b[p] = __ldg(base + p * plane_stride + idx);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z[c] = __ldg(base + (kZ + c) * plane_stride + idx);
+  }
+  __device__ __forceinline__ void store(size_t idx, const float v[kNState]) const {
+#pragma unroll
+    for (int p = 0; p < kNState; ++p) base[p * plane_stride + idx] = v[p];
+  }
+};
+
+// 16-bit storage: beta and z raw, P divided by a per-pixel binary32 scale s = max diag(P)
+// (plane 0 of `scale`), all arithmetic in binary32, round-to-nearest-even on store.
+template <typename T>
+struct State16 {
+  T* base;
+  float* scale;
+  size_t plane_stride;
+  int pitch;
+  static __device__ __forceinline__ float to_f(T v);
+  static __device__ __forceinline__ T from_f(float v);
+  __device__ __forceinline__ void load(size_t idx, float v[kNState]) const {
+    const float s = __ldg(scale + idx);
+#pragma unroll
+    for (int p = 0; p < kNState; ++p) {
+      float f = to_f(base[p * plane_stride + idx]);
+      v[p] = (p >= kP && p < kZ) ? f * s : f;
+    }
+  }
+  __device__ __forceinline__ void load_beta_z(size_t idx, float b[12], float z[3]) const {
+#pragma unroll
+    for (int p = 0; p < 12; ++p) b[p] = to_f(base[p * plane_stride + idx]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z[c] = to_f(base[(kZ + c) * plane_stride + idx]);
+  }
+  __device__ __forceinline__ void store(size_t idx, const float v[kNState]) const {
+    float s = fmaxf(fmaxf(v[kP + 0], v[kP + 4]), fmaxf(v[kP + 7], v[kP + 9]));
+    if (!(s > 0.0f) || !isfinite(s)) s = 1.0f;
+    const float inv_s = 1.0f / s;
+    scale[idx] = s;
+#pragma unroll
+    for (int p = 0; p < kNState; ++p) {
+      float f = (p >= kP && p < kZ) ? v[p] * inv_s : v[p];
+      base[p * plane_stride + idx] = from_f(f);
+    }
+  }
+};
+template <> __device__ __forceinline__ float State16<__nv_bfloat16>::to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 State16<__nv_bfloat16>::from_f(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ float State16<__half>::to_f(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ __half State16<__half>::from_f(float v) { return __float2half_rn(v); }
+
+using StateBF16 = State16<__nv_bfloat16>;
+using StateF16 = State16<__half>;
+
+// ---- per-pixel temporal update ----------------------------------------------------------
+
+// Initial model of a restarted pixel: beta = 0 (init_mode 0) or the feature pass-through
+// beta_c = e_{c+1} (beta_c = z_c with p = [1]); P = p0_delta * I on the used block.
+__device__ __forceinline__ void init_model(const KParams& kp, const float z[3], float st[kNState]) {
+#pragma unroll
+  for (int p = 0; p < 22; ++p) st[p] = 0.0f;
+  if (kp.init_mode == 1) {
+    if (kp.feature_mode == 0) {
+      st[kBeta + 0 * 4 + 1] = 1.0f;
+      st[kBeta + 1 * 4 + 2] = 1.0f;
+      st[kBeta + 2 * 4 + 3] = 1.0f;
+    } else {
+      st[kBeta + 0] = z[0];
+      st[kBeta + 4] = z[1];
+      st[kBeta + 8] = z[2];
+    }
+  }
+  st[kP + 0] = kp.p0_delta;
+  if (kp.feature_mode == 0) {
+    st[kP + 4] = kp.p0_delta;
+    st[kP + 7] = kp.p0_delta;
+    st[kP + 9] = kp.p0_delta;
+  }
+}
+
+// Bilinear fetch of the previous state at q = (qx, qy) (Sec. 5.3: models are reprojected,
+// not colours). q is valid; taps beyond the last row/column are clamped.
+template <class SV>
+__device__ __forceinline__ void gather_bilinear(const SV& prev, int W, int H, float qx, float qy,
+                                                float st[kNState]) {
+  const int x0 = (int)floorf(qx), y0 = (int)floorf(qy);
+  const float fx = qx - (float)x0, fy = qy - (float)y0;
+  const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
+  const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy);
+  const float w01 = (1.0f - fx) * fy, w11 = fx * fy;
+  float a[kNState], b[kNState];
+  prev.load((size_t)y0 * prev.pitch + x0, a);
+  prev.load((size_t)y0 * prev.pitch + x1, b);
+#pragma unroll
+  for (int p = 0; p < kNState; ++p) st[p] = w00 * a[p] + w10 * b[p];
+  prev.load((size_t)y1 * prev.pitch + x0, a);
+  prev.load((size_t)y1 * prev.pitch + x1, b);
+#pragma unroll
+  for (int p = 0; p < kNState; ++p) st[p] += w01 * a[p] + w11 * b[p];
+}
+
+// Eq. 12 feature, Eq. 13 weight and the wRLS update (Eq. 8, 14, 9, 11) of one pixel.
+//   st     in: reprojected state (or anything if !valid); out: state of frame t
+//   I      noisy sample I~_j(t); missing = a channel is non-finite
+//   lo/hi  per-channel min/max of I~ over the 3x3 neighbours (have_box = any finite one)
+// Returns w.
+__device__ __forceinline__ float update_pixel(const KParams& kp, bool valid, float st[kNState],
+                                              const float I[3], bool missing, const float lo[3],
+                                              const float hi[3], bool have_box) {
+  float z[3];
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float zc = st[kZ + c];
+      if (kp.clamp_mode == 0 && have_box) zc = fminf(fmaxf(zc, lo[c]), hi[c]);
+      z[c] = missing ? zc : fmaf(kp.alpha, zc, kp.one_m_alpha * I[c]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z[c] = missing ? 0.0f : I[c];
+    init_model(kp, z, st);
+  }
+
+  // Eq. 13 (one scalar per pixel over RGB); RLS mode: w = 1
+  float w;
+  if (missing) {
+    w = 0.0f;
+  } else if (kp.weight_mode == 1) {
+    w = 1.0f;
+  } else {
+    const float d0 = I[0] - z[0], d1 = I[1] - z[1], d2 = I[2] - z[2];
+    const float dist2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const float nI = sqrtf(I[0] * I[0] + I[1] * I[1] + I[2] * I[2]);
+    const float nz = sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+    const float m = fminf(nI, nz) + kp.eps;
+    w = ex2_approx(-(dist2 / (m * m)) * kp.w_k);
+  }
+
+  // predictor p = [1, z] (Sec. 5.1), or [1] without feature
+  const float z0 = kp.feature_mode == 0 ? z[0] : 0.0f;
+  const float z1 = kp.feature_mode == 0 ? z[1] : 0.0f;
+  const float z2 = kp.feature_mode == 0 ? z[2] : 0.0f;
+  float* P = st + kP;
+  // k = P p
+  const float k0 = P[0] + P[1] * z0 + P[2] * z1 + P[3] * z2;
+  const float k1 = P[1] + P[4] * z0 + P[5] * z1 + P[6] * z2;
+  const float k2 = P[2] + P[5] * z0 + P[7] * z1 + P[8] * z2;
+  const float k3 = P[3] + P[6] * z0 + P[8] * z1 + P[9] * z2;
+  const float s = k0 + k1 * z0 + k2 * z1 + k3 * z2;  // p^T P p
+  // Eq. 14: q^w = P p / (lambda / w + p^T P p) = (w / (lambda + w s)) P p
+  const float g = w / (kp.lambda + w * s);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float* b = st + kBeta + 4 * c;
+    const float e = missing ? 0.0f : I[c] - (b[0] + b[1] * z0 + b[2] * z1 + b[3] * z2);  // Eq. 8
+    const float ge = g * e;                                                            // Eq. 9
+    b[0] += ge * k0;
+    b[1] += ge * k1;
+    b[2] += ge * k2;
+    b[3] += ge * k3;
+  }
+  // Eq. 11: P <- (P - q^w p^T P) / lambda, with p^T P = k^T
+  const float k[4] = {k0, k1, k2, k3};
+  int e = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bb = a; bb < 4; ++bb, ++e) P[e] = (P[e] - g * k[a] * k[bb]) * kp.inv_lambda;
+  if (kp.p_trace_max > 0.0f) {
+    const bool f = kp.feature_mode == 0;
+    const float tr = P[0] + (f ? P[4] + P[7] + P[9] : 0.0f);
+    const bool bad = !(P[0] > 0.0f) || (f && (!(P[4] > 0.0f) || !(P[7] > 0.0f) || !(P[9] > 0.0f)));
+    if (bad || tr > kp.p_trace_max) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) P[q] = 0.0f;
+      P[0] = kp.p0_delta;
+      if (f) { P[4] = kp.p0_delta; P[7] = kp.p0_delta; P[9] = kp.p0_delta; }
+    }
+  }
+  st[kZ + 0] = z[0];
+  st[kZ + 1] = z[1];
+  st[kZ + 2] = z[2];
+  return w;
+}
+
+}  // namespace wrls

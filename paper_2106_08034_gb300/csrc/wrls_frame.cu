@@ -1,0 +1,73 @@
+// Single-frame kernels of the wRLS denoiser: one CTA per 32 x 8 tile.
+//   k_update     : reprojection + Eq. 12 + Eq. 13 + Eq. 8/14/9/11 (tile body update_tile)
+//   k_blend      : 5x5 spatio-temporal blend of Sec. 5.3 (tile body blend_tile)
+//   k_read_state : decode a state copy to 25 binary32 planes
+#include "wrls_internal.h"
+#include "wrls_tiles.cuh"
+
+namespace wrls {
+
+template <class SV>
+__global__ void __launch_bounds__(kTileThreads)
+    k_update(const KParams kp, const int W, const int H, const int reset, const SV prev,
+             const SV next, const float* __restrict__ rad, const float* __restrict__ mot) {
+  __shared__ UpdateSmem sm;
+  update_tile(sm, kp, W, H, reset != 0, prev, next, rad, mot, blockIdx.x * kTW, blockIdx.y * kTH);
+}
+
+template <class SV>
+__global__ void __launch_bounds__(kTileThreads)
+    k_blend(const KParams kp, const int W, const int H, const SV cur, float* __restrict__ out) {
+  __shared__ BlendSmem sm;
+  blend_tile(sm, kp, W, H, cur, out, blockIdx.x * kTW, blockIdx.y * kTH);
+}
+
+template <class SV>
+__global__ void k_read_state(const int W, const int H, const SV cur, float* __restrict__ dst) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W || y >= H) return;
+  float v[kNState];
+  cur.load((size_t)y * cur.pitch + x, v);
+  const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
+#pragma unroll
+  for (int p = 0; p < kNState; ++p) dst[p * npix + j] = v[p];
+}
+
+static dim3 tile_grid(int W, int H) { return dim3((W + kTW - 1) / kTW, (H + kTH - 1) / kTH); }
+
+cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
+                          const float* rad, const float* mot, cudaStream_t cs) {
+  const dim3 grid = tile_grid(prev.W, prev.H);
+  const int rs = reset ? 1 : 0;
+  switch (prev.precision) {
+    case 0: k_update<<<grid, kTileThreads, 0, cs>>>(kp, prev.W, prev.H, rs, prev.f32(), next.f32(), rad, mot); break;
+    case 1: k_update<<<grid, kTileThreads, 0, cs>>>(kp, prev.W, prev.H, rs, prev.bf16(), next.bf16(), rad, mot); break;
+    case 2: k_update<<<grid, kTileThreads, 0, cs>>>(kp, prev.W, prev.H, rs, prev.f16(), next.f16(), rad, mot); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend(const KParams& kp, const StateDesc& cur, float* out, cudaStream_t cs) {
+  const dim3 grid = tile_grid(cur.W, cur.H);
+  switch (cur.precision) {
+    case 0: k_blend<<<grid, kTileThreads, 0, cs>>>(kp, cur.W, cur.H, cur.f32(), out); break;
+    case 1: k_blend<<<grid, kTileThreads, 0, cs>>>(kp, cur.W, cur.H, cur.bf16(), out); break;
+    case 2: k_blend<<<grid, kTileThreads, 0, cs>>>(kp, cur.W, cur.H, cur.f16(), out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs) {
+  const dim3 grid((cur.W + 127) / 128, cur.H);
+  switch (cur.precision) {
+    case 0: k_read_state<<<grid, 128, 0, cs>>>(cur.W, cur.H, cur.f32(), dst); break;
+    case 1: k_read_state<<<grid, 128, 0, cs>>>(cur.W, cur.H, cur.bf16(), dst); break;
+    case 2: k_read_state<<<grid, 128, 0, cs>>>(cur.W, cur.H, cur.f16(), dst); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace wrls

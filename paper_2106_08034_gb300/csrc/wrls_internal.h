@@ -1,0 +1,64 @@
+// Internal declarations shared by the CUDA translation units of libwrls.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/wrls.h"
+#include "wrls_device.cuh"
+
+namespace wrls {
+
+// Geometry of one state copy in device memory. Planar: kNState planes of `elem` bytes
+// per value, each plane pitch x H values padded to a multiple of 64 values; for the
+// 16-bit formats one binary32 P-scale plane follows the 25 planes.
+struct StateDesc {
+  void* base = nullptr;
+  float* scale = nullptr;
+  int precision = 0;
+  int W = 0, H = 0, pitch = 0;
+  size_t plane_stride = 0;  // in values
+
+  StateF32 f32() const { return StateF32{(float*)base, plane_stride, pitch}; }
+  StateBF16 bf16() const { return StateBF16{(__nv_bfloat16*)base, scale, plane_stride, pitch}; }
+  StateF16 f16() const { return StateF16{(__half*)base, scale, plane_stride, pitch}; }
+};
+
+// Bytes of one state copy and its geometry.
+size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_stride,
+                         size_t* scale_offset_bytes);
+
+// Host-side conversion of the public parameters (validated) into kernel parameters.
+bool make_kparams(const wrls_params& p, KParams* kp, const char** why);
+
+cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
+                          const float* rad, const float* mot, cudaStream_t cs);
+cudaError_t launch_blend(const KParams& kp, const StateDesc& cur, float* out, cudaStream_t cs);
+cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs);
+
+void set_error(const char* fmt, ...);
+
+}  // namespace wrls
+
+// The stream object behind the opaque C handle.
+struct wrls_stream {
+  int W = 0, H = 0;
+  wrls_params prm{};
+  wrls::KParams kp{};
+  wrls::StateDesc state[2];
+  void* mem = nullptr;          // both state copies
+  size_t mem_bytes = 0;
+  int cur = 0;                  // copy holding frame t-1
+  bool need_reset = true;
+  bool has_frame = false;
+  cudaStream_t cs = nullptr;
+  int device = 0;
+  uint64_t frames = 0;
+  float* staging = nullptr;     // device I/O buffers of wrls_denoise_frame_host
+  // kernel tracing
+  static constexpr int kTimingCap = 8192;
+  cudaEvent_t* tev = nullptr;   // 3 events per recorded frame
+  int t_pending = 0;
+  double t_update_ms = 0.0, t_blend_ms = 0.0;
+  uint64_t t_frames = 0;
+};

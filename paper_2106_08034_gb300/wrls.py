@@ -1,0 +1,252 @@
+"""Thin ctypes binding of libwrls.so (C ABI in include/wrls.h).
+
+Argument marshalling only: every step of the denoiser runs in the library's CUDA kernels.
+Functions keep the C names. Buffers may be torch tensors (their data_ptr() is passed;
+device tensors for the device entry points, CPU tensors for wrls_denoise_frame_host) or
+raw integer addresses. CUDA streams may be torch.cuda.Stream objects, raw handles or None.
+
+Loading raises if the library has not been built (``__graft_entry__.build()`` or
+``python -m paper_2106_08034_gb300.build``): there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwrls.so")
+
+WRLS_OK = 0
+WRLS_ERR_INVALID_ARG = 1
+WRLS_ERR_OOM = 2
+WRLS_ERR_CUDA = 3
+WRLS_ERR_STATE = 4
+WRLS_ERR_TIMEOUT = 5
+
+WRLS_STATE_F32 = 0
+WRLS_STATE_BF16 = 1
+WRLS_STATE_F16 = 2
+
+N_STATE = 25
+
+# Every symbol include/wrls.h declares (checked by the ABI test).
+EXPORTED = [
+    "wrls_params_default", "wrls_state_bytes", "wrls_stream_create", "wrls_stream_set_cuda_stream",
+    "wrls_denoise_frame", "wrls_denoise_frame_host", "wrls_stream_reset", "wrls_stream_destroy",
+    "wrls_stream_read_state", "wrls_stream_frames", "wrls_last_error",
+    "wrls_stream_enable_timing", "wrls_stream_kernel_times",
+    "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
+]
+
+
+class WrlsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("wrls status %d: %s" % (status, message))
+        self.status = status
+
+
+class wrls_params(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("lambda_", ctypes.c_float), ("h", ctypes.c_float), ("alpha", ctypes.c_float),
+        ("eps", ctypes.c_float), ("p0_delta", ctypes.c_float), ("sigma_s", ctypes.c_float),
+        ("h_s", ctypes.c_float), ("p_trace_max", ctypes.c_float),
+        ("radius", ctypes.c_int32), ("weight_mode", ctypes.c_int32), ("clamp_mode", ctypes.c_int32),
+        ("blend_mode", ctypes.c_int32), ("feature_mode", ctypes.c_int32), ("init_mode", ctypes.c_int32),
+        ("state_precision", ctypes.c_int32), ("n_features", ctypes.c_int32),
+    ]
+
+
+class wrls_frame_io(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("radiance", ctypes.c_void_p),
+                ("variance", ctypes.c_void_p), ("features", ctypes.c_void_p),
+                ("motion", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libwrls.so (raises if missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libwrls.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, P = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(wrls_params)
+    sig = {
+        "wrls_params_default": (None, [P]),
+        "wrls_state_bytes": (ctypes.c_size_t, [i, i, P]),
+        "wrls_stream_create": (i, [i, i, P, ctypes.POINTER(vp)]),
+        "wrls_stream_set_cuda_stream": (i, [vp, vp]),
+        "wrls_denoise_frame": (i, [vp, vp, vp, vp, vp, vp]),
+        "wrls_denoise_frame_host": (i, [vp, vp, vp, vp, vp, vp]),
+        "wrls_stream_reset": (i, [vp]),
+        "wrls_stream_destroy": (None, [vp]),
+        "wrls_stream_read_state": (i, [vp, vp]),
+        "wrls_stream_frames": (ctypes.c_uint64, [vp]),
+        "wrls_last_error": (ctypes.c_char_p, []),
+        "wrls_stream_enable_timing": (i, [vp, i]),
+        "wrls_stream_kernel_times": (i, [vp, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
+        "wrls_batch_create": (i, [i, ctypes.POINTER(vp)]),
+        "wrls_batch_set_cuda_stream": (i, [vp, vp]),
+        "wrls_batch_tick": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
+        "wrls_batch_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream_handle(cs) -> Optional[int]:
+    if cs is None:
+        return None
+    if isinstance(cs, int):
+        return cs
+    return int(cs.cuda_stream)
+
+
+def _check(status: int) -> None:
+    if status != WRLS_OK:
+        raise WrlsError(status, lib().wrls_last_error().decode(errors="replace"))
+
+
+# --- C-named entry points ---------------------------------------------------------------
+
+def wrls_params_default(**overrides) -> wrls_params:
+    p = wrls_params()
+    lib().wrls_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    return p
+
+
+def wrls_state_bytes(width: int, height: int, params: Optional[wrls_params] = None) -> int:
+    p = params if params is not None else wrls_params_default()
+    return int(lib().wrls_state_bytes(int(width), int(height), ctypes.byref(p)))
+
+
+def wrls_stream_create(width: int, height: int, params: Optional[wrls_params] = None) -> int:
+    p = params if params is not None else wrls_params_default()
+    h = ctypes.c_void_p()
+    _check(lib().wrls_stream_create(int(width), int(height), ctypes.byref(p), ctypes.byref(h)))
+    return int(h.value)
+
+
+def wrls_stream_set_cuda_stream(stream: int, cuda_stream) -> None:
+    _check(lib().wrls_stream_set_cuda_stream(stream, _stream_handle(cuda_stream)))
+
+
+def wrls_denoise_frame(stream: int, radiance, variance, features, motion, out) -> None:
+    _check(lib().wrls_denoise_frame(stream, _ptr(radiance), _ptr(variance), _ptr(features),
+                                    _ptr(motion), _ptr(out)))
+
+
+def wrls_denoise_frame_host(stream: int, radiance, variance, features, motion, out) -> None:
+    _check(lib().wrls_denoise_frame_host(stream, _ptr(radiance), _ptr(variance), _ptr(features),
+                                         _ptr(motion), _ptr(out)))
+
+
+def wrls_stream_reset(stream: int) -> None:
+    _check(lib().wrls_stream_reset(stream))
+
+
+def wrls_stream_destroy(stream: Optional[int]) -> None:
+    if stream:
+        lib().wrls_stream_destroy(stream)
+
+
+def wrls_stream_read_state(stream: int, dst) -> None:
+    _check(lib().wrls_stream_read_state(stream, _ptr(dst)))
+
+
+def wrls_stream_frames(stream: int) -> int:
+    return int(lib().wrls_stream_frames(stream))
+
+
+def wrls_stream_enable_timing(stream: int, enable: bool = True) -> None:
+    _check(lib().wrls_stream_enable_timing(stream, 1 if enable else 0))
+
+
+def wrls_stream_kernel_times(stream: int):
+    """(update_ms, blend_ms, frames) summed since the last call."""
+    a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+    _check(lib().wrls_stream_kernel_times(stream, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+    return float(a.value), float(b.value), int(n.value)
+
+
+def wrls_last_error() -> str:
+    return lib().wrls_last_error().decode(errors="replace")
+
+
+def wrls_batch_create(max_streams: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().wrls_batch_create(int(max_streams), ctypes.byref(h)))
+    return int(h.value)
+
+
+def wrls_batch_set_cuda_stream(batch: int, cuda_stream) -> None:
+    _check(lib().wrls_batch_set_cuda_stream(batch, _stream_handle(cuda_stream)))
+
+
+def wrls_batch_tick(batch: int, frames: Sequence[tuple]) -> None:
+    """frames: sequence of (stream, radiance, variance, features, motion, out)."""
+    arr = (wrls_frame_io * len(frames))()
+    for k, (s, rad, var, feat, mot, out) in enumerate(frames):
+        arr[k] = wrls_frame_io(s, _ptr(rad), _ptr(var), _ptr(feat), _ptr(mot), _ptr(out))
+    _check(lib().wrls_batch_tick(batch, arr, len(frames)))
+
+
+def wrls_batch_destroy(batch: Optional[int]) -> None:
+    if batch:
+        lib().wrls_batch_destroy(batch)
+
+
+# --- convenience wrapper ---------------------------------------------------------------------
+
+class Stream:
+    """Owns one wrls_stream; frames are denoised on the given torch CUDA stream."""
+
+    def __init__(self, width: int, height: int, params: Optional[wrls_params] = None, cuda_stream=None):
+        self.width, self.height = int(width), int(height)
+        self.params = params if params is not None else wrls_params_default()
+        self.handle = wrls_stream_create(width, height, self.params)
+        if cuda_stream is not None:
+            wrls_stream_set_cuda_stream(self.handle, cuda_stream)
+
+    def set_cuda_stream(self, cuda_stream) -> None:
+        wrls_stream_set_cuda_stream(self.handle, cuda_stream)
+
+    def denoise(self, radiance, motion, out, variance=None, features=None) -> None:
+        wrls_denoise_frame(self.handle, radiance, variance, features, motion, out)
+
+    def reset(self) -> None:
+        wrls_stream_reset(self.handle)
+
+    def read_state(self, dst) -> None:
+        wrls_stream_read_state(self.handle, dst)
+
+    def close(self) -> None:
+        if self.handle:
+            wrls_stream_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/wrls.h
+declares; host-only entry points behave (no GPU needed)."""
+import os
+import re
+
+import pytest
+
+from paper_2106_08034_gb300 import build as B
+from paper_2106_08034_gb300 import wrls as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "wrls.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    names = set(re.findall(r"\b(wrls_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return W.lib()
+
+
+def test_header_and_binding_agree():
+    assert _declared_functions() == sorted(W.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_params_default_are_the_papers(lib):
+    p = W.wrls_params_default()
+    assert p.struct_size == __import__("ctypes").sizeof(W.wrls_params)
+    assert abs(p.lambda_ - 0.998) < 1e-7 and p.h == 0.75 and p.alpha == 0.75 and p.radius == 2
+
+
+def test_state_bytes(lib):
+    p = W.wrls_params_default()
+    b32 = W.wrls_state_bytes(1920, 1080, p)
+    assert b32 >= 2 * 25 * 4 * 1920 * 1080 and b32 < 2 * 25 * 4 * 1920 * 1088 + 4096
+    p.state_precision = W.WRLS_STATE_BF16
+    b16 = W.wrls_state_bytes(1920, 1080, p)
+    assert b16 >= 2 * 54 * 1920 * 1080 and b16 < 0.6 * b32
+    assert W.wrls_state_bytes(0, 10, p) == 0 and W.wrls_state_bytes(10, 20000, p) == 0
+
+
+def test_invalid_arguments_are_rejected_on_the_host(lib):
+    with pytest.raises(W.WrlsError) as e:
+        W.wrls_stream_create(0, 10)
+    assert e.value.status == W.WRLS_ERR_INVALID_ARG and "width" in W.wrls_last_error()
+    p = W.wrls_params_default()
+    p.radius = 3
+    with pytest.raises(W.WrlsError):
+        W.wrls_stream_create(8, 8, p)
+    p = W.wrls_params_default()
+    p.struct_size = 4
+    with pytest.raises(W.WrlsError):
+        W.wrls_stream_create(8, 8, p)
+    with pytest.raises(W.WrlsError):
+        W.wrls_batch_create(0)
+    assert lib.wrls_denoise_frame(None, None, None, None, None, None) == W.WRLS_ERR_INVALID_ARG
+    W.wrls_stream_destroy(0)
+    W.wrls_batch_destroy(0)

@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded
+inputs. FP32 state: max relative error <= 1e-3 per pixel on the denoised colour and on
+the temporal feature z, over every frame (relative to max(|oracle|, 1e-2))."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2106_08034_gb300 import synth
+from paper_2106_08034_gb300 import wrls as W
+
+from helpers import FLOOR, REL_TOL, cpu_frames, oracle_params_from, oracle_z_planes, rel_err, relmse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2106_08034_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    W.lib()
+
+
+def run_pair(frames, width, height, params=None, hooks=None, check_z=True, tol=REL_TOL):
+    """Denoise the frames with the GPU and with the oracle; assert parity every frame.
+    Returns the per-frame max relative errors."""
+    p = params if params is not None else W.wrls_params_default()
+    s = W.Stream(width, height, p)
+    st = O.OracleStream(width, height, oracle_params_from(p))
+    out = torch.empty(3, height, width, device="cuda")
+    zbuf = torch.empty(W.N_STATE, height, width, device="cuda")
+    errs = []
+    for t, f in enumerate(frames):
+        rad, mot = f["radiance"].clone(), f["motion"].clone()
+        if hooks is not None:
+            rad, mot = hooks(t, rad, mot)
+        s.denoise(rad.cuda(), mot.cuda(), out)
+        ref, _, _ = st.frame(rad.numpy(), mot.numpy())
+        torch.cuda.synchronize()
+        e = rel_err(out.cpu().numpy(), ref)
+        ez = 0.0
+        if check_z:
+            s.read_state(zbuf)
+            ez = rel_err(zbuf[22:25].cpu().numpy(), oracle_z_planes(st))
+        errs.append(max(e, ez))
+        assert e <= tol and ez <= tol, "frame %d: out err %.3g, z err %.3g" % (t, e, ez)
+    s.close()
+    return errs
+
+
+def test_static_128x128_8f():
+    spec = synth.static_128x128_8f()
+    run_pair(cpu_frames(spec), spec.width, spec.height)
+
+
+def test_pan_fireflies_ragged_tiles():
+    spec = synth.SceneSpec(250, 150, 24, seed=31, motion="pan", firefly_frac=0.05)
+    run_pair(cpu_frames(spec), spec.width, spec.height)
+
+
+def test_orbit_edit_light_move_120_frames():
+    spec = synth.SceneSpec(203, 117, 120, seed=32, motion="orbit", firefly_frac=0.05,
+                           tf_edit_frame=60, light_move_frame=90)
+    run_pair(cpu_frames(spec), spec.width, spec.height)
+
+
+@pytest.mark.parametrize("mode", ["rls", "noclamp", "blend_own", "temporal_only", "radius1",
+                                  "no_feature", "passthrough", "trace_guard", "lambda1"])
+def test_modes(mode):
+    kw = {"rls": dict(weight_mode=1), "noclamp": dict(clamp_mode=1), "blend_own": dict(blend_mode=1),
+          "temporal_only": dict(radius=0), "radius1": dict(radius=1), "no_feature": dict(feature_mode=1),
+          "passthrough": dict(init_mode=1), "trace_guard": dict(p_trace_max=3.9),
+          "lambda1": {"lambda": 1.0}}[mode]
+    p = W.wrls_params_default(**kw)
+    spec = synth.SceneSpec(70, 45, 16, seed=33, motion="orbit", firefly_frac=0.05)
+    run_pair(cpu_frames(spec), spec.width, spec.height, p)
+
+
+@pytest.mark.parametrize("wh", [(1, 1), (1, 37), (41, 1), (2, 2), (33, 9), (32, 8), (64, 16)])
+def test_degenerate_sizes(wh):
+    w, h = wh
+    spec = synth.SceneSpec(w, h, 6, seed=34, motion="orbit", firefly_frac=0.1)
+    run_pair(cpu_frames(spec), w, h)
+
+
+def test_missing_samples_and_bad_motion():
+    spec = synth.SceneSpec(90, 60, 10, seed=35, motion="orbit", firefly_frac=0.05)
+
+    def hooks(t, rad, mot):
+        g = torch.Generator().manual_seed(100 + t)
+        m = torch.rand(60, 90, generator=g) < 0.03
+        rad[0][m] = float("nan")
+        rad[2][torch.rand(60, 90, generator=g) < 0.01] = float("inf")
+        mot[0][torch.rand(60, 90, generator=g) < 0.02] = float("nan")
+        mot[1][torch.rand(60, 90, generator=g) < 0.02] = 1e6
+        mot[0][:, :4] = -7.25                      # leaves the image on the left
+        if t == 6:
+            rad[:, 10:13, 20:23] = float("nan")    # a 3x3 hole: clamp box of the centre is empty
+        return rad, mot
+    run_pair(cpu_frames(spec), 90, 60, hooks=hooks)
+
+
+def test_reset_restarts_every_pixel():
+    spec = synth.SceneSpec(64, 40, 8, seed=36, motion="pan", firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    s = W.Stream(64, 40)
+    fresh = W.Stream(64, 40)
+    o1 = torch.empty(3, 40, 64, device="cuda")
+    o2 = torch.empty_like(o1)
+    for t in range(5):
+        s.denoise(fr[t]["radiance"].cuda(), fr[t]["motion"].cuda(), o1)
+    s.reset()
+    s.denoise(fr[5]["radiance"].cuda(), fr[5]["motion"].cuda(), o1)
+    fresh.denoise(fr[5]["radiance"].cuda(), fr[5]["motion"].cuda(), o2)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2)
+    assert W.wrls_stream_frames(s.handle) == 6
+
+
+def test_host_entry_matches_device_entry():
+    spec = synth.SceneSpec(120, 70, 6, seed=37, motion="orbit", firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    a = W.Stream(120, 70)
+    b = W.Stream(120, 70)
+    od = torch.empty(3, 70, 120, device="cuda")
+    oh = torch.empty(3, 70, 120).pin_memory()
+    for f in fr:
+        rad_h, mot_h = f["radiance"].pin_memory(), f["motion"].pin_memory()
+        a.denoise(rad_h.cuda(), mot_h.cuda(), od)
+        W.wrls_denoise_frame_host(b.handle, rad_h, None, None, mot_h, oh)
+        torch.cuda.synchronize()
+        assert torch.equal(od.cpu(), oh)
+
+
+def test_batch_tick_equals_each_stream_alone():
+    sizes = [(64, 48), (100, 33), (257, 129), (31, 7), (128, 128)]
+    specs = [synth.SceneSpec(w, h, 5, seed=40 + i, motion="orbit", firefly_frac=0.05)
+             for i, (w, h) in enumerate(sizes)]
+    frames = [cpu_frames(sp) for sp in specs]
+    alone = [W.Stream(w, h) for (w, h) in sizes]
+    mixed = [W.Stream(w, h) for (w, h) in sizes]
+    batch = W.wrls_batch_create(8)
+    try:
+        for t in range(5):
+            outs_a, outs_b, io = [], [], []
+            for i, (w, h) in enumerate(sizes):
+                rad, mot = frames[i][t]["radiance"].cuda(), frames[i][t]["motion"].cuda()
+                oa = torch.empty(3, h, w, device="cuda")
+                ob = torch.empty_like(oa)
+                alone[i].denoise(rad, mot, oa)
+                io.append((mixed[i].handle, rad, None, None, mot, ob))
+                outs_a.append(oa)
+                outs_b.append(ob)
+            order = [(t + k) % len(sizes) for k in range(len(sizes))]   # any order
+            W.wrls_batch_tick(batch, [io[k] for k in order])
+            torch.cuda.synchronize()
+            for oa, ob in zip(outs_a, outs_b):
+                assert torch.equal(oa, ob)
+    finally:
+        W.wrls_batch_destroy(batch)
+
+
+def test_full_size_pan_1080p_120_frames():
+    """The bench workload at full size: 1920x1080, 120 frames, pan 1.7 px/frame, 5%
+    fireflies; every pixel of every frame against the oracle."""
+    spec = synth.pan_1080p_120f()
+    sc = synth.Scene(spec)
+    p = W.wrls_params_default()
+    s = W.Stream(spec.width, spec.height, p)
+    st = O.OracleStream(spec.width, spec.height, oracle_params_from(p))
+    out = torch.empty(3, spec.height, spec.width, device="cuda")
+    worst = 0.0
+    for t in range(spec.frames):
+        f = sc.frame(t)
+        s.denoise(f["radiance"].cuda(), f["motion"].cuda(), out)
+        ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
+        e = rel_err(out.cpu().numpy(), ref)
+        worst = max(worst, e)
+        assert e <= REL_TOL, (t, e)
+    print("full-size worst rel err %.3g" % worst)
