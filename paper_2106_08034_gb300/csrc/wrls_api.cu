@@ -233,7 +233,7 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
   WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->cs),
                   "wrls_denoise_frame: update kernel launch");
   if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
-  WRLS_CHECK_CUDA(launch_blend(s->kp, next, out, s->cs), "wrls_denoise_frame: blend kernel launch");
+  WRLS_CHECK_CUDA(launch_blend(s->kp, s->blend_cfg, next, out, s->cs), "wrls_denoise_frame: blend kernel launch");
   if (ev) {
     WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
     s->t_pending++;

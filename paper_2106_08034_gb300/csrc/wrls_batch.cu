@@ -31,14 +31,16 @@ struct FrameWork {
   int pitch;
   int W, H;
   int reset;
-  int tiles_x;
-  int tile_begin;
+  int tiles_x;       // tiles per row (32 pixels wide, both phases)
+  int begin_update;  // first work item of this frame in the update list (32 x 8 tiles)
+  int begin_blend;   // first work item of this frame in the blend list (32 x TH tiles)
 };
 
 struct BatchHeader {
   int n;
-  int total_tiles;
-  int pad[2];
+  int total_update;
+  int total_blend;
+  int pad;
 };
 
 template <class SV> __device__ __forceinline__ SV make_view(void* base, float* scale, size_t ps, int pitch);
@@ -52,19 +54,22 @@ template <> __device__ __forceinline__ StateF16 make_view<StateF16>(void* base, 
   return StateF16{(__half*)base, scale, ps, pitch};
 }
 
-// Claim the next work item; returns its frame index in *frame and tile index in the frame.
+// Claim the next work item of a list; returns its tile index within its frame (or -1 when
+// the list is exhausted) and the frame in *frame.
+template <bool BLEND>
 __device__ __forceinline__ int next_item(const BatchHeader* __restrict__ hdr,
                                          const FrameWork* __restrict__ fw, int* counter,
                                          int* s_item, int* s_frame, int* frame) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const int t = atomicAdd(counter, 1);
+    const int total = BLEND ? hdr->total_blend : hdr->total_update;
     int f = -1;
-    if (t < hdr->total_tiles) {
-      int lo = 0, hi = hdr->n - 1;  // last frame with tile_begin <= t
+    if (t < total) {
+      int lo = 0, hi = hdr->n - 1;  // last frame whose list begins at or before t
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (fw[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+        if ((BLEND ? fw[mid].begin_blend : fw[mid].begin_update) <= t) lo = mid; else hi = mid - 1;
       }
       f = lo;
     }
@@ -73,7 +78,8 @@ __device__ __forceinline__ int next_item(const BatchHeader* __restrict__ hdr,
   }
   __syncthreads();
   *frame = *s_frame;
-  return *frame < 0 ? -1 : *s_item - fw[*frame].tile_begin;
+  if (*frame < 0) return -1;
+  return *s_item - (BLEND ? fw[*frame].begin_blend : fw[*frame].begin_update);
 }
 
 template <class SV>
@@ -83,7 +89,7 @@ __global__ void __launch_bounds__(kTileThreads)
   __shared__ int s_item, s_frame;
   for (;;) {
     int f;
-    const int lt = next_item(hdr, fw, counters + 0, &s_item, &s_frame, &f);
+    const int lt = next_item<false>(hdr, fw, counters + 0, &s_item, &s_frame, &f);
     if (lt < 0) break;
     const FrameWork& w = fw[f];
     const SV prev = make_view<SV>(w.prev_base, w.prev_scale, w.plane_stride, w.pitch);
@@ -93,41 +99,44 @@ __global__ void __launch_bounds__(kTileThreads)
   }
 }
 
-template <class SV>
-__global__ void __launch_bounds__(kTileThreads)
+template <class SV, int TH, int R, int MODE>
+__global__ void __launch_bounds__(kTW * TH / R)
     k_batch_blend(const BatchHeader* __restrict__ hdr, const FrameWork* __restrict__ fw, int* counters) {
-  __shared__ BlendSmem sm;
+  extern __shared__ float4 sm_blend[];
   __shared__ int s_item, s_frame;
   for (;;) {
     int f;
-    const int lt = next_item(hdr, fw, counters + 1, &s_item, &s_frame, &f);
+    const int lt = next_item<true>(hdr, fw, counters + 1, &s_item, &s_frame, &f);
     if (lt < 0) break;
     const FrameWork& w = fw[f];
     const SV cur = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
-    blend_tile(sm, w.kp, w.W, w.H, cur, w.out, (lt % w.tiles_x) * kTW, (lt / w.tiles_x) * kTH);
+    blend_tile<SV, TH, R, MODE>(sm_blend, w.kp, w.W, w.H, cur, w.out, (lt % w.tiles_x) * kTW,
+                                (lt / w.tiles_x) * TH);
   }
 }
 
-template <class SV>
-static cudaError_t persistent_grid(int* g_update, int* g_blend) {
-  int dev = 0, sms = 0, a = 0, b = 0;
+static int sm_count() {
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_update<SV>, kTileThreads, 0);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_blend<SV>, kTileThreads, 0);
-  if (e != cudaSuccess) return e;
-  *g_update = sms * (a > 0 ? a : 1);
-  *g_blend = sms * (b > 0 ? b : 1);
-  return cudaSuccess;
+  return sms > 0 ? sms : 1;
 }
 
-template <class SV>
-static cudaError_t capture_tick(cudaStream_t cap, const void* h_table, void* d_table, size_t bytes,
-                                int* d_counters, cudaGraphExec_t* exec) {
-  int gu = 0, gb = 0;
-  cudaError_t e = persistent_grid<SV>(&gu, &gb);
+template <class SV, int TH, int R, int MODE>
+static cudaError_t capture_tick_cfg(cudaStream_t cap, const void* h_table, void* d_table, size_t bytes,
+                                    int* d_counters, cudaGraphExec_t* exec) {
+  constexpr int sbytes = BlendGeom<TH>::kSmemBytes;
+  constexpr int nt = kTW * TH / R;
+  cudaError_t e = cudaFuncSetAttribute(k_batch_blend<SV, TH, R, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sbytes);
   if (e != cudaSuccess) return e;
+  int ou = 0, ob = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_batch_update<SV>, kTileThreads, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_batch_blend<SV, TH, R, MODE>, nt, sbytes);
+  if (e != cudaSuccess) return e;
+  const int sms = sm_count();
+  const int gu = sms * (ou > 0 ? ou : 1), gb = sms * (ob > 0 ? ob : 1);
   const BatchHeader* hdr = (const BatchHeader*)d_table;
   const FrameWork* fw = (const FrameWork*)((char*)d_table + sizeof(BatchHeader));
   cudaGraph_t g = nullptr;
@@ -136,12 +145,39 @@ static cudaError_t capture_tick(cudaStream_t cap, const void* h_table, void* d_t
   cudaMemcpyAsync(d_table, h_table, bytes, cudaMemcpyHostToDevice, cap);
   cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), cap);
   k_batch_update<SV><<<gu, kTileThreads, 0, cap>>>(hdr, fw, d_counters);
-  k_batch_blend<SV><<<gb, kTileThreads, 0, cap>>>(hdr, fw, d_counters);
+  k_batch_blend<SV, TH, R, MODE><<<gb, nt, sbytes, cap>>>(hdr, fw, d_counters);
   e = cudaStreamEndCapture(cap, &g);
   if (e != cudaSuccess) return e;
   e = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
   return e;
+}
+
+template <class SV, int MODE>
+static cudaError_t capture_tick_mode(int cfg, cudaStream_t cap, const void* h, void* d, size_t bytes,
+                                     int* c, cudaGraphExec_t* exec) {
+  switch (cfg) {
+    case 0: return capture_tick_cfg<SV, 16, 4, MODE>(cap, h, d, bytes, c, exec);
+    case 1: return capture_tick_cfg<SV, 8, 4, MODE>(cap, h, d, bytes, c, exec);
+    case 2: return capture_tick_cfg<SV, 16, 2, MODE>(cap, h, d, bytes, c, exec);
+    case 3: return capture_tick_cfg<SV, 32, 4, MODE>(cap, h, d, bytes, c, exec);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class SV>
+static cudaError_t capture_tick(int mode, int cfg, cudaStream_t cap, const void* h, void* d,
+                                size_t bytes, int* c, cudaGraphExec_t* exec) {
+  return mode == 0 ? capture_tick_mode<SV, 0>(cfg, cap, h, d, bytes, c, exec)
+                   : capture_tick_mode<SV, 1>(cfg, cap, h, d, bytes, c, exec);
+}
+
+static int blend_rows(int cfg) {
+  switch (cfg) {
+    case 1: return 8;
+    case 3: return 32;
+    default: return 16;
+  }
 }
 
 }  // namespace wrls
@@ -157,15 +193,19 @@ struct wrls_batch {
   int* d_counters = nullptr;
   void* h_table[2] = {nullptr, nullptr};
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  cudaGraphExec_t exec[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  // graph per (pinned slot, precision, blend mode, blend tile configuration)
+  cudaGraphExec_t exec[2][3][2][kBlendConfigs] = {};
   int slot = 0;
+  int blend_cfg = 0;
   int device = 0;
 };
 
 static void batch_free(wrls_batch* b) {
   for (int s = 0; s < 2; ++s) {
     for (int p = 0; p < 3; ++p)
-      if (b->exec[s][p]) cudaGraphExecDestroy(b->exec[s][p]);
+      for (int m = 0; m < 2; ++m)
+        for (int c = 0; c < kBlendConfigs; ++c)
+          if (b->exec[s][p][m][c]) cudaGraphExecDestroy(b->exec[s][p][m][c]);
     if (b->ev[s]) cudaEventDestroy(b->ev[s]);
     if (b->h_table[s]) cudaFreeHost(b->h_table[s]);
   }
@@ -220,6 +260,7 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
     return WRLS_ERR_INVALID_ARG;
   }
   const int prec = frames[0].stream ? frames[0].stream->prm.state_precision : -1;
+  const int mode = frames[0].stream ? frames[0].stream->prm.blend_mode : -1;
   for (int i = 0; i < n; ++i) {
     const wrls_frame_io& io = frames[i];
     if (!io.stream || !io.radiance || !io.motion || !io.out) {
@@ -230,8 +271,8 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
       set_error("wrls_batch_tick: frame %d buffers must be 4-byte aligned", i);
       return WRLS_ERR_INVALID_ARG;
     }
-    if (io.stream->prm.state_precision != prec) {
-      set_error("wrls_batch_tick: all streams of a tick must share one state precision");
+    if (io.stream->prm.state_precision != prec || io.stream->prm.blend_mode != mode) {
+      set_error("wrls_batch_tick: all streams of a tick must share one state precision and blend mode");
       return WRLS_ERR_INVALID_ARG;
     }
     for (int k = 0; k < i; ++k)
@@ -245,7 +286,9 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
   if (e != cudaSuccess) { set_error("wrls_batch_tick: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
   BatchHeader* hdr = (BatchHeader*)b->h_table[slot];
   FrameWork* fw = (FrameWork*)((char*)b->h_table[slot] + sizeof(BatchHeader));
-  int tiles = 0;
+  const int cfg = b->blend_cfg;
+  const int th_b = blend_rows(cfg);
+  int tiles_u = 0, tiles_b = 0;
   for (int i = 0; i < n; ++i) {
     wrls_stream* s = frames[i].stream;
     const StateDesc& pv = s->state[s->cur];
@@ -265,26 +308,31 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
     w.H = s->H;
     w.reset = s->need_reset ? 1 : 0;
     w.tiles_x = (s->W + kTW - 1) / kTW;
-    w.tile_begin = tiles;
-    tiles += w.tiles_x * ((s->H + kTH - 1) / kTH);
+    w.begin_update = tiles_u;
+    w.begin_blend = tiles_b;
+    tiles_u += w.tiles_x * ((s->H + kTH - 1) / kTH);
+    tiles_b += w.tiles_x * ((s->H + th_b - 1) / th_b);
   }
   hdr->n = n;
-  hdr->total_tiles = tiles;
-  if (!b->exec[slot][prec]) {
+  hdr->total_update = tiles_u;
+  hdr->total_blend = tiles_b;
+  cudaGraphExec_t& ex = b->exec[slot][prec][mode][cfg];
+  if (!ex) {
     const size_t bytes = b->table_bytes;
+    void* h = b->h_table[slot];
     switch (prec) {
-      case 0: e = capture_tick<StateF32>(b->cap, b->h_table[slot], b->d_table, bytes, b->d_counters, &b->exec[slot][prec]); break;
-      case 1: e = capture_tick<StateBF16>(b->cap, b->h_table[slot], b->d_table, bytes, b->d_counters, &b->exec[slot][prec]); break;
-      default: e = capture_tick<StateF16>(b->cap, b->h_table[slot], b->d_table, bytes, b->d_counters, &b->exec[slot][prec]); break;
+      case 0: e = capture_tick<StateF32>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+      case 1: e = capture_tick<StateBF16>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+      default: e = capture_tick<StateF16>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
     }
     if (e != cudaSuccess) {
       cudaGetLastError();
-      b->exec[slot][prec] = nullptr;
+      ex = nullptr;
       set_error("wrls_batch_tick: graph capture failed: %s", cudaGetErrorString(e));
       return WRLS_ERR_CUDA;
     }
   }
-  e = cudaGraphLaunch(b->exec[slot][prec], b->cs);
+  e = cudaGraphLaunch(ex, b->cs);
   if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], b->cs);
   if (e != cudaSuccess) { set_error("wrls_batch_tick: graph launch: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
   for (int i = 0; i < n; ++i) {

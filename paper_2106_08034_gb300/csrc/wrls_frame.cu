@@ -1,4 +1,4 @@
-// Single-frame kernels of the wRLS denoiser: one CTA per 32 x 8 tile.
+// Single-frame kernels of the wRLS denoiser, one CTA per tile:
 //   k_update     : reprojection + Eq. 12 + Eq. 13 + Eq. 8/14/9/11 (tile body update_tile)
 //   k_blend      : 5x5 spatio-temporal blend of Sec. 5.3 (tile body blend_tile)
 //   k_read_state : decode a state copy to 25 binary32 planes
@@ -15,11 +15,11 @@ __global__ void __launch_bounds__(kTileThreads)
   update_tile(sm, kp, W, H, reset != 0, prev, next, rad, mot, blockIdx.x * kTW, blockIdx.y * kTH);
 }
 
-template <class SV>
-__global__ void __launch_bounds__(kTileThreads)
+template <class SV, int TH, int R, int MODE>
+__global__ void __launch_bounds__(kTW * TH / R)
     k_blend(const KParams kp, const int W, const int H, const SV cur, float* __restrict__ out) {
-  __shared__ BlendSmem sm;
-  blend_tile(sm, kp, W, H, cur, out, blockIdx.x * kTW, blockIdx.y * kTH);
+  extern __shared__ float4 sm_blend[];
+  blend_tile<SV, TH, R, MODE>(sm_blend, kp, W, H, cur, out, blockIdx.x * kTW, blockIdx.y * TH);
 }
 
 template <class SV>
@@ -33,11 +33,9 @@ __global__ void k_read_state(const int W, const int H, const SV cur, float* __re
   for (int p = 0; p < kNState; ++p) dst[p * npix + j] = v[p];
 }
 
-static dim3 tile_grid(int W, int H) { return dim3((W + kTW - 1) / kTW, (H + kTH - 1) / kTH); }
-
 cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
                           const float* rad, const float* mot, cudaStream_t cs) {
-  const dim3 grid = tile_grid(prev.W, prev.H);
+  const dim3 grid((prev.W + kTW - 1) / kTW, (prev.H + kTH - 1) / kTH);
   const int rs = reset ? 1 : 0;
   switch (prev.precision) {
     case 0: k_update<<<grid, kTileThreads, 0, cs>>>(kp, prev.W, prev.H, rs, prev.f32(), next.f32(), rad, mot); break;
@@ -48,15 +46,48 @@ cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateD
   return cudaGetLastError();
 }
 
-cudaError_t launch_blend(const KParams& kp, const StateDesc& cur, float* out, cudaStream_t cs) {
-  const dim3 grid = tile_grid(cur.W, cur.H);
-  switch (cur.precision) {
-    case 0: k_blend<<<grid, kTileThreads, 0, cs>>>(kp, cur.W, cur.H, cur.f32(), out); break;
-    case 1: k_blend<<<grid, kTileThreads, 0, cs>>>(kp, cur.W, cur.H, cur.bf16(), out); break;
-    case 2: k_blend<<<grid, kTileThreads, 0, cs>>>(kp, cur.W, cur.H, cur.f16(), out); break;
-    default: return cudaErrorInvalidValue;
+template <class SV, int TH, int R, int MODE>
+static cudaError_t launch_blend_cfg(const KParams& kp, const SV& cur, int W, int H, float* out,
+                                    cudaStream_t cs) {
+  constexpr int bytes = BlendGeom<TH>::kSmemBytes;
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_blend<SV, TH, R, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
   }
+  const dim3 grid((W + kTW - 1) / kTW, (H + TH - 1) / TH);
+  k_blend<SV, TH, R, MODE><<<grid, kTW * TH / R, bytes, cs>>>(kp, W, H, cur, out);
   return cudaGetLastError();
+}
+
+template <class SV, int MODE>
+static cudaError_t launch_blend_mode(const KParams& kp, int cfg, const SV& cur, int W, int H,
+                                     float* out, cudaStream_t cs) {
+  switch (cfg) {
+    case 0: return launch_blend_cfg<SV, 16, 4, MODE>(kp, cur, W, H, out, cs);
+    case 1: return launch_blend_cfg<SV, 8, 4, MODE>(kp, cur, W, H, out, cs);
+    case 2: return launch_blend_cfg<SV, 16, 2, MODE>(kp, cur, W, H, out, cs);
+    case 3: return launch_blend_cfg<SV, 32, 4, MODE>(kp, cur, W, H, out, cs);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class SV>
+static cudaError_t launch_blend_sv(const KParams& kp, int cfg, const SV& cur, int W, int H,
+                                   float* out, cudaStream_t cs) {
+  return kp.blend_mode == 0 ? launch_blend_mode<SV, 0>(kp, cfg, cur, W, H, out, cs)
+                            : launch_blend_mode<SV, 1>(kp, cfg, cur, W, H, out, cs);
+}
+
+cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs) {
+  switch (cur.precision) {
+    case 0: return launch_blend_sv(kp, cfg, cur.f32(), cur.W, cur.H, out, cs);
+    case 1: return launch_blend_sv(kp, cfg, cur.bf16(), cur.W, cur.H, out, cs);
+    case 2: return launch_blend_sv(kp, cfg, cur.f16(), cur.W, cur.H, out, cs);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs) {

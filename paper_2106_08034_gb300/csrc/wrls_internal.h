@@ -33,7 +33,10 @@ bool make_kparams(const wrls_params& p, KParams* kp, const char** why);
 
 cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
                           const float* rad, const float* mot, cudaStream_t cs);
-cudaError_t launch_blend(const KParams& kp, const StateDesc& cur, float* out, cudaStream_t cs);
+// Blend tile configurations (tile rows TH, output rows per thread R):
+// 0: 16 x 4 (default), 1: 8 x 4, 2: 16 x 2, 3: 32 x 4.
+constexpr int kBlendConfigs = 4;
+cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs);
 cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs);
 
 void set_error(const char* fmt, ...);
@@ -55,6 +58,7 @@ struct wrls_stream {
   int device = 0;
   uint64_t frames = 0;
   float* staging = nullptr;     // device I/O buffers of wrls_denoise_frame_host
+  int blend_cfg = 0;            // blend tile configuration
   // kernel tracing
   static constexpr int kTimingCap = 8192;
   cudaEvent_t* tev = nullptr;   // 3 events per recorded frame

@@ -6,11 +6,11 @@
 //  blend_tile  : per pixel, the spatio-temporal blend of Sec. 5.3 over the (2r+1)^2 window
 //                of models after the update; writes the denoised colour.
 //
-// Tiles are 32 x 8 pixels (one warp per tile row: each plane access of a warp is one
+// Update tiles are 32 x 8 pixels (one warp per tile row: each plane access of a warp is one
 // 128-byte row segment). The 3x3 neighbourhood of the radiance (clamp of Eq. 12) and the
 // 5x5 neighbourhood of beta/z (blend) are staged in shared memory with their halos;
 // out-of-image halo pixels are marked (NaN radiance, negative 1/|z|) and skipped.
-// Both bodies start and end with a CTA barrier so a CTA may run them back to back.
+// Both bodies start with a CTA barrier so a CTA may run tiles back to back.
 #pragma once
 #include "wrls_device.cuh"
 
@@ -22,13 +22,6 @@ constexpr int kTileThreads = kTW * kTH;
 
 struct UpdateSmem {
   float rad[3][kTH + 2][kTW + 2];
-};
-
-struct BlendSmem {
-  static constexpr int SW = kTW + 2 * kMaxRadius, SH = kTH + 2 * kMaxRadius;
-  float b[12][SH][SW];
-  float z[3][SH][SW];
-  float r[SH][SW];
 };
 
 template <class SV>
@@ -87,76 +80,139 @@ __device__ __forceinline__ void update_tile(UpdateSmem& sm, const KParams& kp, c
   }
 }
 
-template <class SV>
-__device__ __forceinline__ void blend_tile(BlendSmem& sm, const KParams& kp, const int W,
-                                           const int H, const SV& cur, float* __restrict__ out,
-                                           const int bx0, const int by0) {
-  constexpr int R = kMaxRadius;
-  constexpr int SW = BlendSmem::SW, SH = BlendSmem::SH;
-  const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
-  __syncthreads();
-  for (int i = threadIdx.x; i < SH * SW; i += kTileThreads) {
-    const int ly = i / SW, lx = i % SW;
-    const int gx = bx0 - R + lx, gy = by0 - R + ly;
+// ---- spatio-temporal blend (Sec. 5.3) -------------------------------------------------------
+//
+// A blend tile is 32 x TH output pixels; each thread produces R vertically adjacent outputs of
+// one column, so a neighbour read from shared memory serves up to 5 of the thread's outputs.
+// Shared memory holds the (32+4) x (TH+4) window of the models after the update, one 20-float
+// record per pixel: beta[12], z[3], 1/(|z|+eps) (negative = outside the image), 4 pad floats.
+// The 80-byte record stride makes the four 128-bit loads of a warp conflict-free.
+constexpr int kBlendRec = 20;
+constexpr int kBlendSW = kTW + 2 * kMaxRadius;
+
+template <int TH>
+struct BlendGeom {
+  static constexpr int SH = TH + 2 * kMaxRadius;
+  static constexpr int kSmemBytes = SH * kBlendSW * kBlendRec * 4;
+};
+
+// Fill the shared window of the blend tile at (bx0, by0) from the state copy `cur`.
+template <class SV, int TH, int NT>
+__device__ __forceinline__ void blend_fill(float4* __restrict__ sm, const KParams& kp, const int W,
+                                           const int H, const SV& cur, const int bx0, const int by0) {
+  constexpr int R0 = kMaxRadius, SH = BlendGeom<TH>::SH;
+#pragma unroll 2
+  for (int i = threadIdx.x; i < SH * kBlendSW; i += NT) {
+    const int ly = i / kBlendSW, lx = i % kBlendSW;
+    const int gx = bx0 - R0 + lx, gy = by0 - R0 + ly;
+    float4* rec = sm + i * (kBlendRec / 4);
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
       float b[12], z[3];
       cur.load_beta_z((size_t)gy * cur.pitch + gx, b, z);
-#pragma unroll
-      for (int p = 0; p < 12; ++p) sm.b[p][ly][lx] = b[p];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) sm.z[c][ly][lx] = z[c];
-      sm.r[ly][lx] = 1.0f / (sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]) + kp.eps);
+      const float r = 1.0f / (sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]) + kp.eps);
+      rec[0] = make_float4(b[0], b[1], b[2], b[3]);
+      rec[1] = make_float4(b[4], b[5], b[6], b[7]);
+      rec[2] = make_float4(b[8], b[9], b[10], b[11]);
+      rec[3] = make_float4(z[0], z[1], z[2], r);
     } else {
-      sm.r[ly][lx] = -1.0f;
+      rec[3] = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     }
   }
-  __syncthreads();
-  const int x = bx0 + tx, y = by0 + ty;
-  if (x < W && y < H) {
-    const int cy = ty + R, cx = tx + R;
-    const float zi0 = sm.z[0][cy][cx], zi1 = sm.z[1][cy][cx], zi2 = sm.z[2][cy][cx];
-    const float ri = sm.r[cy][cx];
-    const bool feat = kp.feature_mode == 0;
-    const float p1 = feat ? zi0 : 0.0f, p2 = feat ? zi1 : 0.0f, p3 = feat ? zi2 : 0.0f;
-    const int r = kp.radius;
-    float acc[12];
+}
+
+// Blend the outputs of the tile whose window is in `sm`. MODE 0: out_i = sum_k b_ik (p_i .
+// beta_k) / sum_k b_ik (neighbours' models predict pixel i); MODE 1: sum_k b_ik (p_k . beta_k)
+// / sum_k b_ik. b_ik = exp(-|dxy|^2 / (2 sigma_s^2)) exp(-d_z(i,k)^2 / h_s^2) with d_z the
+// Eq. 13 distance of the features; 1 / (min(|z_i|, |z_k|) + eps) = max(r_i, r_k).
+template <int TH, int R, int MODE>
+__device__ __forceinline__ void blend_compute(const float4* __restrict__ sm, const KParams& kp,
+                                              const int W, const int H, float* __restrict__ out,
+                                              const int bx0, const int by0) {
+  constexpr int R0 = kMaxRadius;
+  constexpr int RW = 2 * R0 + 1;
+  const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
+  const int x = bx0 + tx, y0 = by0 + ty * R;
+  const int rad = kp.radius;
+  const bool feat = kp.feature_mode == 0;
+  float zi[R][3], ri[R], den[R];
+  float acc[R][MODE == 0 ? 12 : 3];
 #pragma unroll
-    for (int p = 0; p < 12; ++p) acc[p] = 0.0f;
-    float num0 = 0.0f, num1 = 0.0f, num2 = 0.0f, den = 0.0f;
-    for (int dy = -r; dy <= r; ++dy) {
-      for (int dx = -r; dx <= r; ++dx) {
-        const int ky = cy + dy, kx = cx + dx;
-        const float rk = sm.r[ky][kx];
-        if (rk < 0.0f) continue;
-        const float e0 = zi0 - sm.z[0][ky][kx], e1 = zi1 - sm.z[1][ky][kx], e2 = zi2 - sm.z[2][ky][kx];
-        const float rm = fmaxf(ri, rk);  // = 1 / (min(|z_i|, |z_k|) + eps)
+  for (int i = 0; i < R; ++i) {
+    const float4 q = sm[((ty * R + i + R0) * kBlendSW + tx + R0) * (kBlendRec / 4) + 3];
+    zi[i][0] = q.x; zi[i][1] = q.y; zi[i][2] = q.z; ri[i] = q.w;
+    den[i] = 0.0f;
+#pragma unroll
+    for (int p = 0; p < (MODE == 0 ? 12 : 3); ++p) acc[i][p] = 0.0f;
+  }
+#pragma unroll
+  for (int kr = 0; kr < R + 2 * R0; ++kr) {
+#pragma unroll
+    for (int dx = -R0; dx <= R0; ++dx) {
+      if (dx < -rad || dx > rad) continue;
+      const float4* rec = sm + ((ty * R + kr) * kBlendSW + tx + R0 + dx) * (kBlendRec / 4);
+      const float4 q3 = rec[3];
+      if (q3.w < 0.0f) continue;
+      const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2];
+      float pk0 = 0.0f, pk1 = 0.0f, pk2 = 0.0f;
+      if (MODE == 1) {
+        const float a1 = feat ? q3.x : 0.0f, a2 = feat ? q3.y : 0.0f, a3 = feat ? q3.z : 0.0f;
+        pk0 = q0.x + q0.y * a1 + q0.z * a2 + q0.w * a3;
+        pk1 = q1.x + q1.y * a1 + q1.z * a2 + q1.w * a3;
+        pk2 = q2.x + q2.y * a1 + q2.z * a2 + q2.w * a3;
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int dy = kr - R0 - i;
+        if (dy < -R0 || dy > R0) continue;
+        if (dy < -rad || dy > rad) continue;
+        const float e0 = zi[i][0] - q3.x, e1 = zi[i][1] - q3.y, e2 = zi[i][2] - q3.z;
+        const float rm = fmaxf(ri[i], q3.w);
         const float d2 = (e0 * e0 + e1 * e1 + e2 * e2) * (rm * rm);
-        const float b = ex2_approx(kp.spatial[(dy + R) * (2 * R + 1) + (dx + R)] - d2 * kp.range_k);
-        den += b;
-        if (kp.blend_mode == 0) {
-#pragma unroll
-          for (int p = 0; p < 12; ++p) acc[p] += b * sm.b[p][ky][kx];
+        const float b = ex2_approx(kp.spatial[(dy + R0) * RW + (dx + R0)] - d2 * kp.range_k);
+        den[i] += b;
+        if (MODE == 0) {
+          acc[i][0] += b * q0.x; acc[i][1] += b * q0.y; acc[i][2] += b * q0.z; acc[i][3] += b * q0.w;
+          acc[i][4] += b * q1.x; acc[i][5] += b * q1.y; acc[i][6] += b * q1.z; acc[i][7] += b * q1.w;
+          acc[i][8] += b * q2.x; acc[i][9] += b * q2.y; acc[i][10] += b * q2.z; acc[i][11] += b * q2.w;
         } else {
-          const float q1 = feat ? sm.z[0][ky][kx] : 0.0f, q2 = feat ? sm.z[1][ky][kx] : 0.0f,
-                      q3 = feat ? sm.z[2][ky][kx] : 0.0f;
-          num0 += b * (sm.b[0][ky][kx] + sm.b[1][ky][kx] * q1 + sm.b[2][ky][kx] * q2 + sm.b[3][ky][kx] * q3);
-          num1 += b * (sm.b[4][ky][kx] + sm.b[5][ky][kx] * q1 + sm.b[6][ky][kx] * q2 + sm.b[7][ky][kx] * q3);
-          num2 += b * (sm.b[8][ky][kx] + sm.b[9][ky][kx] * q1 + sm.b[10][ky][kx] * q2 + sm.b[11][ky][kx] * q3);
+          acc[i][0] += b * pk0; acc[i][1] += b * pk1; acc[i][2] += b * pk2;
         }
       }
     }
-    if (kp.blend_mode == 0) {
-      // sum_k b_k (p_i . beta_k) = p_i . sum_k b_k beta_k
-      num0 = acc[0] + acc[1] * p1 + acc[2] * p2 + acc[3] * p3;
-      num1 = acc[4] + acc[5] * p1 + acc[6] * p2 + acc[7] * p3;
-      num2 = acc[8] + acc[9] * p1 + acc[10] * p2 + acc[11] * p3;
-    }
-    const float inv = 1.0f / den;
-    const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
-    out[j] = num0 * inv;
-    out[npix + j] = num1 * inv;
-    out[2 * npix + j] = num2 * inv;
   }
+  if (x >= W) return;
+  const size_t npix = (size_t)W * H;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int y = y0 + i;
+    if (y >= H) break;
+    float o0, o1, o2;
+    if (MODE == 0) {
+      // sum_k b_k (p_i . beta_k) = p_i . sum_k b_k beta_k, p_i = [1, z_i]
+      const float p1 = feat ? zi[i][0] : 0.0f, p2 = feat ? zi[i][1] : 0.0f, p3 = feat ? zi[i][2] : 0.0f;
+      o0 = acc[i][0] + acc[i][1] * p1 + acc[i][2] * p2 + acc[i][3] * p3;
+      o1 = acc[i][4] + acc[i][5] * p1 + acc[i][6] * p2 + acc[i][7] * p3;
+      o2 = acc[i][8] + acc[i][9] * p1 + acc[i][10] * p2 + acc[i][11] * p3;
+    } else {
+      o0 = acc[i][0]; o1 = acc[i][1]; o2 = acc[i][2];
+    }
+    const float inv = 1.0f / den[i];
+    const size_t j = (size_t)y * W + x;
+    out[j] = o0 * inv;
+    out[npix + j] = o1 * inv;
+    out[2 * npix + j] = o2 * inv;
+  }
+}
+
+// Whole blend tile: barrier, fill, barrier, compute (a CTA may run tiles back to back).
+template <class SV, int TH, int R, int MODE>
+__device__ __forceinline__ void blend_tile(float4* __restrict__ sm, const KParams& kp, const int W,
+                                           const int H, const SV& cur, float* __restrict__ out,
+                                           const int bx0, const int by0) {
+  __syncthreads();
+  blend_fill<SV, TH, kTW * TH / R>(sm, kp, W, H, cur, bx0, by0);
+  __syncthreads();
+  blend_compute<TH, R, MODE>(sm, kp, W, H, out, bx0, by0);
 }
 
 }  // namespace wrls
