@@ -238,6 +238,7 @@ def run_wrls(args):
         for _ in range(args.warmup):
             step()
     cs.synchronize()
+    blend_times, blend_cfg = W.wrls_stream_autotune(s.handle, out, reps=5)
     W.wrls_stream_enable_timing(s.handle, True)
 
     clocks = ClockSampler(smi_device_id(torch, dev, local))
@@ -310,6 +311,7 @@ def run_wrls(args):
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "bytes_per_px": BYTES_UPDATE_F32,
                 "kernel_ms": {"update": round(upd_per, 5), "blend": round(bl_per, 5)},
+                "blend_autotune_ms": [round(t, 5) for t in blend_times], "blend_config": blend_cfg,
                 "path": {"bytes_per_px": BYTES_PATH_F32,
                          "achieved": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9, 1),
                          "frac": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9 / peak, 4)}}

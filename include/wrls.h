@@ -144,6 +144,26 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst);
 uint64_t wrls_stream_frames(const wrls_stream* s);
 
 /*
+ * Autotuner of the blend kernel's tile shape: times every blend tile configuration (output
+ * tile rows x output rows per thread: 16x4, 8x4, 16x2, 32x4) on the stream's current state,
+ * `reps` launches each (>= 1), on the stream's CUDA stream, and keeps the fastest for later
+ * frames. All configurations give bitwise identical outputs. Requires one denoised frame;
+ * `out` (device, 3 x H x W) is overwritten and ends up holding the current frame's output.
+ * times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per launch and
+ * *chosen (optional) the selected configuration. Synchronises the stream.
+ */
+#define WRLS_BLEND_CONFIGS 4
+wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen);
+
+/* Select a blend tile configuration (0..WRLS_BLEND_CONFIGS-1) directly. */
+wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config);
+
+/* Synchronise the stream's CUDA stream and report device-side failures of the frames
+ * since the last check: WRLS_ERR_TIMEOUT if a kernel's bounded wait for its own bulk
+ * copy gave up (that frame's output and state are then unreliable). Clears the record. */
+wrls_status wrls_stream_check(wrls_stream* s);
+
+/*
  * Kernel tracing. With timing enabled, every frame records CUDA events on the stream's
  * CUDA stream before and after each of its kernels (temporal update, spatial blend).
  * wrls_stream_kernel_times synchronises the recorded events, adds their durations to
@@ -185,7 +205,8 @@ wrls_status wrls_batch_create(int max_streams, wrls_batch** out);
 wrls_status wrls_batch_set_cuda_stream(wrls_batch* b, void* cuda_stream);
 
 /* Run one tick over n frames (1 <= n <= max_streams; each stream at most once, all
- * streams of the same state precision and parameters). Asynchronous. */
+ * streams of the same state precision and blend mode). The blend tile configuration is the
+ * one tuned for the largest stream of the tick. Asynchronous. */
 wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n);
 
 /* Synchronise and free. NULL is a no-op. */

@@ -1,9 +1,12 @@
 // C ABI of libwrls.so (declared in include/wrls.h): parameter handling, stream objects
 // owning the per-pixel state, and the per-frame entry points.
 #include <math.h>
+#include <stdlib.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <cudaTypedefs.h>
 
 #include <new>
 
@@ -39,6 +42,48 @@ size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_
   return round_up(bytes, 256);
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+bool encode_stage_maps(StateDesc& d, const char** why) {
+  d.stage_ok = false;
+  memset(&d.maps, 0, sizeof(d.maps));
+  if (d.pitch < kStageW || d.H < kStageH) return true;  // smaller images read taps from global memory
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) { *why = "cuTensorMapEncodeTiled is not available from the driver"; return false; }
+  const bool f32 = d.precision == 0;
+  const cuuint64_t elem = f32 ? 4 : 2;
+  const cuuint64_t dims[3] = {(cuuint64_t)d.pitch, (cuuint64_t)d.H, (cuuint64_t)kNState};
+  const cuuint64_t strides[2] = {(cuuint64_t)d.pitch * elem, (cuuint64_t)d.plane_stride * elem};
+  const cuuint32_t box[3] = {(cuuint32_t)kStageW, (cuuint32_t)kStageH, (cuuint32_t)kNState};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(&d.maps.planes, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
+                   d.base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for the state planes"; return false; }
+  if (!f32) {
+    const cuuint64_t dims2[2] = {(cuuint64_t)d.pitch, (cuuint64_t)d.H};
+    const cuuint64_t strides2[1] = {(cuuint64_t)d.pitch * 4};
+    const cuuint32_t box2[2] = {(cuuint32_t)kStageW, (cuuint32_t)kStageH};
+    r = enc(&d.maps.scale, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.scale, dims2, strides2, box2, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for the P-scale plane"; return false; }
+  }
+  d.stage_ok = true;
+  return true;
+}
+
 bool make_kparams(const wrls_params& p, KParams* kp, const char** why) {
   if (p.struct_size != sizeof(wrls_params)) { *why = "params.struct_size != sizeof(wrls_params)"; return false; }
   if (!(p.lambda > 0.0f && p.lambda <= 1.0f)) { *why = "lambda must be in (0, 1]"; return false; }
@@ -64,10 +109,13 @@ bool make_kparams(const wrls_params& p, KParams* kp, const char** why) {
   kp->p0_delta = p.p0_delta;
   kp->p_trace_max = p.p_trace_max;
   kp->range_k = (float)(log2e / ((double)p.h_s * (double)p.h_s));
+  // Offsets beyond the window radius get -inf: their blend weight is exactly 0.
   for (int dy = -kMaxRadius; dy <= kMaxRadius; ++dy)
     for (int dx = -kMaxRadius; dx <= kMaxRadius; ++dx)
       kp->spatial[(dy + kMaxRadius) * (2 * kMaxRadius + 1) + dx + kMaxRadius] =
-          (float)(-(double)(dx * dx + dy * dy) / (2.0 * (double)p.sigma_s * (double)p.sigma_s) * log2e);
+          (abs(dx) > p.radius || abs(dy) > p.radius)
+              ? -INFINITY
+              : (float)(-(double)(dx * dx + dy * dy) / (2.0 * (double)p.sigma_s * (double)p.sigma_s) * log2e);
   kp->radius = p.radius;
   kp->weight_mode = p.weight_mode;
   kp->clamp_mode = p.clamp_mode;
@@ -171,14 +219,23 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
   s->prm = *p;
   s->kp = kp;
   cudaGetDevice(&s->device);
-  cudaError_t e = cudaMalloc(&s->mem, 2 * copy);
+  cudaError_t e = cudaMalloc(&s->mem, 2 * copy + 256);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error("wrls_stream_create: cudaMalloc(%zu) failed: %s", 2 * copy, cudaGetErrorString(e));
+    set_error("wrls_stream_create: cudaMalloc(%zu) failed: %s", 2 * copy + 256, cudaGetErrorString(e));
     delete s;
     return e == cudaErrorMemoryAllocation ? WRLS_ERR_OOM : WRLS_ERR_CUDA;
   }
-  s->mem_bytes = 2 * copy;
+  s->mem_bytes = 2 * copy + 256;
+  s->err = (int*)((char*)s->mem + 2 * copy);
+  e = cudaMemset(s->err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(s->mem);
+    set_error("wrls_stream_create: cudaMemset failed: %s", cudaGetErrorString(e));
+    delete s;
+    return WRLS_ERR_CUDA;
+  }
   for (int i = 0; i < 2; ++i) {
     StateDesc& d = s->state[i];
     d.base = (char*)s->mem + i * copy;
@@ -188,6 +245,12 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
     d.H = height;
     d.pitch = pitch;
     d.plane_stride = ps;
+    if (!encode_stage_maps(d, &why)) {
+      cudaFree(s->mem);
+      set_error("wrls_stream_create: %s", why);
+      delete s;
+      return WRLS_ERR_CUDA;
+    }
   }
   *out = s;
   return WRLS_OK;
@@ -230,7 +293,7 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
     ev = s->tev + 3 * s->t_pending;
     WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
   }
-  WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->cs),
+  WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs),
                   "wrls_denoise_frame: update kernel launch");
   if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
   WRLS_CHECK_CUDA(launch_blend(s->kp, s->blend_cfg, next, out, s->cs), "wrls_denoise_frame: blend kernel launch");
@@ -306,6 +369,64 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst) {
 }
 
 uint64_t wrls_stream_frames(const wrls_stream* s) { return s ? s->frames : 0; }
+
+wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config) {
+  if (!s || config < 0 || config >= kBlendConfigs) {
+    set_error("wrls_stream_set_blend_config: bad stream or configuration %d", config);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  s->blend_cfg = config;
+  return WRLS_OK;
+}
+
+wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen) {
+  if (!s || !out || reps < 1) { set_error("wrls_stream_autotune: bad argument"); return WRLS_ERR_INVALID_ARG; }
+  if (!s->has_frame) { set_error("wrls_stream_autotune: no frame denoised yet"); return WRLS_ERR_STATE; }
+  const StateDesc& cur = s->state[s->cur];
+  cudaEvent_t e0, e1;
+  WRLS_CHECK_CUDA(cudaEventCreate(&e0), "wrls_stream_autotune: event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    set_error("wrls_stream_autotune: event");
+    return WRLS_ERR_CUDA;
+  }
+  int best = 0;
+  float best_ms = 0.0f;
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < kBlendConfigs && e == cudaSuccess; ++c) {
+    e = launch_blend(s->kp, c, cur, out, s->cs);  // warm-up (and first-use setup)
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s->cs);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_blend(s->kp, c, cur, out, s->cs);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s->cs);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (times_ms) times_ms[c] = ms;
+    if (c == 0 || ms < best_ms) { best = c; best_ms = ms; }
+  }
+  if (e == cudaSuccess) e = launch_blend(s->kp, best, cur, out, s->cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) { set_error("wrls_stream_autotune: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
+  s->blend_cfg = best;
+  if (chosen) *chosen = best;
+  return WRLS_OK;
+}
+
+wrls_status wrls_stream_check(wrls_stream* s) {
+  if (!s) { set_error("wrls_stream_check: stream is NULL"); return WRLS_ERR_INVALID_ARG; }
+  WRLS_CHECK_CUDA(cudaStreamSynchronize(s->cs), "wrls_stream_check: synchronize");
+  int flag = 0;
+  WRLS_CHECK_CUDA(cudaMemcpy(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost), "wrls_stream_check: read");
+  if (flag != 0) {
+    WRLS_CHECK_CUDA(cudaMemset(s->err, 0, sizeof(int)), "wrls_stream_check: clear");
+    set_error("wrls_stream_check: a bounded device-side wait gave up (status %d)", flag);
+    return (wrls_status)flag;
+  }
+  return WRLS_OK;
+}
 
 wrls_status wrls_stream_enable_timing(wrls_stream* s, int enable) {
   if (!s) { set_error("wrls_stream_enable_timing: stream is NULL"); return WRLS_ERR_INVALID_ARG; }

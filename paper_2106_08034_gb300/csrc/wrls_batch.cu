@@ -18,7 +18,8 @@
 
 namespace wrls {
 
-struct FrameWork {
+struct alignas(128) FrameWork {
+  StageMaps maps;    // TMA tensor maps of the previous state copy
   KParams kp;
   void* prev_base;
   float* prev_scale;
@@ -28,6 +29,8 @@ struct FrameWork {
   const float* rad;
   const float* mot;
   float* out;
+  int* err;          // the stream's device error word
+  int stage_ok;
   int pitch;
   int W, H;
   int reset;
@@ -36,11 +39,10 @@ struct FrameWork {
   int begin_blend;   // first work item of this frame in the blend list (32 x TH tiles)
 };
 
-struct BatchHeader {
+struct alignas(128) BatchHeader {
   int n;
   int total_update;
   int total_blend;
-  int pad;
 };
 
 template <class SV> __device__ __forceinline__ SV make_view(void* base, float* scale, size_t ps, int pitch);
@@ -82,20 +84,34 @@ __device__ __forceinline__ int next_item(const BatchHeader* __restrict__ hdr,
   return *s_item - (BLEND ? fw[*frame].begin_blend : fw[*frame].begin_update);
 }
 
+// The tensor maps live in the work table (global memory written by a copy before the launch):
+// acquire them for the tensormap proxy before the first bulk copy that uses them.
+__device__ __forceinline__ void acquire_tensormap(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
+}
+
 template <class SV>
 __global__ void __launch_bounds__(kTileThreads)
     k_batch_update(const BatchHeader* __restrict__ hdr, const FrameWork* __restrict__ fw, int* counters) {
-  __shared__ UpdateSmem sm;
+  extern __shared__ unsigned char dsmem[];
+  UpdateSmem<SV>& sm = *reinterpret_cast<UpdateSmem<SV>*>(align128(dsmem));
   __shared__ int s_item, s_frame;
+  if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
+  uint32_t phase = 0;
   for (;;) {
     int f;
     const int lt = next_item<false>(hdr, fw, counters + 0, &s_item, &s_frame, &f);
     if (lt < 0) break;
     const FrameWork& w = fw[f];
+    if (threadIdx.x == 0 && w.stage_ok) {
+      acquire_tensormap(&w.maps.planes);
+      if constexpr (SV::kHasScale) acquire_tensormap(&w.maps.scale);
+    }
     const SV prev = make_view<SV>(w.prev_base, w.prev_scale, w.plane_stride, w.pitch);
     const SV next = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
-    update_tile(sm, w.kp, w.W, w.H, w.reset != 0, prev, next, w.rad, w.mot,
-                (lt % w.tiles_x) * kTW, (lt / w.tiles_x) * kTH);
+    if (!update_tile(sm, phase, w.err, w.kp, w.W, w.H, w.reset != 0, w.stage_ok != 0, prev, next,
+                     &w.maps, w.rad, w.mot, (lt % w.tiles_x) * kTW, (lt / w.tiles_x) * kTH))
+      return;
   }
 }
 
@@ -126,12 +142,15 @@ template <class SV, int TH, int R, int MODE>
 static cudaError_t capture_tick_cfg(cudaStream_t cap, const void* h_table, void* d_table, size_t bytes,
                                     int* d_counters, cudaGraphExec_t* exec) {
   constexpr int sbytes = BlendGeom<TH>::kSmemBytes;
+  constexpr int ubytes = update_smem_bytes<SV>();
   constexpr int nt = kTW * TH / R;
   cudaError_t e = cudaFuncSetAttribute(k_batch_blend<SV, TH, R, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, sbytes);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_batch_update<SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, ubytes);
+  if (e != cudaSuccess) return e;
   int ou = 0, ob = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_batch_update<SV>, kTileThreads, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_batch_update<SV>, kTileThreads, ubytes);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_batch_blend<SV, TH, R, MODE>, nt, sbytes);
   if (e != cudaSuccess) return e;
@@ -144,7 +163,7 @@ static cudaError_t capture_tick_cfg(cudaStream_t cap, const void* h_table, void*
   if (e != cudaSuccess) return e;
   cudaMemcpyAsync(d_table, h_table, bytes, cudaMemcpyHostToDevice, cap);
   cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), cap);
-  k_batch_update<SV><<<gu, kTileThreads, 0, cap>>>(hdr, fw, d_counters);
+  k_batch_update<SV><<<gu, kTileThreads, ubytes, cap>>>(hdr, fw, d_counters);
   k_batch_blend<SV, TH, R, MODE><<<gb, nt, sbytes, cap>>>(hdr, fw, d_counters);
   e = cudaStreamEndCapture(cap, &g);
   if (e != cudaSuccess) return e;
@@ -196,7 +215,6 @@ struct wrls_batch {
   // graph per (pinned slot, precision, blend mode, blend tile configuration)
   cudaGraphExec_t exec[2][3][2][kBlendConfigs] = {};
   int slot = 0;
-  int blend_cfg = 0;
   int device = 0;
 };
 
@@ -286,7 +304,14 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
   if (e != cudaSuccess) { set_error("wrls_batch_tick: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
   BatchHeader* hdr = (BatchHeader*)b->h_table[slot];
   FrameWork* fw = (FrameWork*)((char*)b->h_table[slot] + sizeof(BatchHeader));
-  const int cfg = b->blend_cfg;
+  int cfg = 0;
+  {
+    size_t most = 0;
+    for (int i = 0; i < n; ++i) {
+      const size_t px = (size_t)frames[i].stream->W * frames[i].stream->H;
+      if (px > most) { most = px; cfg = frames[i].stream->blend_cfg; }
+    }
+  }
   const int th_b = blend_rows(cfg);
   int tiles_u = 0, tiles_b = 0;
   for (int i = 0; i < n; ++i) {
@@ -294,6 +319,9 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
     const StateDesc& pv = s->state[s->cur];
     const StateDesc& nx = s->state[s->cur ^ 1];
     FrameWork& w = fw[i];
+    w.maps = pv.maps;
+    w.stage_ok = pv.stage_ok ? 1 : 0;
+    w.err = s->err;
     w.kp = s->kp;
     w.prev_base = pv.base;
     w.prev_scale = pv.scale;

@@ -7,6 +7,7 @@
 // temporal feature z[3] (Eq. 12): 25 values. Planes: 0-11 beta[c][a] (c*4+a),
 // 12-21 P upper triangle (00,01,02,03,11,12,13,22,23,33), 22-24 z.
 #pragma once
+#include <cuda.h>  // CUtensorMap (types only; the encoder is looked up at run time)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -32,7 +33,8 @@ struct KParams {
   float p0_delta;     // P of a restarted pixel
   float p_trace_max;  // wind-up guard, 0 = off
   float range_k;      // log2(e) / h_s^2: blend range exponent in base 2
-  float spatial[kMaxTaps];  // -(dx^2+dy^2) / (2 sigma_s^2) * log2(e), row-major offsets
+  float spatial[kMaxTaps];  // -(dx^2+dy^2) / (2 sigma_s^2) * log2(e), row-major offsets;
+                            // -inf beyond the window radius
   int radius;
   int weight_mode;
   int clamp_mode;
@@ -46,6 +48,73 @@ __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// ---- TMA / mbarrier helpers (inline PTX) ------------------------------------------------
+
+// Staged window of the previous state for one 32 x 8 update tile: kStageH rows x kStageW
+// columns of every plane (covers the tile's bilinear taps plus motion spread and the
+// 16-byte alignment of the box origin).
+constexpr int kStageW = 40;
+constexpr int kStageH = 12;
+constexpr int kStagePix = kStageW * kStageH;
+// Bounded waits give up after this many SM clocks (about one second) and report
+// WRLS_ERR_TIMEOUT through the stream's error word.
+constexpr long long kWaitLimit = 2000000000LL;
+
+// Tensor maps of one state copy: all planes as a 3-D tensor (x, y, plane) and, for the
+// 16-bit formats, the binary32 P-scale plane as a 2-D tensor.
+struct StageMaps {
+  CUtensorMap planes;
+  CUtensorMap scale;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the completion of phase `phase`; false if it did not complete in kWaitLimit clocks.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, phase)) {
+    if (clock64() - t0 > kWaitLimit) return false;
+  }
+  return true;
+}
+// Order this thread's generic-proxy shared-memory accesses before later async-proxy (TMA) ones.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // ---- state storage formats -------------------------------------------------------------
@@ -68,6 +137,16 @@ struct StateF32 {
   __device__ __forceinline__ void store(size_t idx, const float v[kNState]) const {
 #pragma unroll
     for (int p = 0; p < kNState; ++p) base[p * plane_stride + idx] = v[p];
+  }
+  // Staged window: [plane][kStageH][kStageW] binary32; box origin x multiple of 4 (16 B).
+  static constexpr int kAlignX = 4;
+  static constexpr uint32_t kStageBytes = kNState * kStagePix * 4;
+  static constexpr uint32_t kTxBytes = kStageBytes;  // bytes the bulk copies deliver
+  static constexpr bool kHasScale = false;
+  static __device__ __forceinline__ void load_staged(const unsigned char* stage, int idx, float v[kNState]) {
+    const float* f = (const float*)stage;
+#pragma unroll
+    for (int p = 0; p < kNState; ++p) v[p] = f[p * kStagePix + idx];
   }
 };
 
@@ -94,6 +173,23 @@ struct State16 {
     for (int p = 0; p < 12; ++p) b[p] = to_f(base[p * plane_stride + idx]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) z[c] = to_f(base[(kZ + c) * plane_stride + idx]);
+  }
+  // Staged window: [plane][kStageH][kStageW] 16-bit values, then (128-byte aligned) the
+  // [kStageH][kStageW] binary32 P scales; box origin x multiple of 8 (16 B).
+  static constexpr int kAlignX = 8;
+  static constexpr uint32_t kPlaneBytes = kNState * kStagePix * 2;
+  static constexpr uint32_t kScaleOffset = (kPlaneBytes + 127) / 128 * 128;
+  static constexpr uint32_t kStageBytes = kScaleOffset + kStagePix * 4;
+  static constexpr uint32_t kTxBytes = kPlaneBytes + kStagePix * 4;  // bytes the bulk copies deliver
+  static constexpr bool kHasScale = true;
+  static __device__ __forceinline__ void load_staged(const unsigned char* stage, int idx, float v[kNState]) {
+    const T* h = (const T*)stage;
+    const float s = ((const float*)(stage + kScaleOffset))[idx];
+#pragma unroll
+    for (int p = 0; p < kNState; ++p) {
+      const float f = to_f(h[p * kStagePix + idx]);
+      v[p] = (p >= kP && p < kZ) ? f * s : f;
+    }
   }
   __device__ __forceinline__ void store(size_t idx, const float v[kNState]) const {
     float s = fmaxf(fmaxf(v[kP + 0], v[kP + 4]), fmaxf(v[kP + 7], v[kP + 9]));
@@ -158,6 +254,27 @@ __device__ __forceinline__ void gather_bilinear(const SV& prev, int W, int H, fl
   for (int p = 0; p < kNState; ++p) st[p] = w00 * a[p] + w10 * b[p];
   prev.load((size_t)y1 * prev.pitch + x0, a);
   prev.load((size_t)y1 * prev.pitch + x1, b);
+#pragma unroll
+  for (int p = 0; p < kNState; ++p) st[p] += w01 * a[p] + w11 * b[p];
+}
+
+// Bilinear fetch from the staged window whose origin is (X0, Y0).
+template <class SV>
+__device__ __forceinline__ void gather_bilinear_staged(const unsigned char* stage, int X0, int Y0, int W,
+                                                       int H, float qx, float qy, float st[kNState]) {
+  const int x0 = (int)floorf(qx), y0 = (int)floorf(qy);
+  const float fx = qx - (float)x0, fy = qy - (float)y0;
+  const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
+  const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy);
+  const float w01 = (1.0f - fx) * fy, w11 = fx * fy;
+  const int r0 = (y0 - Y0) * kStageW, r1 = (y1 - Y0) * kStageW;
+  float a[kNState], b[kNState];
+  SV::load_staged(stage, r0 + x0 - X0, a);
+  SV::load_staged(stage, r0 + x1 - X0, b);
+#pragma unroll
+  for (int p = 0; p < kNState; ++p) st[p] = w00 * a[p] + w10 * b[p];
+  SV::load_staged(stage, r1 + x0 - X0, a);
+  SV::load_staged(stage, r1 + x1 - X0, b);
 #pragma unroll
   for (int p = 0; p < kNState; ++p) st[p] += w01 * a[p] + w11 * b[p];
 }

@@ -9,10 +9,15 @@ namespace wrls {
 
 template <class SV>
 __global__ void __launch_bounds__(kTileThreads)
-    k_update(const KParams kp, const int W, const int H, const int reset, const SV prev,
-             const SV next, const float* __restrict__ rad, const float* __restrict__ mot) {
-  __shared__ UpdateSmem sm;
-  update_tile(sm, kp, W, H, reset != 0, prev, next, rad, mot, blockIdx.x * kTW, blockIdx.y * kTH);
+    k_update(const KParams kp, const int W, const int H, const int reset, const int stage_ok,
+             const SV prev, const SV next, const __grid_constant__ StageMaps maps,
+             const float* __restrict__ rad, const float* __restrict__ mot, int* err) {
+  extern __shared__ unsigned char dsmem[];
+  UpdateSmem<SV>& sm = *reinterpret_cast<UpdateSmem<SV>*>(align128(dsmem));
+  if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
+  uint32_t phase = 0;
+  update_tile(sm, phase, err, kp, W, H, reset != 0, stage_ok != 0, prev, next, &maps, rad, mot,
+              blockIdx.x * kTW, blockIdx.y * kTH);
 }
 
 template <class SV, int TH, int R, int MODE>
@@ -33,17 +38,31 @@ __global__ void k_read_state(const int W, const int H, const SV cur, float* __re
   for (int p = 0; p < kNState; ++p) dst[p * npix + j] = v[p];
 }
 
-cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
-                          const float* rad, const float* mot, cudaStream_t cs) {
-  const dim3 grid((prev.W + kTW - 1) / kTW, (prev.H + kTH - 1) / kTH);
-  const int rs = reset ? 1 : 0;
-  switch (prev.precision) {
-    case 0: k_update<<<grid, kTileThreads, 0, cs>>>(kp, prev.W, prev.H, rs, prev.f32(), next.f32(), rad, mot); break;
-    case 1: k_update<<<grid, kTileThreads, 0, cs>>>(kp, prev.W, prev.H, rs, prev.bf16(), next.bf16(), rad, mot); break;
-    case 2: k_update<<<grid, kTileThreads, 0, cs>>>(kp, prev.W, prev.H, rs, prev.f16(), next.f16(), rad, mot); break;
-    default: return cudaErrorInvalidValue;
+template <class SV>
+static cudaError_t launch_update_t(const KParams& kp, const StateDesc& prev, const SV& pv, const SV& nx,
+                                  bool reset, const float* rad, const float* mot, int* err,
+                                  cudaStream_t cs) {
+  constexpr int bytes = update_smem_bytes<SV>();
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_update<SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
   }
+  const dim3 grid((prev.W + kTW - 1) / kTW, (prev.H + kTH - 1) / kTH);
+  k_update<SV><<<grid, kTileThreads, bytes, cs>>>(kp, prev.W, prev.H, reset ? 1 : 0, prev.stage_ok ? 1 : 0,
+                                                   pv, nx, prev.maps, rad, mot, err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
+                          const float* rad, const float* mot, int* err, cudaStream_t cs) {
+  switch (prev.precision) {
+    case 0: return launch_update_t(kp, prev, prev.f32(), next.f32(), reset, rad, mot, err, cs);
+    case 1: return launch_update_t(kp, prev, prev.bf16(), next.bf16(), reset, rad, mot, err, cs);
+    case 2: return launch_update_t(kp, prev, prev.f16(), next.f16(), reset, rad, mot, err, cs);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <class SV, int TH, int R, int MODE>

@@ -18,6 +18,8 @@ struct StateDesc {
   int precision = 0;
   int W = 0, H = 0, pitch = 0;
   size_t plane_stride = 0;  // in values
+  StageMaps maps{};          // TMA tensor maps of this copy (planes; P scales for 16-bit)
+  bool stage_ok = false;     // maps encoded and the image is at least one staging box
 
   StateF32 f32() const { return StateF32{(float*)base, plane_stride, pitch}; }
   StateBF16 bf16() const { return StateBF16{(__nv_bfloat16*)base, scale, plane_stride, pitch}; }
@@ -32,7 +34,9 @@ size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_
 bool make_kparams(const wrls_params& p, KParams* kp, const char** why);
 
 cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
-                          const float* rad, const float* mot, cudaStream_t cs);
+                          const float* rad, const float* mot, int* err, cudaStream_t cs);
+// Encode the TMA tensor maps of a state copy (sets stage_ok; false only on a driver error).
+bool encode_stage_maps(StateDesc& d, const char** why);
 // Blend tile configurations (tile rows TH, output rows per thread R):
 // 0: 16 x 4 (default), 1: 8 x 4, 2: 16 x 2, 3: 32 x 4.
 constexpr int kBlendConfigs = 4;
@@ -49,7 +53,8 @@ struct wrls_stream {
   wrls_params prm{};
   wrls::KParams kp{};
   wrls::StateDesc state[2];
-  void* mem = nullptr;          // both state copies
+  void* mem = nullptr;          // both state copies, then the device error word
+  int* err = nullptr;           // device error word (WRLS_ERR_TIMEOUT from a bounded wait)
   size_t mem_bytes = 0;
   int cur = 0;                  // copy holding frame t-1
   bool need_reset = true;

@@ -12,6 +12,7 @@
 // out-of-image halo pixels are marked (NaN radiance, negative 1/|z|) and skipped.
 // Both bodies start with a CTA barrier so a CTA may run tiles back to back.
 #pragma once
+#include "../../include/wrls.h"
 #include "wrls_device.cuh"
 
 namespace wrls {
@@ -20,125 +21,217 @@ constexpr int kTW = 32;
 constexpr int kTH = 8;
 constexpr int kTileThreads = kTW * kTH;
 
-struct UpdateSmem {
-  float rad[3][kTH + 2][kTW + 2];
-};
-
+// Shared memory of an update tile: the staged previous-state window, the radiance tile with a
+// 1-pixel halo, the tap-footprint reduction and the copy's mbarrier.
 template <class SV>
-__device__ __forceinline__ void update_tile(UpdateSmem& sm, const KParams& kp, const int W,
-                                            const int H, const bool reset, const SV& prev,
-                                            const SV& next, const float* __restrict__ rad,
-                                            const float* __restrict__ mot, const int bx0,
-                                            const int by0) {
+struct UpdateSmem {
+  alignas(128) unsigned char stage[SV::kStageBytes];
+  float rad[3][kTH + 2][kTW + 2];
+  int red[kTileThreads / 32][4];
+  int box[4];
+  alignas(8) uint64_t bar;
+};
+template <class SV>
+constexpr int update_smem_bytes() { return (int)sizeof(UpdateSmem<SV>) + 128; }  // + alignment slack
+
+// Update tile at (bx0, by0): the footprint of the bilinear taps of the tile's valid pixels is
+// reduced over the CTA; when it fits the kStageW x kStageH box, one thread copies that window
+// of every state plane into shared memory with a TMA bulk tensor copy (completion on the
+// mbarrier) while all threads stage the radiance tile; the taps are then read from shared
+// memory. Otherwise (large motion spread) the taps are read from global memory.
+// `phase` is the CTA's mbarrier phase. Returns false if the bounded wait for the copy gave up
+// (the error word is set; the caller must return).
+template <class SV>
+__device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint32_t& phase, int* err,
+                                           const KParams& kp, const int W, const int H,
+                                           const bool reset, const bool stage_ok, const SV& prev,
+                                           const SV& next, const StageMaps* maps,
+                                           const float* __restrict__ rad,
+                                           const float* __restrict__ mot, const int bx0,
+                                           const int by0) {
   const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t npix = (size_t)W * H;
+  const int x = bx0 + tx, y = by0 + ty;
+  const bool inside = x < W && y < H;
+  const size_t j = (size_t)y * W + x;
+  __syncthreads();  // the previous tile is done with shared memory
+
+  // reprojection q = pi(v_j) = j + v_j (Table 2), in binary32
+  float qx = 0.0f, qy = 0.0f;
+  bool valid = false;
+  if (inside) {
+    qx = (float)x + __ldg(mot + j);
+    qy = (float)y + __ldg(mot + npix + j);
+    valid = !reset && qx >= 0.0f && qx <= (float)(W - 1) && qy >= 0.0f && qy <= (float)(H - 1);
+  }
+  int lo_x = 0x7fffffff, hi_x = -1, lo_y = 0x7fffffff, hi_y = -1;
+  if (valid) {
+    const int x0 = (int)floorf(qx), y0 = (int)floorf(qy);
+    lo_x = x0; hi_x = min(x0 + 1, W - 1);
+    lo_y = y0; hi_y = min(y0 + 1, H - 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo_x = min(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
+    hi_x = max(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
+    lo_y = min(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
+    hi_y = max(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+  }
+  if (lane == 0) {
+    sm.red[warp][0] = lo_x; sm.red[warp][1] = hi_x; sm.red[warp][2] = lo_y; sm.red[warp][3] = hi_y;
+  }
   __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 1; w < kTileThreads / 32; ++w) {
+      lo_x = min(lo_x, sm.red[w][0]); hi_x = max(hi_x, sm.red[w][1]);
+      lo_y = min(lo_y, sm.red[w][2]); hi_y = max(hi_y, sm.red[w][3]);
+    }
+    int fits = 0, X0 = 0, Y0 = 0;
+    if (stage_ok && hi_x >= 0) {
+      X0 = lo_x - lo_x % SV::kAlignX;  // TMA box origin: 16-byte aligned column
+      Y0 = lo_y;
+      fits = (hi_x - X0 < kStageW) && (hi_y - Y0 < kStageH);
+    }
+    sm.box[0] = X0; sm.box[1] = Y0; sm.box[2] = fits;
+    if (fits) {
+      fence_proxy_async();
+      mbar_expect_tx(&sm.bar, SV::kTxBytes);
+      tma_load_3d(sm.stage, &maps->planes, X0, Y0, 0, &sm.bar);
+      if constexpr (SV::kHasScale) tma_load_2d(sm.stage + SV::kScaleOffset, &maps->scale, X0, Y0, &sm.bar);
+    }
+  }
+  // radiance tile with a 1-pixel halo (out-of-image = NaN, skipped by the clamp)
   for (int i = threadIdx.x; i < (kTH + 2) * (kTW + 2); i += kTileThreads) {
     const int ly = i / (kTW + 2), lx = i % (kTW + 2);
     const int gx = bx0 - 1 + lx, gy = by0 - 1 + ly;
     float r = __int_as_float(0x7fc00000), g = r, b = r;
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-      const size_t j = (size_t)gy * W + gx;
-      r = __ldg(rad + j);
-      g = __ldg(rad + npix + j);
-      b = __ldg(rad + 2 * npix + j);
+      const size_t jj = (size_t)gy * W + gx;
+      r = __ldg(rad + jj);
+      g = __ldg(rad + npix + jj);
+      b = __ldg(rad + 2 * npix + jj);
     }
     sm.rad[0][ly][lx] = r;
     sm.rad[1][ly][lx] = g;
     sm.rad[2][ly][lx] = b;
   }
   __syncthreads();
-  const int x = bx0 + tx, y = by0 + ty;
-  if (x < W && y < H) {
-    const size_t j = (size_t)y * W + x;
-    float I[3] = {sm.rad[0][ty + 1][tx + 1], sm.rad[1][ty + 1][tx + 1], sm.rad[2][ty + 1][tx + 1]};
-    const bool missing = !(isfinite(I[0]) && isfinite(I[1]) && isfinite(I[2]));
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    bool have_box = false;
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        const float a = sm.rad[0][ty + dy][tx + dx], b = sm.rad[1][ty + dy][tx + dx],
-                    c = sm.rad[2][ty + dy][tx + dx];
-        if (isfinite(a) && isfinite(b) && isfinite(c)) {
-          have_box = true;
-          lo[0] = fminf(lo[0], a); hi[0] = fmaxf(hi[0], a);
-          lo[1] = fminf(lo[1], b); hi[1] = fmaxf(hi[1], b);
-          lo[2] = fminf(lo[2], c); hi[2] = fmaxf(hi[2], c);
-        }
-      }
-    // reprojection q = pi(v_j) = j + v_j (Table 2), in binary32
-    const float qx = (float)x + __ldg(mot + j);
-    const float qy = (float)y + __ldg(mot + npix + j);
-    const bool valid = !reset && qx >= 0.0f && qx <= (float)(W - 1) && qy >= 0.0f &&
-                       qy <= (float)(H - 1);
-    float st[kNState];
-    if (valid) gather_bilinear(prev, W, H, qx, qy, st);
-    update_pixel(kp, valid, st, I, missing, lo, hi, have_box);
-    next.store((size_t)y * next.pitch + x, st);
+  const int X0 = sm.box[0], Y0 = sm.box[1];
+  const bool fits = sm.box[2] != 0;
+  bool ok = true;
+  if (fits) ok = mbar_wait_bounded(&sm.bar, phase);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, (int)WRLS_ERR_TIMEOUT);
+    mbar_wait_bounded(&sm.bar, phase);  // the copy may still be in flight
+    return false;
   }
+  if (fits) phase ^= 1u;
+  if (!inside) return true;
+
+  float I[3] = {sm.rad[0][ty + 1][tx + 1], sm.rad[1][ty + 1][tx + 1], sm.rad[2][ty + 1][tx + 1]};
+  const bool missing = !(isfinite(I[0]) && isfinite(I[1]) && isfinite(I[2]));
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool have_box = false;
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      const float a = sm.rad[0][ty + dy][tx + dx], b = sm.rad[1][ty + dy][tx + dx],
+                  c = sm.rad[2][ty + dy][tx + dx];
+      if (isfinite(a) && isfinite(b) && isfinite(c)) {
+        have_box = true;
+        lo[0] = fminf(lo[0], a); hi[0] = fmaxf(hi[0], a);
+        lo[1] = fminf(lo[1], b); hi[1] = fmaxf(hi[1], b);
+        lo[2] = fminf(lo[2], c); hi[2] = fmaxf(hi[2], c);
+      }
+    }
+  float st[kNState];
+  if (valid) {
+    if (fits) gather_bilinear_staged<SV>(sm.stage, X0, Y0, W, H, qx, qy, st);
+    else gather_bilinear(prev, W, H, qx, qy, st);
+  }
+  update_pixel(kp, valid, st, I, missing, lo, hi, have_box);
+  next.store((size_t)y * next.pitch + x, st);
+  return true;
+}
+
+// 128-byte aligned view of a dynamic shared-memory buffer.
+__device__ __forceinline__ unsigned char* align128(unsigned char* p) {
+  return p + ((128u - (smem_u32(p) & 127u)) & 127u);
 }
 
 // ---- spatio-temporal blend (Sec. 5.3) -------------------------------------------------------
 //
 // A blend tile is 32 x TH output pixels; each thread produces R vertically adjacent outputs of
 // one column, so a neighbour read from shared memory serves up to 5 of the thread's outputs.
-// Shared memory holds the (32+4) x (TH+4) window of the models after the update, one 20-float
-// record per pixel: beta[12], z[3], 1/(|z|+eps) (negative = outside the image), 4 pad floats.
-// The 80-byte record stride makes the four 128-bit loads of a warp conflict-free.
-constexpr int kBlendRec = 20;
+// Shared memory holds the (32+4) x (TH+4) window of the models after the update as two record
+// arrays: beta[12] per pixel (48-byte stride) and {z[3], 1/(|z|+eps)} per pixel (16 bytes);
+// both strides make a warp's 128-bit loads conflict-free.
+//
+// No neighbour is tested in the inner loop. A window pixel outside the image gets beta = 0,
+// z = kFarZ and 1/(|z|+eps) = 0, so its feature distance to any pixel of the image is huge and
+// its weight exp2(-huge) is exactly 0; offsets beyond the window radius (radius < 2) get a
+// spatial exponent of -inf, weight exactly 0. Adding exact zeros leaves every sum unchanged,
+// so the result equals skipping those neighbours.
 constexpr int kBlendSW = kTW + 2 * kMaxRadius;
+constexpr float kFarZ = 1.0e18f;
 
 template <int TH>
 struct BlendGeom {
   static constexpr int SH = TH + 2 * kMaxRadius;
-  static constexpr int kSmemBytes = SH * kBlendSW * kBlendRec * 4;
+  static constexpr int kPix = SH * kBlendSW;
+  static constexpr int kSmemBytes = kPix * (48 + 16);
 };
 
 // Fill the shared window of the blend tile at (bx0, by0) from the state copy `cur`.
 template <class SV, int TH, int NT>
-__device__ __forceinline__ void blend_fill(float4* __restrict__ sm, const KParams& kp, const int W,
-                                           const int H, const SV& cur, const int bx0, const int by0) {
-  constexpr int R0 = kMaxRadius, SH = BlendGeom<TH>::SH;
-#pragma unroll 2
-  for (int i = threadIdx.x; i < SH * kBlendSW; i += NT) {
+__device__ __forceinline__ void blend_fill(float4* __restrict__ sb, float4* __restrict__ szr,
+                                           const KParams& kp, const int W, const int H, const SV& cur,
+                                           const int bx0, const int by0) {
+  constexpr int R0 = kMaxRadius;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < BlendGeom<TH>::kPix; i += NT) {
     const int ly = i / kBlendSW, lx = i % kBlendSW;
     const int gx = bx0 - R0 + lx, gy = by0 - R0 + ly;
-    float4* rec = sm + i * (kBlendRec / 4);
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
       float b[12], z[3];
       cur.load_beta_z((size_t)gy * cur.pitch + gx, b, z);
       const float r = 1.0f / (sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]) + kp.eps);
-      rec[0] = make_float4(b[0], b[1], b[2], b[3]);
-      rec[1] = make_float4(b[4], b[5], b[6], b[7]);
-      rec[2] = make_float4(b[8], b[9], b[10], b[11]);
-      rec[3] = make_float4(z[0], z[1], z[2], r);
+      sb[3 * i + 0] = make_float4(b[0], b[1], b[2], b[3]);
+      sb[3 * i + 1] = make_float4(b[4], b[5], b[6], b[7]);
+      sb[3 * i + 2] = make_float4(b[8], b[9], b[10], b[11]);
+      szr[i] = make_float4(z[0], z[1], z[2], r);
     } else {
-      rec[3] = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+      const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      sb[3 * i + 0] = zero;
+      sb[3 * i + 1] = zero;
+      sb[3 * i + 2] = zero;
+      szr[i] = make_float4(kFarZ, kFarZ, kFarZ, 0.0f);
     }
   }
 }
 
-// Blend the outputs of the tile whose window is in `sm`. MODE 0: out_i = sum_k b_ik (p_i .
-// beta_k) / sum_k b_ik (neighbours' models predict pixel i); MODE 1: sum_k b_ik (p_k . beta_k)
-// / sum_k b_ik. b_ik = exp(-|dxy|^2 / (2 sigma_s^2)) exp(-d_z(i,k)^2 / h_s^2) with d_z the
+// Blend the outputs of the tile whose window is in shared memory. MODE 0: out_i = sum_k b_ik
+// (p_i . beta_k) / sum_k b_ik (neighbours' models predict pixel i); MODE 1: sum_k b_ik (p_k .
+// beta_k) / sum_k b_ik. b_ik = exp(-|dxy|^2 / (2 sigma_s^2)) exp(-d_z(i,k)^2 / h_s^2) with d_z the
 // Eq. 13 distance of the features; 1 / (min(|z_i|, |z_k|) + eps) = max(r_i, r_k).
 template <int TH, int R, int MODE>
-__device__ __forceinline__ void blend_compute(const float4* __restrict__ sm, const KParams& kp,
+__device__ __forceinline__ void blend_compute(const float4* __restrict__ sb,
+                                              const float4* __restrict__ szr, const KParams& kp,
                                               const int W, const int H, float* __restrict__ out,
                                               const int bx0, const int by0) {
   constexpr int R0 = kMaxRadius;
   constexpr int RW = 2 * R0 + 1;
   const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
   const int x = bx0 + tx, y0 = by0 + ty * R;
-  const int rad = kp.radius;
   const bool feat = kp.feature_mode == 0;
   float zi[R][3], ri[R], den[R];
   float acc[R][MODE == 0 ? 12 : 3];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    const float4 q = sm[((ty * R + i + R0) * kBlendSW + tx + R0) * (kBlendRec / 4) + 3];
+    const float4 q = szr[(ty * R + i + R0) * kBlendSW + tx + R0];
     zi[i][0] = q.x; zi[i][1] = q.y; zi[i][2] = q.z; ri[i] = q.w;
     den[i] = 0.0f;
 #pragma unroll
@@ -148,11 +241,9 @@ __device__ __forceinline__ void blend_compute(const float4* __restrict__ sm, con
   for (int kr = 0; kr < R + 2 * R0; ++kr) {
 #pragma unroll
     for (int dx = -R0; dx <= R0; ++dx) {
-      if (dx < -rad || dx > rad) continue;
-      const float4* rec = sm + ((ty * R + kr) * kBlendSW + tx + R0 + dx) * (kBlendRec / 4);
-      const float4 q3 = rec[3];
-      if (q3.w < 0.0f) continue;
-      const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2];
+      const int k = (ty * R + kr) * kBlendSW + tx + R0 + dx;
+      const float4 q3 = szr[k];
+      const float4 q0 = sb[3 * k + 0], q1 = sb[3 * k + 1], q2 = sb[3 * k + 2];
       float pk0 = 0.0f, pk1 = 0.0f, pk2 = 0.0f;
       if (MODE == 1) {
         const float a1 = feat ? q3.x : 0.0f, a2 = feat ? q3.y : 0.0f, a3 = feat ? q3.z : 0.0f;
@@ -163,8 +254,7 @@ __device__ __forceinline__ void blend_compute(const float4* __restrict__ sm, con
 #pragma unroll
       for (int i = 0; i < R; ++i) {
         const int dy = kr - R0 - i;
-        if (dy < -R0 || dy > R0) continue;
-        if (dy < -rad || dy > rad) continue;
+        if (dy < -R0 || dy > R0) continue;  // compile-time
         const float e0 = zi[i][0] - q3.x, e1 = zi[i][1] - q3.y, e2 = zi[i][2] - q3.z;
         const float rm = fmaxf(ri[i], q3.w);
         const float d2 = (e0 * e0 + e1 * e1 + e2 * e2) * (rm * rm);
@@ -205,14 +295,17 @@ __device__ __forceinline__ void blend_compute(const float4* __restrict__ sm, con
 }
 
 // Whole blend tile: barrier, fill, barrier, compute (a CTA may run tiles back to back).
+// `smem` is 16-byte aligned and holds BlendGeom<TH>::kSmemBytes.
 template <class SV, int TH, int R, int MODE>
-__device__ __forceinline__ void blend_tile(float4* __restrict__ sm, const KParams& kp, const int W,
+__device__ __forceinline__ void blend_tile(float4* __restrict__ smem, const KParams& kp, const int W,
                                            const int H, const SV& cur, float* __restrict__ out,
                                            const int bx0, const int by0) {
+  float4* sb = smem;
+  float4* szr = smem + 3 * BlendGeom<TH>::kPix;
   __syncthreads();
-  blend_fill<SV, TH, kTW * TH / R>(sm, kp, W, H, cur, bx0, by0);
+  blend_fill<SV, TH, kTW * TH / R>(sb, szr, kp, W, H, cur, bx0, by0);
   __syncthreads();
-  blend_compute<TH, R, MODE>(sm, kp, W, H, out, bx0, by0);
+  blend_compute<TH, R, MODE>(sb, szr, kp, W, H, out, bx0, by0);
 }
 
 }  // namespace wrls

@@ -35,7 +35,8 @@ EXPORTED = [
     "wrls_params_default", "wrls_state_bytes", "wrls_stream_create", "wrls_stream_set_cuda_stream",
     "wrls_denoise_frame", "wrls_denoise_frame_host", "wrls_stream_reset", "wrls_stream_destroy",
     "wrls_stream_read_state", "wrls_stream_frames", "wrls_last_error",
-    "wrls_stream_enable_timing", "wrls_stream_kernel_times",
+    "wrls_stream_enable_timing", "wrls_stream_kernel_times", "wrls_stream_check",
+    "wrls_stream_autotune", "wrls_stream_set_blend_config",
     "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
 ]
 
@@ -89,6 +90,9 @@ def lib():
         "wrls_stream_frames": (ctypes.c_uint64, [vp]),
         "wrls_last_error": (ctypes.c_char_p, []),
         "wrls_stream_enable_timing": (i, [vp, i]),
+        "wrls_stream_check": (i, [vp]),
+        "wrls_stream_autotune": (i, [vp, vp, i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
+        "wrls_stream_set_blend_config": (i, [vp, i]),
         "wrls_stream_kernel_times": (i, [vp, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
         "wrls_batch_create": (i, [i, ctypes.POINTER(vp)]),
@@ -176,6 +180,26 @@ def wrls_stream_read_state(stream: int, dst) -> None:
 
 def wrls_stream_frames(stream: int) -> int:
     return int(lib().wrls_stream_frames(stream))
+
+
+BLEND_CONFIGS = 4
+
+
+def wrls_stream_autotune(stream: int, out, reps: int = 5):
+    """Time every blend tile configuration; returns (per-config ms list, chosen index)."""
+    times = (ctypes.c_float * BLEND_CONFIGS)()
+    chosen = ctypes.c_int()
+    _check(lib().wrls_stream_autotune(stream, _ptr(out), int(reps), times, ctypes.byref(chosen)))
+    return [float(t) for t in times], int(chosen.value)
+
+
+def wrls_stream_set_blend_config(stream: int, config: int) -> None:
+    _check(lib().wrls_stream_set_blend_config(stream, int(config)))
+
+
+def wrls_stream_check(stream: int) -> None:
+    """Synchronise and raise WrlsError if a kernel's bounded wait gave up."""
+    _check(lib().wrls_stream_check(stream))
 
 
 def wrls_stream_enable_timing(stream: int, enable: bool = True) -> None:
