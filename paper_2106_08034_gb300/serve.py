@@ -1,0 +1,280 @@
+"""Serving loop for interactive viewer sessions (continuous batching over the C ABI).
+
+A session is one viewer: a resolution, a frame rate and a lifetime. It is admitted when a
+session slot is free and the device memory its persistent per-pixel state needs
+(``wrls_state_bytes``) plus its output buffer fits the budget; otherwise it waits in the
+queue until a departure frees memory. Admitted sessions keep their state resident on the
+device across frames. Each round of the loop takes every session whose next frame is due,
+and denoises all of them with one ``wrls_batch_tick`` (one persistent, graph-captured
+launch pair over the (stream, tile) work list). Up to ``depth`` ticks are in flight, so
+sessions that arrive while others are on the GPU join the next tick and their work overlaps
+on the device. A frame's latency is the time from its release (its due time) to the
+completion of the tick that denoised it, observed on the host by polling the tick's CUDA
+event. If a session falls more than one frame behind, the older due frames are dropped.
+
+Inputs come from per-resolution rings of pre-generated frames on the device, read-only and
+shared by sessions of one resolution; session k's n-th processed frame is ring[n % len].
+"""
+from __future__ import annotations
+
+import dataclasses
+import heapq
+import math
+import random
+import time
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import torch
+
+from . import synth
+from . import wrls as W
+
+
+@dataclasses.dataclass
+class Session:
+    sid: int
+    width: int
+    height: int
+    fps: float
+    arrive: float
+    depart: float
+    stream: Optional[W.Stream] = None
+    out: Optional[torch.Tensor] = None
+    bytes: int = 0
+    next_due: float = 0.0
+    processed: int = 0
+    dropped: int = 0
+    in_flight: int = 0
+
+
+@dataclasses.dataclass
+class Tick:
+    event: torch.cuda.Event
+    releases: List[Tuple[int, float]]   # (sid, release time) per frame
+    pixels: int
+
+
+class Server:
+    """Admission by device memory, continuous batching, latency accounting."""
+
+    def __init__(self, hbm_budget_bytes: int, max_sessions: int = 64,
+                 params: Optional[W.wrls_params] = None, depth: int = 2, deadline_s: float = 1 / 60,
+                 rings: Optional[Dict[Tuple[int, int], Tuple[torch.Tensor, torch.Tensor]]] = None,
+                 cuda_stream: Optional[torch.cuda.Stream] = None):
+        self.budget = int(hbm_budget_bytes)
+        self.max_sessions = int(max_sessions)
+        self.params = params if params is not None else W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
+        self.depth = int(depth)
+        self.deadline = float(deadline_s)
+        self.rings = rings if rings is not None else {}
+        self.cs = cuda_stream if cuda_stream is not None else torch.cuda.Stream()
+        self.batch = W.wrls_batch_create(self.max_sessions)
+        W.wrls_batch_set_cuda_stream(self.batch, self.cs)
+        self.active: Dict[int, Session] = {}
+        self.queue: List[Session] = []
+        self.used = 0
+        self.ticks: List[Tick] = []
+        self.latencies: List[float] = []
+        self.missed = 0
+        self.frames_done = 0
+        self.pixels_done = 0
+        self.admitted_total = 0
+        self.max_concurrent = 0
+        self.rejected_budget = 0
+
+    # --- admission --------------------------------------------------------------------
+    def session_bytes(self, w: int, h: int) -> int:
+        return W.wrls_state_bytes(w, h, self.params) + 3 * w * h * 4
+
+    def request(self, s: Session, now: float) -> None:
+        self.queue.append(s)
+        self._admit(now)
+
+    def _admit(self, now: float) -> None:
+        keep = []
+        for s in self.queue:
+            need = self.session_bytes(s.width, s.height)
+            if len(self.active) < self.max_sessions and self.used + need <= self.budget:
+                s.bytes = need
+                s.stream = W.Stream(s.width, s.height, self.params, cuda_stream=self.cs)
+                s.out = torch.empty(3, s.height, s.width, device="cuda")
+                s.next_due = max(now, s.arrive)
+                self.active[s.sid] = s
+                self.used += need
+                self.admitted_total += 1
+            else:
+                if self.used + need > self.budget:
+                    self.rejected_budget += 1
+                keep.append(s)
+        self.queue = keep
+        self.max_concurrent = max(self.max_concurrent, len(self.active))
+
+    def depart(self, sid: int, now: float) -> None:
+        s = self.active.get(sid)
+        if s is None:
+            self.queue = [q for q in self.queue if q.sid != sid]
+            return
+        if s.in_flight:
+            s.depart = now      # leave after its frames complete
+            return
+        del self.active[sid]
+        self.used -= s.bytes
+        s.stream.close()
+        s.stream = None
+        self._admit(now)
+
+    # --- batching ---------------------------------------------------------------------
+    def due_frames(self, now: float) -> List[Session]:
+        ready = []
+        for s in self.active.values():
+            if s.in_flight or now < s.next_due or now >= s.depart:
+                continue
+            period = 1.0 / s.fps
+            behind = int((now - s.next_due) / period)
+            if behind > 0:                      # keep only the newest due frame
+                s.dropped += behind
+                self.missed += behind
+                s.next_due += behind * period
+            ready.append(s)
+        return ready
+
+    def launch(self, ready: Sequence[Session]) -> None:
+        io, rel, px = [], [], 0
+        for s in ready:
+            rad, mot = self.rings[(s.width, s.height)]
+            k = s.processed % rad.shape[0]
+            io.append((s.stream.handle, rad[k], None, None, mot[k], s.out))
+            rel.append((s.sid, s.next_due))
+            px += s.width * s.height
+            s.next_due += 1.0 / s.fps
+            s.in_flight += 1
+        W.wrls_batch_tick(self.batch, io)
+        ev = torch.cuda.Event()
+        ev.record(self.cs)
+        self.ticks.append(Tick(ev, rel, px))
+
+    def poll(self, now: float) -> None:
+        done = [t for t in self.ticks if t.event.query()]
+        if not done:
+            return
+        t_done = time.perf_counter()
+        for t in done:
+            self.ticks.remove(t)
+            self.pixels_done += t.pixels
+            for sid, rel in t.releases:
+                lat = t_done - rel
+                self.latencies.append(lat)
+                if lat > self.deadline:
+                    self.missed += 1
+                self.frames_done += 1
+                s = self.active.get(sid)
+                if s is not None:
+                    s.in_flight -= 1
+                    s.processed += 1
+        for sid in [sid for sid, s in self.active.items() if s.in_flight == 0 and now >= s.depart]:
+            self.depart(sid, now)
+
+    def close(self) -> None:
+        self.cs.synchronize()
+        for s in list(self.active.values()):
+            s.stream.close()
+        self.active.clear()
+        W.wrls_batch_destroy(self.batch)
+        self.batch = 0
+
+
+def make_rings(resolutions: Sequence[Tuple[int, int]], frames: int = 4, seed: int = 11,
+               device="cuda") -> Dict[Tuple[int, int], Tuple[torch.Tensor, torch.Tensor]]:
+    rings = {}
+    for i, (w, h) in enumerate(resolutions):
+        sc = synth.Scene(synth.SceneSpec(w, h, frames, seed=seed + i, motion="orbit", firefly_frac=0.05))
+        rad = torch.empty(frames, 3, h, w, device=device)
+        mot = torch.empty(frames, 2, h, w, device=device)
+        for t in range(frames):
+            f = sc.frame(t, device=device)
+            rad[t].copy_(f["radiance"])
+            mot[t].copy_(f["motion"])
+        rings[(w, h)] = (rad, mot)
+    return rings
+
+
+def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0, 60.0),
+             resolutions=synth.SERVING_RESOLUTIONS, fps_range=(30.0, 60.0), max_sessions: int = 64,
+             hbm_budget_bytes: Optional[int] = None, deadline_s: float = 1 / 60, depth: int = 2,
+             seed: int = 5, warm_start: bool = True, params: Optional[W.wrls_params] = None,
+             rings=None) -> dict:
+    """Run the serving loop in real time for `duration_s`. Sessions arrive as a Poisson
+    process; with warm_start the run starts from the stationary population (Poisson count
+    with mean arrival_rate * mean lifetime, residual lifetimes uniform)."""
+    rng = random.Random(seed)
+    if rings is None:
+        rings = make_rings(resolutions)
+    if hbm_budget_bytes is None:
+        free, _ = torch.cuda.mem_get_info()
+        hbm_budget_bytes = int(0.5 * free)
+    srv = Server(hbm_budget_bytes, max_sessions=max_sessions, params=params, depth=depth,
+                 deadline_s=deadline_s, rings=rings)
+    t0 = time.perf_counter()
+    sid = 0
+    initial = []
+    if warm_start:
+        mean_pop = arrival_rate * 0.5 * (lifetime[0] + lifetime[1])
+        # Poisson(mean_pop) by inversion
+        n, p, L = 0, 1.0, math.exp(-mean_pop)
+        while True:
+            p *= rng.random()
+            if p <= L:
+                break
+            n += 1
+        for _ in range(n):
+            w, h = rng.choice(list(resolutions))
+            life = rng.uniform(*lifetime)
+            initial.append(Session(sid, w, h, rng.uniform(*fps_range), t0, t0 + rng.uniform(0, life)))
+            sid += 1
+    arrivals = []
+    t = t0
+    while True:
+        t += rng.expovariate(arrival_rate)
+        if t > t0 + duration_s:
+            break
+        w, h = rng.choice(list(resolutions))
+        arrivals.append(Session(sid, w, h, rng.uniform(*fps_range), t, t + rng.uniform(*lifetime)))
+        sid += 1
+    for s in initial:
+        srv.request(s, t0)
+    pending = list(arrivals)
+    end = t0 + duration_s
+    rounds = 0
+    with torch.cuda.stream(srv.cs):
+        while True:
+            now = time.perf_counter()
+            if now >= end:
+                break
+            while pending and pending[0].arrive <= now:
+                srv.request(pending.pop(0), now)
+            for s in [s for s in srv.active.values() if now >= s.depart and s.in_flight == 0]:
+                srv.depart(s.sid, now)
+            srv.poll(now)
+            if len(srv.ticks) < srv.depth:
+                ready = srv.due_frames(now)
+                if ready:
+                    srv.launch(ready)
+                    rounds += 1
+        srv.cs.synchronize()
+        srv.poll(time.perf_counter())
+    wall = time.perf_counter() - t0
+    lat = sorted(srv.latencies)
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] * 1e3 if lat else None
+    res = {
+        "duration_s": round(wall, 3), "frames": srv.frames_done, "ticks": rounds,
+        "mpix_per_s": round(srv.pixels_done / wall / 1e6, 2),
+        "p50_ms": round(pct(0.50), 3) if lat else None, "p99_ms": round(pct(0.99), 3) if lat else None,
+        "deadline_ms": round(deadline_s * 1e3, 2),
+        "missed_or_dropped": srv.missed, "admitted": srv.admitted_total,
+        "max_concurrent": srv.max_concurrent, "queued_at_end": len(srv.queue),
+        "hbm_budget_gb": round(hbm_budget_bytes / 1e9, 2), "hbm_used_gb_at_end": round(srv.used / 1e9, 3),
+    }
+    srv.close()
+    return res
