@@ -212,6 +212,36 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n);
 /* Synchronise and free. NULL is a no-op. */
 void wrls_batch_destroy(wrls_batch* b);
 
+/*
+ * wrls_batch_tick_static: the batched tick for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is an integration entry point.
+ *
+ * Some callers must not call cudaMalloc: a plugin living inside a host application that
+ * owns the device memory budget (allocating would break its accounting or fail under its
+ * cap), or a frame loop that cannot afford the implicit device synchronisation that an
+ * allocation may cause. wrls_batch_create allocates a device work table, work counters and
+ * pinned host buffers; this entry point allocates nothing. Its work table and its two work
+ * counters live in one statically sized device array compiled into the library (10,752
+ * bytes, for at most WRLS_STATIC_BATCH_MAX frames per call); every GPU that loads the
+ * library holds that array until the process exits. The streams passed in were created
+ * with wrls_stream_create beforehand and keep their own state; the caller passes all
+ * inputs and outputs as with wrls_batch_tick.
+ *
+ *   frames, n      one frame of each of n streams, 1 <= n <= WRLS_STATIC_BATCH_MAX (larger n
+ *                  is rejected with WRLS_ERR_INVALID_ARG); same rules as wrls_batch_tick.
+ *   cuda_stream    the cudaStream_t (as void*) to enqueue on; NULL = legacy default stream.
+ *
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress) with that device current and caches it; make that first call
+ * before any stream capture. Every call reuses the same array and overwrites what the
+ * previous call left there (the work counters are cleared by each call), so calls whose
+ * work overlaps on the GPU (on different CUDA streams, or from different host threads
+ * without ordering) race: serialise them on one CUDA stream. Outputs equal those of
+ * wrls_batch_tick. Asynchronous.
+ */
+#define WRLS_STATIC_BATCH_MAX 16
+wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "wrls_internal.h"
@@ -383,3 +384,186 @@ void wrls_batch_destroy(wrls_batch* b) {
 }
 
 }  // extern "C"
+
+// ---- wrls_batch_tick_static: the batched tick without any device allocation -------------
+//
+// For callers that cannot allocate device memory (see include/wrls.h). The work table and
+// the two work counters live in the file-scope array below instead of cudaMalloc'ed memory.
+// Host code must not pass the array's name to a kernel (on the host it names a stand-in, not
+// device memory): its device address is looked up once per device with
+// cudaGetSymbolAddress, on the first call made with that device current, and cached.
+
+constexpr int kStaticBatchMax = 16;  // frames per call
+constexpr size_t kStaticTableBytes = sizeof(BatchHeader) + kStaticBatchMax * sizeof(FrameWork);
+constexpr size_t kStaticCountersOffset = (kStaticTableBytes + 255) / 256 * 256;
+constexpr size_t kStaticScratchBytes = kStaticCountersOffset + 256;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static void* g_static_addr[256] = {};  // device address of g_static_scratch per device ordinal
+
+static wrls_status static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    set_error("wrls_batch_tick_static: no usable current device");
+    return WRLS_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress((void**)&ptr, g_static_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      set_error("wrls_batch_tick_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return WRLS_ERR_CUDA;
+    }
+    g_static_addr[dev] = ptr;
+  }
+  *out = g_static_addr[dev];
+  return WRLS_OK;
+}
+
+template <class SV, int TH, int R, int MODE>
+static cudaError_t launch_static_cfg(cudaStream_t cs, void* d_table, int* d_counters) {
+  constexpr int sbytes = BlendGeom<TH>::kSmemBytes;
+  constexpr int ubytes = update_smem_bytes<SV>();
+  constexpr int nt = kTW * TH / R;
+  cudaError_t e = cudaFuncSetAttribute(k_batch_blend<SV, TH, R, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sbytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_batch_update<SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, ubytes);
+  if (e != cudaSuccess) return e;
+  int ou = 0, ob = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_batch_update<SV>, kTileThreads, ubytes);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_batch_blend<SV, TH, R, MODE>, nt, sbytes);
+  if (e != cudaSuccess) return e;
+  const int sms = sm_count();
+  const BatchHeader* hdr = (const BatchHeader*)d_table;
+  const FrameWork* fw = (const FrameWork*)((char*)d_table + sizeof(BatchHeader));
+  k_batch_update<SV><<<sms * (ou > 0 ? ou : 1), kTileThreads, ubytes, cs>>>(hdr, fw, d_counters);
+  k_batch_blend<SV, TH, R, MODE><<<sms * (ob > 0 ? ob : 1), nt, sbytes, cs>>>(hdr, fw, d_counters);
+  return cudaGetLastError();
+}
+
+template <class SV, int MODE>
+static cudaError_t launch_static_mode(int cfg, cudaStream_t cs, void* d_table, int* d_counters) {
+  switch (cfg) {
+    case 0: return launch_static_cfg<SV, 16, 4, MODE>(cs, d_table, d_counters);
+    case 1: return launch_static_cfg<SV, 8, 4, MODE>(cs, d_table, d_counters);
+    case 2: return launch_static_cfg<SV, 16, 2, MODE>(cs, d_table, d_counters);
+    case 3: return launch_static_cfg<SV, 32, 4, MODE>(cs, d_table, d_counters);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class SV>
+static cudaError_t launch_static(int mode, int cfg, cudaStream_t cs, void* d_table, int* d_counters) {
+  return mode == 0 ? launch_static_mode<SV, 0>(cfg, cs, d_table, d_counters)
+                   : launch_static_mode<SV, 1>(cfg, cs, d_table, d_counters);
+}
+
+extern "C" wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n, void* cuda_stream) {
+  if (!frames) { set_error("wrls_batch_tick_static: frames is NULL"); return WRLS_ERR_INVALID_ARG; }
+  if (n < 1 || n > kStaticBatchMax) {
+    set_error("wrls_batch_tick_static: n = %d frames outside [1, %d] (the static work table holds at most %d)",
+              n, kStaticBatchMax, kStaticBatchMax);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  const int prec = frames[0].stream ? frames[0].stream->prm.state_precision : -1;
+  const int mode = frames[0].stream ? frames[0].stream->prm.blend_mode : -1;
+  for (int i = 0; i < n; ++i) {
+    const wrls_frame_io& io = frames[i];
+    if (!io.stream || !io.radiance || !io.motion || !io.out) {
+      set_error("wrls_batch_tick_static: frame %d has a NULL stream, radiance, motion or out", i);
+      return WRLS_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)io.radiance | (uintptr_t)io.motion | (uintptr_t)io.out) & 3u) {
+      set_error("wrls_batch_tick_static: frame %d buffers must be 4-byte aligned", i);
+      return WRLS_ERR_INVALID_ARG;
+    }
+    if (io.stream->prm.state_precision != prec || io.stream->prm.blend_mode != mode) {
+      set_error("wrls_batch_tick_static: all streams of a call must share one state precision and blend mode");
+      return WRLS_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < i; ++k)
+      if (frames[k].stream == io.stream) {
+        set_error("wrls_batch_tick_static: stream of frame %d appears twice", i);
+        return WRLS_ERR_INVALID_ARG;
+      }
+  }
+  void* scratch = nullptr;
+  wrls_status st = static_scratch_address(&scratch);
+  if (st != WRLS_OK) return st;
+  int cfg = 0;
+  size_t most = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t px = (size_t)frames[i].stream->W * frames[i].stream->H;
+    if (px > most) { most = px; cfg = frames[i].stream->blend_cfg; }
+  }
+  const int th_b = blend_rows(cfg);
+  // The table is built on the stack and copied with cudaMemcpyAsync from pageable memory,
+  // which returns once the bytes are staged, so the stack buffer may go out of scope.
+  alignas(128) unsigned char host_table[kStaticTableBytes];
+  memset(host_table, 0, sizeof(host_table));
+  BatchHeader* hdr = (BatchHeader*)host_table;
+  FrameWork* fw = (FrameWork*)(host_table + sizeof(BatchHeader));
+  int tiles_u = 0, tiles_b = 0;
+  for (int i = 0; i < n; ++i) {
+    wrls_stream* s = frames[i].stream;
+    const StateDesc& pv = s->state[s->cur];
+    const StateDesc& nx = s->state[s->cur ^ 1];
+    FrameWork& w = fw[i];
+    w.maps = pv.maps;
+    w.stage_ok = pv.stage_ok ? 1 : 0;
+    w.err = s->err;
+    w.kp = s->kp;
+    w.prev_base = pv.base;
+    w.prev_scale = pv.scale;
+    w.next_base = nx.base;
+    w.next_scale = nx.scale;
+    w.plane_stride = pv.plane_stride;
+    w.rad = frames[i].radiance;
+    w.mot = frames[i].motion;
+    w.out = frames[i].out;
+    w.pitch = pv.pitch;
+    w.W = s->W;
+    w.H = s->H;
+    w.reset = s->need_reset ? 1 : 0;
+    w.tiles_x = (s->W + kTW - 1) / kTW;
+    w.begin_update = tiles_u;
+    w.begin_blend = tiles_b;
+    tiles_u += w.tiles_x * ((s->H + kTH - 1) / kTH);
+    tiles_b += w.tiles_x * ((s->H + th_b - 1) / th_b);
+  }
+  hdr->n = n;
+  hdr->total_update = tiles_u;
+  hdr->total_blend = tiles_b;
+  cudaStream_t cs = (cudaStream_t)cuda_stream;
+  int* counters = (int*)((unsigned char*)scratch + kStaticCountersOffset);
+  const size_t bytes = sizeof(BatchHeader) + (size_t)n * sizeof(FrameWork);
+  cudaError_t e = cudaMemcpyAsync(scratch, host_table, bytes, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), cs);
+  if (e == cudaSuccess) {
+    switch (prec) {
+      case 0: e = launch_static<StateF32>(mode, cfg, cs, scratch, counters); break;
+      case 1: e = launch_static<StateBF16>(mode, cfg, cs, scratch, counters); break;
+      default: e = launch_static<StateF16>(mode, cfg, cs, scratch, counters); break;
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("wrls_batch_tick_static: %s", cudaGetErrorString(e));
+    return WRLS_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    wrls_stream* s = frames[i].stream;
+    s->cur ^= 1;
+    s->need_reset = false;
+    s->has_frame = true;
+    s->frames++;
+  }
+  return WRLS_OK;
+}

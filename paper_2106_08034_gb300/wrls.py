@@ -38,6 +38,7 @@ EXPORTED = [
     "wrls_stream_enable_timing", "wrls_stream_kernel_times", "wrls_stream_check",
     "wrls_stream_autotune", "wrls_stream_set_blend_config",
     "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
+    "wrls_batch_tick_static",
 ]
 
 
@@ -99,6 +100,7 @@ def lib():
         "wrls_batch_set_cuda_stream": (i, [vp, vp]),
         "wrls_batch_tick": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
         "wrls_batch_destroy": (None, [vp]),
+        "wrls_batch_tick_static": (i, [ctypes.POINTER(wrls_frame_io), i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -233,6 +235,18 @@ def wrls_batch_tick(batch: int, frames: Sequence[tuple]) -> None:
     for k, (s, rad, var, feat, mot, out) in enumerate(frames):
         arr[k] = wrls_frame_io(s, _ptr(rad), _ptr(var), _ptr(feat), _ptr(mot), _ptr(out))
     _check(lib().wrls_batch_tick(batch, arr, len(frames)))
+
+
+STATIC_BATCH_MAX = 16
+
+
+def wrls_batch_tick_static(frames: Sequence[tuple], cuda_stream=None) -> None:
+    """The batched tick that allocates nothing (work table in a static device array).
+    frames: sequence of (stream, radiance, variance, features, motion, out)."""
+    arr = (wrls_frame_io * max(1, len(frames)))()
+    for k, (s, rad, var, feat, mot, out) in enumerate(frames):
+        arr[k] = wrls_frame_io(s, _ptr(rad), _ptr(var), _ptr(feat), _ptr(mot), _ptr(out))
+    _check(lib().wrls_batch_tick_static(arr, len(frames), _stream_handle(cuda_stream)))
 
 
 def wrls_batch_destroy(batch: Optional[int]) -> None:
