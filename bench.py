@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first N frames of the sequence (small profiling captures)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched BF16 16-stream leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--batched-passes", type=int, default=3)
     return ap.parse_args()
 
 
@@ -157,6 +161,99 @@ def cpu_oracle_rate(spec, seconds: float, frames_ring: int = 4):
     return n * spec.width * spec.height / dt / 1e6, n, dt, O.get_threads()
 
 
+def batched_leg(args, torch, W, synth, dev):
+    """16 concurrent streams of mixed sizes (mix16_60f), BF16 state, one graph-captured
+    persistent tick per frame index. Inputs: a ring of 8 generated frames per stream
+    (the kernels' work depends only on the resolution); 60 ticks per pass."""
+    specs = synth.mix16_60f()
+    ring = 8
+    cs = torch.cuda.Stream(device=dev)
+    data = []
+    for sp in specs:
+        sc = synth.Scene(sp)
+        rad = torch.empty(ring, 3, sp.height, sp.width, device=dev)
+        mot = torch.empty(ring, 2, sp.height, sp.width, device=dev)
+        for t in range(ring):
+            f = sc.frame(t, device=dev)
+            rad[t].copy_(f["radiance"])
+            mot[t].copy_(f["motion"])
+        data.append((rad, mot))
+    torch.cuda.synchronize()
+    params = W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
+    streams = [W.Stream(sp.width, sp.height, params, cuda_stream=cs) for sp in specs]
+    outs = [torch.empty(3, sp.height, sp.width, device=dev) for sp in specs]
+    batch = W.wrls_batch_create(len(specs))
+    W.wrls_batch_set_cuda_stream(batch, cs)
+    px = sum(sp.width * sp.height for sp in specs)
+
+    def tick(t):
+        W.wrls_batch_tick(batch, [(streams[i].handle, data[i][0][t % ring], None, None,
+                                   data[i][1][t % ring], outs[i]) for i in range(len(specs))])
+    for t in range(8):
+        tick(t)
+    cs.synchronize()
+    big = max(range(len(specs)), key=lambda i: specs[i].width * specs[i].height)
+    times, cfg = W.wrls_stream_autotune(streams[big].handle, outs[big], reps=3)
+    n_ticks = specs[0].frames * max(1, args.batched_passes)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_ticks)]
+    torch.cuda.synchronize()
+    for t in range(n_ticks):
+        ev[t][0].record(cs)
+        tick(t)
+        ev[t][1].record(cs)
+    ev[-1][1].synchronize()
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    per = sorted(a.elapsed_time(b) for a, b in ev)
+    for s in streams:
+        W.wrls_stream_check(s.handle)
+    W.wrls_batch_destroy(batch)
+    for s in streams:
+        s.close()
+    bytes_bf16 = 140
+    return {
+        "workload": ("mix16_60f: 16 streams (4x512^2, 4x1280x720, 4x1920x1080, 2x2560x1440, "
+                     "2x3840x2160), orbit motion, 5%% fireflies; %d ticks of 16 frames" % n_ticks),
+        "value": round(n_ticks * px / (total_ms / 1e3) / 1e6, 1), "unit": "Mpix/s",
+        "state": "bf16 (+ binary32 P scale), binary32 compute", "mpix_per_tick": round(px / 1e6, 3),
+        "tick_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4),
+                    "max": round(per[-1], 4)},
+        "frame_latency_note": "all 16 frames of a tick are released at its launch: frame latency = tick time",
+        "hbm_path_frac": round(bytes_bf16 * n_ticks * px / (total_ms / 1e3) / 1e9 / measured_peaks()[0], 4),
+        "blend_config": cfg, "launches_per_tick": 2,
+    }
+
+
+def bf16_error_statement(torch, W, synth, dev, frames=60):
+    """relMSE against the truth of the BF16-, FP16- and FP32-state paths on a 1280x720 orbit
+    sequence with fireflies, a transfer-function edit and a light move (GPU generated)."""
+    spec = synth.SceneSpec(1280, 720, frames, seed=77, motion="orbit", firefly_frac=0.05,
+                           tf_edit_frame=frames // 2, light_move_frame=(3 * frames) // 4)
+    sc = synth.Scene(spec)
+    fr = [sc.frame(t, device=dev) for t in range(frames)]
+    res = {}
+    outs = {}
+    for name, prec in [("f32", W.WRLS_STATE_F32), ("bf16", W.WRLS_STATE_BF16), ("f16", W.WRLS_STATE_F16)]:
+        s = W.Stream(spec.width, spec.height, W.wrls_params_default(state_precision=prec))
+        o = torch.empty(3, spec.height, spec.width, device=dev)
+        acc = 0.0
+        last = []
+        for f in fr:
+            s.denoise(f["radiance"], f["motion"], o)
+            t = f["truth"]
+            acc += float(((o - t) ** 2 / (t * t + 1e-2)).mean())
+            last.append(o.clone())
+        s.close()
+        res[name] = acc / frames
+        outs[name] = last
+    dev_bf16 = max(float(((a - b).abs().amax(0) / b.abs().amax(0).clamp_min(1e-2)).max())
+                   for a, b in zip(outs["bf16"], outs["f32"]))
+    return {"sequence": "1280x720 orbit, 60 frames, 5% fireflies, TF edit, light move",
+            "relmse_f32": round(res["f32"], 6), "relmse_bf16": round(res["bf16"], 6),
+            "relmse_f16": round(res["f16"], 6),
+            "bf16_over_f32": round(res["bf16"] / res["f32"], 5), "f16_over_f32": round(res["f16"] / res["f32"], 5),
+            "bf16_max_pixel_rel_dev_from_f32": round(dev_bf16, 5)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -238,7 +335,22 @@ def run_wrls(args):
         for _ in range(args.warmup):
             step()
     cs.synchronize()
+    # tile configuration of the two-kernel pipeline, then the fastest pipeline (untimed)
+    W.wrls_stream_set_pipeline(s.handle, 0)
     blend_times, blend_cfg = W.wrls_stream_autotune(s.handle, out, reps=5)
+    pipe_ms = {}
+    for pipeline in (0, 1, 2):
+        W.wrls_stream_set_pipeline(s.handle, pipeline)
+        step()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(cs)
+        step()
+        b.record(cs)
+        b.synchronize()
+        pipe_ms[pipeline] = a.elapsed_time(b) / T
+    best_pipeline = min(pipe_ms, key=pipe_ms.get)
+    W.wrls_stream_set_pipeline(s.handle, best_pipeline)
     W.wrls_stream_enable_timing(s.handle, True)
 
     clocks = ClockSampler(smi_device_id(torch, dev, local))
@@ -304,17 +416,34 @@ def run_wrls(args):
     peak, peak_kind = measured_peaks()
     upd_per = upd_ms / max(nfr, 1)
     bl_per = bl_ms / max(nfr, 1)
-    achieved = BYTES_UPDATE_F32 * px / (upd_per / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_update (reproject + Eq. 12-14 update)",
+    if best_pipeline == 0:
+        kname, kbytes = "k_update (reproject + Eq. 12-14 update; k_blend separate)", BYTES_UPDATE_F32
+    else:
+        kname, kbytes = "k_fused (reproject + Eq. 12-14 update + 5x5 blend, one launch)", BYTES_PATH_F32
+    achieved = kbytes * px / (upd_per / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "bytes_per_px": BYTES_UPDATE_F32,
-                "kernel_ms": {"update": round(upd_per, 5), "blend": round(bl_per, 5)},
+                "bytes_per_px": kbytes,
+                "kernel_ms": {"update" if best_pipeline == 0 else "fused": round(upd_per, 5),
+                              "blend": round(bl_per, 5)},
+                "pipeline": best_pipeline, "pipeline_ms_per_frame": {str(k): round(v, 5) for k, v in pipe_ms.items()},
                 "blend_autotune_ms": [round(t, 5) for t in blend_times], "blend_config": blend_cfg,
                 "path": {"bytes_per_px": BYTES_PATH_F32,
                          "achieved": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9, 1),
                          "frac": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9 / peak, 4)}}
+
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(args, torch, W, synth, dev)
+        batched["error"] = bf16_error_statement(torch, W, synth, dev)
+    serving = None
+    if not args.no_serve:
+        from paper_2106_08034_gb300 import serve
+        serving = serve.simulate(duration_s=args.serve_seconds)
+        serving["workload"] = ("Poisson viewer sessions (2/s, lifetime U[10,60] s, 720p/1080p/1440p/2160p, "
+                               "30-60 fps, <= 64 resident, BF16 state), warm-started at the stationary population")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -334,7 +463,8 @@ def run_wrls(args):
                        "l2": "inputs larger than L2: state ping-pong 2 x 207 MB per frame",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 2 * T * args.steps, "clocks": ck,
+            "batched_bf16": batched, "serving": serving,
+            "gpu_launches": (2 if best_pipeline == 0 else 1) * T * args.steps, "clocks": ck,
         }
         print(json.dumps(line), flush=True)
     s.close()

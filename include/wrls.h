@@ -144,18 +144,38 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst);
 uint64_t wrls_stream_frames(const wrls_stream* s);
 
 /*
- * Autotuner of the blend kernel's tile shape: times every blend tile configuration (output
- * tile rows x output rows per thread: 16x4, 8x4, 16x2, 32x4) on the stream's current state,
- * `reps` launches each (>= 1), on the stream's CUDA stream, and keeps the fastest for later
- * frames. All configurations give bitwise identical outputs. Requires one denoised frame;
- * `out` (device, 3 x H x W) is overwritten and ends up holding the current frame's output.
- * times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per launch and
- * *chosen (optional) the selected configuration. Synchronises the stream.
+ * Autotuner of the blend kernel's tile shape (two-kernel pipeline): times every blend tile
+ * configuration on the
+ * stream's current state, `reps` launches each (>= 1), on the stream's CUDA stream, and
+ * keeps the fastest for later frames. Configurations (output tile rows x output rows per
+ * thread): 0: 16x4, 1: 8x4, 2: 16x2, 3: 32x4 with one CTA per tile; 4: 16x4, 5: 8x4,
+ * 6: 16x2, 7: 8x2 with persistent CTAs that prefetch the next tile's window while blending
+ * (binary32 state only). All configurations give bitwise identical outputs. Requires one
+ * denoised frame; `out` (device, 3 x H x W) is overwritten and ends up holding the current
+ * frame's output. times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per
+ * launch (-1 for a configuration the state format does not offer) and *chosen (optional)
+ * the selected configuration. Synchronises the stream. The batched tick uses the
+ * one-CTA-per-tile configuration of the same tile shape.
  */
-#define WRLS_BLEND_CONFIGS 4
+#define WRLS_BLEND_CONFIGS 8
 wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen);
 
-/* Select a blend tile configuration (0..WRLS_BLEND_CONFIGS-1) directly. */
+/*
+ * Choose how wrls_denoise_frame runs a frame. 0 (default after create): an update kernel
+ * followed by a blend kernel (blend tile chosen by wrls_stream_set_blend_config /
+ * wrls_stream_autotune). 1 or 2: one persistent
+ * "wavefront" kernel that claims 32 x 8 update tiles in raster order and, a few tiles behind,
+ * blends 32 x 16 output tiles whose neighbourhoods are complete, so the memory-bound update
+ * of some tiles overlaps the arithmetic-bound blend of others and the blend reads the new
+ * state from L2 (1: each blend thread produces 2 rows, all 256 threads blend; 2: 4 rows,
+ * 128 threads blend with more register reuse and fewer CTAs per SM). Its inter-CTA waits are
+ * bounded (WRLS_ERR_TIMEOUT via wrls_stream_check). All give bitwise identical results.
+ * With the fused kernel the kernel timing reports the whole frame as the update time.
+ */
+wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused);
+
+/* Select a blend tile configuration (0..WRLS_BLEND_CONFIGS-1) directly; configurations
+ * 4-7 need the binary32 state (WRLS_ERR_INVALID_ARG otherwise). */
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config);
 
 /* Synchronise the stream's CUDA stream and report device-side failures of the frames

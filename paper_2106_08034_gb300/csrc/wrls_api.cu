@@ -219,16 +219,21 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
   s->prm = *p;
   s->kp = kp;
   cudaGetDevice(&s->device);
-  cudaError_t e = cudaMalloc(&s->mem, 2 * copy + 256);
+  // both state copies, then the error word (+0), the fused kernel's counters (+64) and tile
+  // flags (+256)
+  const size_t scratch = fused_scratch_bytes(width, height);
+  cudaError_t e = cudaMalloc(&s->mem, 2 * copy + scratch);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error("wrls_stream_create: cudaMalloc(%zu) failed: %s", 2 * copy + 256, cudaGetErrorString(e));
+    set_error("wrls_stream_create: cudaMalloc(%zu) failed: %s", 2 * copy + scratch, cudaGetErrorString(e));
     delete s;
     return e == cudaErrorMemoryAllocation ? WRLS_ERR_OOM : WRLS_ERR_CUDA;
   }
-  s->mem_bytes = 2 * copy + 256;
+  s->mem_bytes = 2 * copy + scratch;
   s->err = (int*)((char*)s->mem + 2 * copy);
-  e = cudaMemset(s->err, 0, sizeof(int));
+  s->work = (int*)((char*)s->mem + 2 * copy + 64);
+  s->flags = (int*)((char*)s->mem + 2 * copy + 256);
+  e = cudaMemset(s->err, 0, scratch);
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(s->mem);
@@ -293,10 +298,17 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
     ev = s->tev + 3 * s->t_pending;
     WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
   }
-  WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs),
-                  "wrls_denoise_frame: update kernel launch");
-  if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
-  WRLS_CHECK_CUDA(launch_blend(s->kp, s->blend_cfg, next, out, s->cs), "wrls_denoise_frame: blend kernel launch");
+  if (s->pipeline != 0) {
+    WRLS_CHECK_CUDA(launch_fused(s->pipeline, s->kp, prev, next, s->need_reset, radiance, motion, out, s->err, s->work,
+                                 s->flags, (int)((s->frames + 1) & 0x7fffffff), s->cs),
+                    "wrls_denoise_frame: fused kernel launch");
+    if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
+  } else {
+    WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs),
+                    "wrls_denoise_frame: update kernel launch");
+    if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
+    WRLS_CHECK_CUDA(launch_blend(s->kp, s->blend_cfg, next, out, s->cs), "wrls_denoise_frame: blend kernel launch");
+  }
   if (ev) {
     WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
     s->t_pending++;
@@ -370,9 +382,18 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst) {
 
 uint64_t wrls_stream_frames(const wrls_stream* s) { return s ? s->frames : 0; }
 
+wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused) {
+  if (!s || fused < 0 || fused > 2) {
+    set_error("wrls_stream_set_pipeline: bad stream or value %d (0 = two kernels, 1 or 2 = fused)", fused);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  s->pipeline = fused;
+  return WRLS_OK;
+}
+
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config) {
-  if (!s || config < 0 || config >= kBlendConfigs) {
-    set_error("wrls_stream_set_blend_config: bad stream or configuration %d", config);
+  if (!s || !blend_config_ok(config, s->prm.state_precision)) {
+    set_error("wrls_stream_set_blend_config: bad stream or configuration %d for this state format", config);
     return WRLS_ERR_INVALID_ARG;
   }
   s->blend_cfg = config;
@@ -394,6 +415,10 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
   float best_ms = 0.0f;
   cudaError_t e = cudaSuccess;
   for (int c = 0; c < kBlendConfigs && e == cudaSuccess; ++c) {
+    if (!blend_config_ok(c, cur.precision)) {
+      if (times_ms) times_ms[c] = -1.0f;
+      continue;
+    }
     e = launch_blend(s->kp, c, cur, out, s->cs);  // warm-up (and first-use setup)
     if (e == cudaSuccess) e = cudaEventRecord(e0, s->cs);
     for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_blend(s->kp, c, cur, out, s->cs);

@@ -15,7 +15,7 @@
 #include <new>
 
 #include "wrls_internal.h"
-#include "wrls_tiles.cuh"
+#include "wrls_fused.cuh"
 
 namespace wrls {
 
@@ -38,12 +38,17 @@ struct alignas(128) FrameWork {
   int tiles_x;       // tiles per row (32 pixels wide, both phases)
   int begin_update;  // first work item of this frame in the update list (32 x 8 tiles)
   int begin_blend;   // first work item of this frame in the blend list (32 x TH tiles)
+  int begin_fused;   // first work item of this frame in the fused list
+  int* flags;        // the stream's tile flags (fused kernel)
+  int epoch;         // the frame's flag stamp
+  int lag;           // fused kernel: blends trail their dependencies by this many items
 };
 
 struct alignas(128) BatchHeader {
   int n;
   int total_update;
   int total_blend;
+  int total_fused;
 };
 
 template <class SV> __device__ __forceinline__ SV make_view(void* base, float* scale, size_t ps, int pitch);
@@ -59,20 +64,26 @@ template <> __device__ __forceinline__ StateF16 make_view<StateF16>(void* base, 
 
 // Claim the next work item of a list; returns its tile index within its frame (or -1 when
 // the list is exhausted) and the frame in *frame.
-template <bool BLEND>
+// Lists: 0 = update tiles, 1 = blend tiles, 2 = fused items.
+template <int LIST>
+__device__ __forceinline__ int list_begin(const FrameWork& w) {
+  return LIST == 0 ? w.begin_update : (LIST == 1 ? w.begin_blend : w.begin_fused);
+}
+
+template <int LIST>
 __device__ __forceinline__ int next_item(const BatchHeader* __restrict__ hdr,
                                          const FrameWork* __restrict__ fw, int* counter,
                                          int* s_item, int* s_frame, int* frame) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const int t = atomicAdd(counter, 1);
-    const int total = BLEND ? hdr->total_blend : hdr->total_update;
+    const int total = LIST == 0 ? hdr->total_update : (LIST == 1 ? hdr->total_blend : hdr->total_fused);
     int f = -1;
     if (t < total) {
       int lo = 0, hi = hdr->n - 1;  // last frame whose list begins at or before t
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if ((BLEND ? fw[mid].begin_blend : fw[mid].begin_update) <= t) lo = mid; else hi = mid - 1;
+        if (list_begin<LIST>(fw[mid]) <= t) lo = mid; else hi = mid - 1;
       }
       f = lo;
     }
@@ -82,7 +93,7 @@ __device__ __forceinline__ int next_item(const BatchHeader* __restrict__ hdr,
   __syncthreads();
   *frame = *s_frame;
   if (*frame < 0) return -1;
-  return *s_item - (BLEND ? fw[*frame].begin_blend : fw[*frame].begin_update);
+  return *s_item - list_begin<LIST>(fw[*frame]);
 }
 
 // The tensor maps live in the work table (global memory written by a copy before the launch):
@@ -97,11 +108,12 @@ __global__ void __launch_bounds__(kTileThreads)
   extern __shared__ unsigned char dsmem[];
   UpdateSmem<SV>& sm = *reinterpret_cast<UpdateSmem<SV>*>(align128(dsmem));
   __shared__ int s_item, s_frame;
-  if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
   uint32_t phase = 0;
   for (;;) {
     int f;
-    const int lt = next_item<false>(hdr, fw, counters + 0, &s_item, &s_frame, &f);
+    const int lt = next_item<0>(hdr, fw, counters + 0, &s_item, &s_frame, &f);
     if (lt < 0) break;
     const FrameWork& w = fw[f];
     if (threadIdx.x == 0 && w.stage_ok) {
@@ -110,7 +122,7 @@ __global__ void __launch_bounds__(kTileThreads)
     }
     const SV prev = make_view<SV>(w.prev_base, w.prev_scale, w.plane_stride, w.pitch);
     const SV next = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
-    if (!update_tile(sm, phase, w.err, w.kp, w.W, w.H, w.reset != 0, w.stage_ok != 0, prev, next,
+    if (!update_tile(sm, &bar, phase, w.err, w.kp, w.W, w.H, w.reset != 0, w.stage_ok != 0, prev, next,
                      &w.maps, w.rad, w.mot, (lt % w.tiles_x) * kTW, (lt / w.tiles_x) * kTH))
       return;
   }
@@ -123,12 +135,40 @@ __global__ void __launch_bounds__(kTW * TH / R)
   __shared__ int s_item, s_frame;
   for (;;) {
     int f;
-    const int lt = next_item<true>(hdr, fw, counters + 1, &s_item, &s_frame, &f);
+    const int lt = next_item<1>(hdr, fw, counters + 1, &s_item, &s_frame, &f);
     if (lt < 0) break;
     const FrameWork& w = fw[f];
     const SV cur = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
     blend_tile<SV, TH, R, MODE>(sm_blend, w.kp, w.W, w.H, cur, w.out, (lt % w.tiles_x) * kTW,
                                 (lt / w.tiles_x) * TH);
+  }
+}
+
+// Fused wavefront over all frames of the tick: the frames' item lists are concatenated, so
+// every dependency of an item (same frame, smaller index) was claimed earlier.
+template <class SV, int MODE, int R, int MIN_CTAS>
+__global__ void __launch_bounds__(kTileThreads, MIN_CTAS)
+    k_batch_fused(const BatchHeader* __restrict__ hdr, const FrameWork* __restrict__ fw, int* counters) {
+  extern __shared__ unsigned char dsmem[];
+  unsigned char* base = align128(dsmem);
+  __shared__ int s_item, s_frame, s_ok;
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  uint32_t phase = 0;
+  for (;;) {
+    int f;
+    const int lt = next_item<2>(hdr, fw, counters + 2, &s_item, &s_frame, &f);
+    if (lt < 0) break;
+    const FrameWork& w = fw[f];
+    if (threadIdx.x == 0 && w.stage_ok) {
+      acquire_tensormap(&w.maps.planes);
+      if constexpr (SV::kHasScale) acquire_tensormap(&w.maps.scale);
+    }
+    const SV prev = make_view<SV>(w.prev_base, w.prev_scale, w.plane_stride, w.pitch);
+    const SV next = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
+    if (!fused_item<SV, MODE, R>(base, &bar, phase, &s_ok, lt, w.kp, w.W, w.H, w.reset != 0, w.stage_ok != 0, prev,
+                                 next, &w.maps, w.rad, w.mot, w.out, w.err, w.flags, w.epoch, w.lag))
+      break;
   }
 }
 
@@ -163,7 +203,7 @@ static cudaError_t capture_tick_cfg(cudaStream_t cap, const void* h_table, void*
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaMemcpyAsync(d_table, h_table, bytes, cudaMemcpyHostToDevice, cap);
-  cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), cap);
+  cudaMemsetAsync(d_counters, 0, 4 * sizeof(int), cap);
   k_batch_update<SV><<<gu, kTileThreads, ubytes, cap>>>(hdr, fw, d_counters);
   k_batch_blend<SV, TH, R, MODE><<<gb, nt, sbytes, cap>>>(hdr, fw, d_counters);
   e = cudaStreamEndCapture(cap, &g);
@@ -192,6 +232,42 @@ static cudaError_t capture_tick(int mode, int cfg, cudaStream_t cap, const void*
                    : capture_tick_mode<SV, 1>(cfg, cap, h, d, bytes, c, exec);
 }
 
+template <class SV, int MODE, int R, int MIN_CTAS>
+static cudaError_t capture_fused_v(cudaStream_t cap, const void* h_table, void* d_table, size_t bytes,
+                                   int* d_counters, cudaGraphExec_t* exec) {
+  constexpr int fbytes = fused_smem_bytes<SV>();
+  cudaError_t e = cudaFuncSetAttribute(k_batch_fused<SV, MODE, R, MIN_CTAS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, fbytes);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_fused<SV, MODE, R, MIN_CTAS>, kTileThreads, fbytes);
+  if (e != cudaSuccess) return e;
+  const int grid = sm_count() * (occ > 0 ? occ : 1);
+  const BatchHeader* hdr = (const BatchHeader*)d_table;
+  const FrameWork* fw = (const FrameWork*)((char*)d_table + sizeof(BatchHeader));
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaMemcpyAsync(d_table, h_table, bytes, cudaMemcpyHostToDevice, cap);
+  cudaMemsetAsync(d_counters, 0, 4 * sizeof(int), cap);
+  k_batch_fused<SV, MODE, R, MIN_CTAS><<<grid, kTileThreads, fbytes, cap>>>(hdr, fw, d_counters);
+  e = cudaStreamEndCapture(cap, &g);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+template <class SV>
+static cudaError_t capture_fused(int mode, int variant, cudaStream_t cap, const void* h, void* d, size_t bytes,
+                                 int* c, cudaGraphExec_t* exec) {
+  if (variant == 2)
+    return mode == 0 ? capture_fused_v<SV, 0, 4, 2>(cap, h, d, bytes, c, exec)
+                     : capture_fused_v<SV, 1, 4, 2>(cap, h, d, bytes, c, exec);
+  return mode == 0 ? capture_fused_v<SV, 0, 2, 3>(cap, h, d, bytes, c, exec)
+                   : capture_fused_v<SV, 1, 2, 3>(cap, h, d, bytes, c, exec);
+}
+
 static int blend_rows(int cfg) {
   switch (cfg) {
     case 1: return 8;
@@ -213,8 +289,11 @@ struct wrls_batch {
   int* d_counters = nullptr;
   void* h_table[2] = {nullptr, nullptr};
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  // graph per (pinned slot, precision, blend mode, blend tile configuration)
-  cudaGraphExec_t exec[2][3][2][kBlendConfigs] = {};
+  // graph per (pinned slot, precision, blend mode, blend tile configuration) for the
+  // two-kernel tick, and per (pinned slot, precision, blend mode, variant) for the fused tick
+  cudaGraphExec_t exec[2][3][2][kBlendSyncConfigs] = {};
+  cudaGraphExec_t exec_fused[2][3][2][2] = {};
+  int fused_ctas = 0;  // resident CTAs of the fused kernel (sets the blends' lag)
   int slot = 0;
   int device = 0;
 };
@@ -223,8 +302,12 @@ static void batch_free(wrls_batch* b) {
   for (int s = 0; s < 2; ++s) {
     for (int p = 0; p < 3; ++p)
       for (int m = 0; m < 2; ++m)
-        for (int c = 0; c < kBlendConfigs; ++c)
+        for (int c = 0; c < kBlendSyncConfigs; ++c)
           if (b->exec[s][p][m][c]) cudaGraphExecDestroy(b->exec[s][p][m][c]);
+    for (int p = 0; p < 3; ++p)
+      for (int m = 0; m < 2; ++m)
+        for (int v = 0; v < 2; ++v)
+          if (b->exec_fused[s][p][m][v]) cudaGraphExecDestroy(b->exec_fused[s][p][m][v]);
     if (b->ev[s]) cudaEventDestroy(b->ev[s]);
     if (b->h_table[s]) cudaFreeHost(b->h_table[s]);
   }
@@ -248,9 +331,10 @@ wrls_status wrls_batch_create(int max_streams, wrls_batch** out) {
   if (!b) { set_error("wrls_batch_create: host allocation failed"); return WRLS_ERR_OOM; }
   b->max_streams = max_streams;
   cudaGetDevice(&b->device);
+  b->fused_ctas = 3 * sm_count();
   b->table_bytes = sizeof(BatchHeader) + (size_t)max_streams * sizeof(FrameWork);
   cudaError_t e = cudaMalloc(&b->d_table, b->table_bytes);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counters, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counters, 4 * sizeof(int));
   for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
     e = cudaMallocHost(&b->h_table[s], b->table_bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[s], cudaEventDisableTiming);
@@ -305,16 +389,20 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
   if (e != cudaSuccess) { set_error("wrls_batch_tick: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
   BatchHeader* hdr = (BatchHeader*)b->h_table[slot];
   FrameWork* fw = (FrameWork*)((char*)b->h_table[slot] + sizeof(BatchHeader));
-  int cfg = 0;
+  int cfg = 0, pipeline = 1;
   {
     size_t most = 0;
     for (int i = 0; i < n; ++i) {
       const size_t px = (size_t)frames[i].stream->W * frames[i].stream->H;
-      if (px > most) { most = px; cfg = frames[i].stream->blend_cfg; }
+      if (px > most) {
+        most = px;
+        cfg = blend_sync_config(frames[i].stream->blend_cfg);
+        pipeline = frames[i].stream->pipeline;
+      }
     }
   }
   const int th_b = blend_rows(cfg);
-  int tiles_u = 0, tiles_b = 0;
+  int tiles_u = 0, tiles_b = 0, items_f = 0;
   for (int i = 0; i < n; ++i) {
     wrls_stream* s = frames[i].stream;
     const StateDesc& pv = s->state[s->cur];
@@ -339,20 +427,35 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
     w.tiles_x = (s->W + kTW - 1) / kTW;
     w.begin_update = tiles_u;
     w.begin_blend = tiles_b;
+    w.begin_fused = items_f;
+    w.flags = s->flags;
+    w.epoch = (int)((s->frames + 1) & 0x7fffffff);
     tiles_u += w.tiles_x * ((s->H + kTH - 1) / kTH);
     tiles_b += w.tiles_x * ((s->H + th_b - 1) / th_b);
+    w.lag = fused_lag(s->W, s->H, b->fused_ctas);
+    items_f += fused_items(s->W, s->H, w.lag);
   }
   hdr->n = n;
   hdr->total_update = tiles_u;
   hdr->total_blend = tiles_b;
-  cudaGraphExec_t& ex = b->exec[slot][prec][mode][cfg];
+  hdr->total_fused = items_f;
+  cudaGraphExec_t& ex = pipeline != 0 ? b->exec_fused[slot][prec][mode][pipeline == 2 ? 1 : 0]
+                                      : b->exec[slot][prec][mode][cfg];
   if (!ex) {
     const size_t bytes = b->table_bytes;
     void* h = b->h_table[slot];
-    switch (prec) {
-      case 0: e = capture_tick<StateF32>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-      case 1: e = capture_tick<StateBF16>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-      default: e = capture_tick<StateF16>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+    if (pipeline != 0) {
+      switch (prec) {
+        case 0: e = capture_fused<StateF32>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+        case 1: e = capture_fused<StateBF16>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+        default: e = capture_fused<StateF16>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+      }
+    } else {
+      switch (prec) {
+        case 0: e = capture_tick<StateF32>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+        case 1: e = capture_tick<StateBF16>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+        default: e = capture_tick<StateF16>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+      }
     }
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -501,7 +604,7 @@ extern "C" wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n
   size_t most = 0;
   for (int i = 0; i < n; ++i) {
     const size_t px = (size_t)frames[i].stream->W * frames[i].stream->H;
-    if (px > most) { most = px; cfg = frames[i].stream->blend_cfg; }
+    if (px > most) { most = px; cfg = blend_sync_config(frames[i].stream->blend_cfg); }
   }
   const int th_b = blend_rows(cfg);
   // The table is built on the stack and copied with cudaMemcpyAsync from pageable memory,

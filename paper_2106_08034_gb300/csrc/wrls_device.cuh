@@ -134,6 +134,12 @@ struct StateF32 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) z[c] = __ldg(base + (kZ + c) * plane_stride + idx);
   }
+  __device__ __forceinline__ void load_beta_z_l2(size_t idx, float b[12], float z[3]) const {
+#pragma unroll
+    for (int p = 0; p < 12; ++p) b[p] = __ldcg(base + p * plane_stride + idx);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z[c] = __ldcg(base + (kZ + c) * plane_stride + idx);
+  }
   __device__ __forceinline__ void store(size_t idx, const float v[kNState]) const {
 #pragma unroll
     for (int p = 0; p < kNState; ++p) base[p * plane_stride + idx] = v[p];
@@ -174,6 +180,14 @@ struct State16 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) z[c] = to_f(base[(kZ + c) * plane_stride + idx]);
   }
+  __device__ __forceinline__ void load_beta_z_l2(size_t idx, float b[12], float z[3]) const {
+    const unsigned short* u = (const unsigned short*)base;
+#pragma unroll
+    for (int p = 0; p < 12; ++p) b[p] = to_f(from_bits(__ldcg(u + p * plane_stride + idx)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z[c] = to_f(from_bits(__ldcg(u + (kZ + c) * plane_stride + idx)));
+  }
+  static __device__ __forceinline__ T from_bits(unsigned short v);
   // Staged window: [plane][kStageH][kStageW] 16-bit values, then (128-byte aligned) the
   // [kStageH][kStageW] binary32 P scales; box origin x multiple of 8 (16 B).
   static constexpr int kAlignX = 8;
@@ -206,6 +220,10 @@ struct State16 {
 template <> __device__ __forceinline__ float State16<__nv_bfloat16>::to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 State16<__nv_bfloat16>::from_f(float v) { return __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ float State16<__half>::to_f(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 State16<__nv_bfloat16>::from_bits(unsigned short v) {
+  return __ushort_as_bfloat16(v);
+}
+template <> __device__ __forceinline__ __half State16<__half>::from_bits(unsigned short v) { return __ushort_as_half(v); }
 template <> __device__ __forceinline__ __half State16<__half>::from_f(float v) { return __float2half_rn(v); }
 
 using StateBF16 = State16<__nv_bfloat16>;

@@ -13,10 +13,11 @@ __global__ void __launch_bounds__(kTileThreads)
              const SV prev, const SV next, const __grid_constant__ StageMaps maps,
              const float* __restrict__ rad, const float* __restrict__ mot, int* err) {
   extern __shared__ unsigned char dsmem[];
+  __shared__ alignas(8) uint64_t bar;
   UpdateSmem<SV>& sm = *reinterpret_cast<UpdateSmem<SV>*>(align128(dsmem));
-  if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
   uint32_t phase = 0;
-  update_tile(sm, phase, err, kp, W, H, reset != 0, stage_ok != 0, prev, next, &maps, rad, mot,
+  update_tile(sm, &bar, phase, err, kp, W, H, reset != 0, stage_ok != 0, prev, next, &maps, rad, mot,
               blockIdx.x * kTW, blockIdx.y * kTH);
 }
 
@@ -101,6 +102,7 @@ static cudaError_t launch_blend_sv(const KParams& kp, int cfg, const SV& cur, in
 }
 
 cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs) {
+  if (cfg >= kBlendSyncConfigs) return launch_blend_pipelined(kp, cfg - kBlendSyncConfigs, cur, out, cs);
   switch (cur.precision) {
     case 0: return launch_blend_sv(kp, cfg, cur.f32(), cur.W, cur.H, out, cs);
     case 1: return launch_blend_sv(kp, cfg, cur.bf16(), cur.W, cur.H, out, cs);

@@ -37,11 +37,28 @@ cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateD
                           const float* rad, const float* mot, int* err, cudaStream_t cs);
 // Encode the TMA tensor maps of a state copy (sets stage_ok; false only on a driver error).
 bool encode_stage_maps(StateDesc& d, const char** why);
-// Blend tile configurations (tile rows TH, output rows per thread R):
-// 0: 16 x 4 (default), 1: 8 x 4, 2: 16 x 2, 3: 32 x 4.
-constexpr int kBlendConfigs = 4;
+// Blend tile configurations (tile rows TH x output rows per thread R):
+// 0: 16x4 (default), 1: 8x4, 2: 16x2, 3: 32x4 -- one CTA per tile, synchronous fill;
+// 4: 16x4, 5: 8x4, 6: 16x2, 7: 8x2 -- persistent, pipelined fill (binary32 state only).
+constexpr int kBlendConfigs = 8;
+constexpr int kBlendSyncConfigs = 4;
+inline bool blend_config_ok(int cfg, int precision) {
+  return cfg >= 0 && cfg < kBlendConfigs && (cfg < kBlendSyncConfigs || precision == 0);
+}
+// The synchronous configuration with the same tile shape (used by the batched tick).
+inline int blend_sync_config(int cfg) {
+  static const int map[kBlendConfigs] = {0, 1, 2, 3, 0, 1, 2, 1};
+  return (cfg >= 0 && cfg < kBlendConfigs) ? map[cfg] : 0;
+}
 cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs);
+cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs);
 cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs);
+// Fused wavefront kernel (update + blend in one persistent launch).
+size_t fused_scratch_bytes(int W, int H);
+// variant 1: blend with 2 rows per thread (all threads), 3 CTAs/SM; 2: 4 rows per thread, 2 CTAs/SM.
+cudaError_t launch_fused(int variant, const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
+                         const float* rad, const float* mot, float* out, int* err, int* work, int* flags,
+                         int epoch, cudaStream_t cs);
 
 void set_error(const char* fmt, ...);
 
@@ -55,6 +72,9 @@ struct wrls_stream {
   wrls::StateDesc state[2];
   void* mem = nullptr;          // both state copies, then the device error word
   int* err = nullptr;           // device error word (WRLS_ERR_TIMEOUT from a bounded wait)
+  int* work = nullptr;          // fused kernel: item and exit counters (zero between launches)
+  int* flags = nullptr;         // fused kernel: per-update-tile done flags (frame epochs)
+  int pipeline = 0;             // 0 = update kernel + blend kernel; 1, 2 = fused kernel variants
   size_t mem_bytes = 0;
   int cur = 0;                  // copy holding frame t-1
   bool need_reset = true;

@@ -22,14 +22,14 @@ constexpr int kTH = 8;
 constexpr int kTileThreads = kTW * kTH;
 
 // Shared memory of an update tile: the staged previous-state window, the radiance tile with a
-// 1-pixel halo, the tap-footprint reduction and the copy's mbarrier.
+// 1-pixel halo and the tap-footprint reduction. (The copy's mbarrier lives outside, so that a
+// fused kernel may reuse this space for a blend window between tiles.)
 template <class SV>
 struct UpdateSmem {
   alignas(128) unsigned char stage[SV::kStageBytes];
   float rad[3][kTH + 2][kTW + 2];
   int red[kTileThreads / 32][4];
   int box[4];
-  alignas(8) uint64_t bar;
 };
 template <class SV>
 constexpr int update_smem_bytes() { return (int)sizeof(UpdateSmem<SV>) + 128; }  // + alignment slack
@@ -39,10 +39,10 @@ constexpr int update_smem_bytes() { return (int)sizeof(UpdateSmem<SV>) + 128; } 
 // of every state plane into shared memory with a TMA bulk tensor copy (completion on the
 // mbarrier) while all threads stage the radiance tile; the taps are then read from shared
 // memory. Otherwise (large motion spread) the taps are read from global memory.
-// `phase` is the CTA's mbarrier phase. Returns false if the bounded wait for the copy gave up
-// (the error word is set; the caller must return).
+// `bar` is the CTA's mbarrier (count 1) and `phase` its current phase. Returns false if the
+// bounded wait for the copy gave up (the error word is set; the caller must return).
 template <class SV>
-__device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint32_t& phase, int* err,
+__device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint64_t* bar, uint32_t& phase, int* err,
                                            const KParams& kp, const int W, const int H,
                                            const bool reset, const bool stage_ok, const SV& prev,
                                            const SV& next, const StageMaps* maps,
@@ -97,9 +97,9 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint32_t& phase,
     sm.box[0] = X0; sm.box[1] = Y0; sm.box[2] = fits;
     if (fits) {
       fence_proxy_async();
-      mbar_expect_tx(&sm.bar, SV::kTxBytes);
-      tma_load_3d(sm.stage, &maps->planes, X0, Y0, 0, &sm.bar);
-      if constexpr (SV::kHasScale) tma_load_2d(sm.stage + SV::kScaleOffset, &maps->scale, X0, Y0, &sm.bar);
+      mbar_expect_tx(bar, SV::kTxBytes);
+      tma_load_3d(sm.stage, &maps->planes, X0, Y0, 0, bar);
+      if constexpr (SV::kHasScale) tma_load_2d(sm.stage + SV::kScaleOffset, &maps->scale, X0, Y0, bar);
     }
   }
   // radiance tile with a 1-pixel halo (out-of-image = NaN, skipped by the clamp)
@@ -121,10 +121,10 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint32_t& phase,
   const int X0 = sm.box[0], Y0 = sm.box[1];
   const bool fits = sm.box[2] != 0;
   bool ok = true;
-  if (fits) ok = mbar_wait_bounded(&sm.bar, phase);
+  if (fits) ok = mbar_wait_bounded(bar, phase);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) atomicExch(err, (int)WRLS_ERR_TIMEOUT);
-    mbar_wait_bounded(&sm.bar, phase);  // the copy may still be in flight
+    mbar_wait_bounded(bar, phase);  // the copy may still be in flight
     return false;
   }
   if (fits) phase ^= 1u;
@@ -186,18 +186,20 @@ struct BlendGeom {
 };
 
 // Fill the shared window of the blend tile at (bx0, by0) from the state copy `cur`.
-template <class SV, int TH, int NT>
+// COHERENT: read through L2 only (the state was written by other CTAs of the same launch).
+template <class SV, int TH, int NT, bool COHERENT = false, int UNROLL = 4>
 __device__ __forceinline__ void blend_fill(float4* __restrict__ sb, float4* __restrict__ szr,
                                            const KParams& kp, const int W, const int H, const SV& cur,
                                            const int bx0, const int by0) {
   constexpr int R0 = kMaxRadius;
-#pragma unroll 4
+#pragma unroll UNROLL
   for (int i = threadIdx.x; i < BlendGeom<TH>::kPix; i += NT) {
     const int ly = i / kBlendSW, lx = i % kBlendSW;
     const int gx = bx0 - R0 + lx, gy = by0 - R0 + ly;
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
       float b[12], z[3];
-      cur.load_beta_z((size_t)gy * cur.pitch + gx, b, z);
+      if constexpr (COHERENT) cur.load_beta_z_l2((size_t)gy * cur.pitch + gx, b, z);
+      else cur.load_beta_z((size_t)gy * cur.pitch + gx, b, z);
       const float r = 1.0f / (sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]) + kp.eps);
       sb[3 * i + 0] = make_float4(b[0], b[1], b[2], b[3]);
       sb[3 * i + 1] = make_float4(b[4], b[5], b[6], b[7]);

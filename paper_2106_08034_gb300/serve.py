@@ -174,6 +174,12 @@ class Server:
         for sid in [sid for sid, s in self.active.items() if s.in_flight == 0 and now >= s.depart]:
             self.depart(sid, now)
 
+    def snapshot(self) -> Dict[int, Tuple[int, int, int, torch.Tensor]]:
+        """Synchronise; {sid: (width, height, frames processed, copy of the last output)}."""
+        self.cs.synchronize()
+        self.poll(time.perf_counter())
+        return {sid: (s.width, s.height, s.processed, s.out.clone()) for sid, s in self.active.items()}
+
     def close(self) -> None:
         self.cs.synchronize()
         for s in list(self.active.values()):

@@ -23,11 +23,13 @@ def _built():
     W.lib()
 
 
-def run_pair(frames, width, height, params=None, hooks=None, check_z=True, tol=REL_TOL):
+def run_pair(frames, width, height, params=None, hooks=None, check_z=True, tol=REL_TOL, pipeline=None):
     """Denoise the frames with the GPU and with the oracle; assert parity every frame.
     Returns the per-frame max relative errors."""
     p = params if params is not None else W.wrls_params_default()
     s = W.Stream(width, height, p)
+    if pipeline is not None:
+        W.wrls_stream_set_pipeline(s.handle, pipeline)
     st = O.OracleStream(width, height, oracle_params_from(p))
     out = torch.empty(3, height, width, device="cuda")
     zbuf = torch.empty(W.N_STATE, height, width, device="cuda")
@@ -135,13 +137,16 @@ def test_host_entry_matches_device_entry():
         assert torch.equal(od.cpu(), oh)
 
 
-def test_batch_tick_equals_each_stream_alone():
+@pytest.mark.parametrize("pipeline", [0, 1, 2])
+def test_batch_tick_equals_each_stream_alone(pipeline):
     sizes = [(64, 48), (100, 33), (257, 129), (31, 7), (128, 128)]
     specs = [synth.SceneSpec(w, h, 5, seed=40 + i, motion="orbit", firefly_frac=0.05)
              for i, (w, h) in enumerate(sizes)]
     frames = [cpu_frames(sp) for sp in specs]
     alone = [W.Stream(w, h) for (w, h) in sizes]
     mixed = [W.Stream(w, h) for (w, h) in sizes]
+    for s in alone + mixed:
+        W.wrls_stream_set_pipeline(s.handle, pipeline)
     batch = W.wrls_batch_create(8)
     try:
         for t in range(5):
@@ -189,6 +194,7 @@ def test_blend_configs_bitwise_identical_and_autotune():
     outs = []
     for cfg in range(W.BLEND_CONFIGS):
         s = W.Stream(spec.width, spec.height)
+        W.wrls_stream_set_pipeline(s.handle, 0)
         W.wrls_stream_set_blend_config(s.handle, cfg)
         o = torch.empty(3, spec.height, spec.width, device="cuda")
         for f in fr:
@@ -206,12 +212,13 @@ def test_blend_configs_bitwise_identical_and_autotune():
         assert torch.equal(o, outs[0])
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5, 6, 7])
 def test_blend_configs_match_oracle(cfg):
     spec = synth.SceneSpec(97, 53, 5, seed=51, motion="pan", firefly_frac=0.05)
     p = W.wrls_params_default()
     fr = cpu_frames(spec)
     s = W.Stream(spec.width, spec.height, p)
+    W.wrls_stream_set_pipeline(s.handle, 0)
     W.wrls_stream_set_blend_config(s.handle, cfg)
     st = O.OracleStream(spec.width, spec.height, oracle_params_from(p))
     out = torch.empty(3, spec.height, spec.width, device="cuda")
@@ -238,6 +245,49 @@ def test_staged_and_global_gather_paths(kind):
             mot.copy_((torch.rand(2, 96, 160, generator=g) - 0.5) * 12.0)
         return rad, mot
     run_pair(fr, 160, 96, hooks=hooks)
+
+
+@pytest.mark.parametrize("pipeline", [0, 1, 2])
+def test_pipelines_match_oracle(pipeline):
+    spec = synth.SceneSpec(181, 95, 24, seed=56, motion="pan", firefly_frac=0.05)
+    run_pair(cpu_frames(spec), spec.width, spec.height, pipeline=pipeline)
+
+
+@pytest.mark.parametrize("precision", [W.WRLS_STATE_F32, W.WRLS_STATE_BF16])
+def test_pipelines_bitwise_identical(precision):
+    """Two kernels, and both fused-kernel variants, give identical outputs and states."""
+    spec = synth.SceneSpec(333, 200, 6, seed=57, motion="orbit", firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    res = []
+    for pipeline in (0, 1, 2):
+        s = W.Stream(spec.width, spec.height, W.wrls_params_default(state_precision=precision))
+        W.wrls_stream_set_pipeline(s.handle, pipeline)
+        o = torch.empty(3, spec.height, spec.width, device="cuda")
+        st = torch.empty(W.N_STATE, spec.height, spec.width, device="cuda")
+        for f in fr:
+            s.denoise(f["radiance"].cuda(), f["motion"].cuda(), o)
+        s.read_state(st)
+        W.wrls_stream_check(s.handle)
+        torch.cuda.synchronize()
+        res.append((o.clone(), st.clone()))
+        s.close()
+    for o, st in res[1:]:
+        assert torch.equal(o, res[0][0]) and torch.equal(st, res[0][1])
+
+
+def test_pipelined_blend_rejected_for_16bit_state():
+    s = W.Stream(64, 64, W.wrls_params_default(state_precision=W.WRLS_STATE_BF16))
+    W.wrls_stream_set_pipeline(s.handle, 0)
+    with pytest.raises(W.WrlsError):
+        W.wrls_stream_set_blend_config(s.handle, 4)
+    W.wrls_stream_set_blend_config(s.handle, 3)
+    o = torch.empty(3, 64, 64, device="cuda")
+    spec = synth.SceneSpec(64, 64, 2, seed=55, motion="orbit")
+    for f in cpu_frames(spec):
+        s.denoise(f["radiance"].cuda(), f["motion"].cuda(), o)
+    times, chosen = W.wrls_stream_autotune(s.handle, o, reps=1)
+    assert all(t < 0 for t in times[4:]) and chosen < 4
+    s.close()
 
 
 def test_stream_check_reports_ok():
