@@ -339,7 +339,7 @@ def run_wrls(args):
     W.wrls_stream_set_pipeline(s.handle, 0)
     blend_times, blend_cfg = W.wrls_stream_autotune(s.handle, out, reps=5)
     pipe_ms = {}
-    for pipeline in (0, 1, 2):
+    for pipeline in (0, 1, 2, 3):
         W.wrls_stream_set_pipeline(s.handle, pipeline)
         step()
         a = torch.cuda.Event(enable_timing=True)
@@ -416,8 +416,10 @@ def run_wrls(args):
     peak, peak_kind = measured_peaks()
     upd_per = upd_ms / max(nfr, 1)
     bl_per = bl_ms / max(nfr, 1)
-    if best_pipeline == 0:
-        kname, kbytes = "k_update (reproject + Eq. 12-14 update; k_blend separate)", BYTES_UPDATE_F32
+    if best_pipeline in (0, 3):
+        kname = ("k_update" if best_pipeline == 0 else "k_update_pipe") + \
+            " (reproject + Eq. 12-14 update; the blend is a separate kernel)"
+        kbytes = BYTES_UPDATE_F32
     else:
         kname, kbytes = "k_fused (reproject + Eq. 12-14 update + 5x5 blend, one launch)", BYTES_PATH_F32
     achieved = kbytes * px / (upd_per / 1e3) / 1e9
@@ -426,7 +428,7 @@ def run_wrls(args):
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "bytes_per_px": kbytes,
-                "kernel_ms": {"update" if best_pipeline == 0 else "fused": round(upd_per, 5),
+                "kernel_ms": {"update" if best_pipeline in (0, 3) else "fused": round(upd_per, 5),
                               "blend": round(bl_per, 5)},
                 "pipeline": best_pipeline, "pipeline_ms_per_frame": {str(k): round(v, 5) for k, v in pipe_ms.items()},
                 "blend_autotune_ms": [round(t, 5) for t in blend_times], "blend_config": blend_cfg,
@@ -464,7 +466,7 @@ def run_wrls(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "batched_bf16": batched, "serving": serving,
-            "gpu_launches": (2 if best_pipeline == 0 else 1) * T * args.steps, "clocks": ck,
+            "gpu_launches": (2 if best_pipeline in (0, 3) else 1) * T * args.steps, "clocks": ck,
         }
         print(json.dumps(line), flush=True)
     s.close()

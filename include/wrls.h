@@ -148,9 +148,10 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
  * configuration on the
  * stream's current state, `reps` launches each (>= 1), on the stream's CUDA stream, and
  * keeps the fastest for later frames. Configurations (output tile rows x output rows per
- * thread): 0: 16x4, 1: 8x4, 2: 16x2, 3: 32x4 with one CTA per tile; 4: 16x4, 5: 8x4,
- * 6: 16x2, 7: 8x2 with persistent CTAs that prefetch the next tile's window while blending
- * (binary32 state only). All configurations give bitwise identical outputs. Requires one
+ * thread): 0: 16x4, 1: 8x4, 2: 16x2, 3: 32x4 with one CTA per tile; 4: 16x2, 5: 16x2,
+ * 6: 8x2, 7: 16x4 with persistent CTAs whose windows are filled by TMA bulk tensor copies,
+ * double-buffered (4, 6: the next window arrives while the current one is blended) or single
+ * (5, 7: more CTAs per SM) (binary32 state, images of at least 40 x 20 pixels). All configurations give bitwise identical outputs. Requires one
  * denoised frame; `out` (device, 3 x H x W) is overwritten and ends up holding the current
  * frame's output. times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per
  * launch (-1 for a configuration the state format does not offer) and *chosen (optional)
@@ -169,7 +170,9 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
  * of some tiles overlaps the arithmetic-bound blend of others and the blend reads the new
  * state from L2 (1: each blend thread produces 2 rows, all 256 threads blend; 2: 4 rows,
  * 128 threads blend with more register reuse and fewer CTAs per SM). Its inter-CTA waits are
- * bounded (WRLS_ERR_TIMEOUT via wrls_stream_check). All give bitwise identical results.
+ * bounded (WRLS_ERR_TIMEOUT via wrls_stream_check). 3: as 0, with a persistent update kernel
+ * that prefetches each tile's motion, radiance and state window (TMA) while the tile before it
+ * is being updated. The batched tick runs pipeline 3 as 0. All give bitwise identical results.
  * With the fused kernel the kernel timing reports the whole frame as the update time.
  */
 wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused);

@@ -20,8 +20,11 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libwrls.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "-I", os.path.join(ROOT, "include")]
+# -prec-div=false / -prec-sqrt=false: division and square root by the approximate SFU
+# sequences (relative error ~1e-7, far inside the 1e-3 parity tolerance). Denormals are
+# kept (no -ftz) so binary32 decisions such as q >= 0 are taken on unflushed values.
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-prec-div=false", "-prec-sqrt=false",
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include")]
 
 
 def nvcc() -> str:

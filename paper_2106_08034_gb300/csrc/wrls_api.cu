@@ -57,7 +57,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 bool encode_stage_maps(StateDesc& d, const char** why) {
   d.stage_ok = false;
+  d.blend_tma_ok = false;
   memset(&d.maps, 0, sizeof(d.maps));
+  memset(&d.bmaps, 0, sizeof(d.bmaps));
   if (d.pitch < kStageW || d.H < kStageH) return true;  // smaller images read taps from global memory
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) { *why = "cuTensorMapEncodeTiled is not available from the driver"; return false; }
@@ -81,6 +83,19 @@ bool encode_stage_maps(StateDesc& d, const char** why) {
     if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for the P-scale plane"; return false; }
   }
   d.stage_ok = true;
+  if (f32 && d.H >= 20) {
+    const cuuint32_t bb16[3] = {(cuuint32_t)kBlendBoxW, 20, 12}, bz16[3] = {(cuuint32_t)kBlendBoxW, 20, 3};
+    const cuuint32_t bb8[3] = {(cuuint32_t)kBlendBoxW, 12, 12}, bz8[3] = {(cuuint32_t)kBlendBoxW, 12, 3};
+    CUtensorMap* m[4] = {&d.bmaps.beta16, &d.bmaps.z16, &d.bmaps.beta8, &d.bmaps.z8};
+    const cuuint32_t* bx[4] = {bb16, bz16, bb8, bz8};
+    for (int i = 0; i < 4; ++i) {
+      r = enc(m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, d.base, dims, strides, bx[i], es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for a blend window"; return false; }
+    }
+    d.blend_tma_ok = true;
+  }
   return true;
 }
 
@@ -298,16 +313,21 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
     ev = s->tev + 3 * s->t_pending;
     WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
   }
-  if (s->pipeline != 0) {
+  if (s->pipeline == 1 || s->pipeline == 2) {
     WRLS_CHECK_CUDA(launch_fused(s->pipeline, s->kp, prev, next, s->need_reset, radiance, motion, out, s->err, s->work,
                                  s->flags, (int)((s->frames + 1) & 0x7fffffff), s->cs),
                     "wrls_denoise_frame: fused kernel launch");
     if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
   } else {
-    WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs),
-                    "wrls_denoise_frame: update kernel launch");
+    if (s->pipeline == 3)
+      WRLS_CHECK_CUDA(launch_update_pipelined(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs),
+                      "wrls_denoise_frame: update kernel launch");
+    else
+      WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs),
+                      "wrls_denoise_frame: update kernel launch");
     if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
-    WRLS_CHECK_CUDA(launch_blend(s->kp, s->blend_cfg, next, out, s->cs), "wrls_denoise_frame: blend kernel launch");
+    WRLS_CHECK_CUDA(launch_blend(s->kp, s->blend_cfg, next, out, s->err, s->cs),
+                    "wrls_denoise_frame: blend kernel launch");
   }
   if (ev) {
     WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
@@ -383,8 +403,8 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst) {
 uint64_t wrls_stream_frames(const wrls_stream* s) { return s ? s->frames : 0; }
 
 wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused) {
-  if (!s || fused < 0 || fused > 2) {
-    set_error("wrls_stream_set_pipeline: bad stream or value %d (0 = two kernels, 1 or 2 = fused)", fused);
+  if (!s || fused < 0 || fused > 3) {
+    set_error("wrls_stream_set_pipeline: bad stream or value %d (0, 3 = two kernels, 1, 2 = fused)", fused);
     return WRLS_ERR_INVALID_ARG;
   }
   s->pipeline = fused;
@@ -392,7 +412,7 @@ wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused) {
 }
 
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config) {
-  if (!s || !blend_config_ok(config, s->prm.state_precision)) {
+  if (!s || !blend_config_ok(config, s->prm.state_precision, s->state[0].blend_tma_ok)) {
     set_error("wrls_stream_set_blend_config: bad stream or configuration %d for this state format", config);
     return WRLS_ERR_INVALID_ARG;
   }
@@ -415,13 +435,13 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
   float best_ms = 0.0f;
   cudaError_t e = cudaSuccess;
   for (int c = 0; c < kBlendConfigs && e == cudaSuccess; ++c) {
-    if (!blend_config_ok(c, cur.precision)) {
+    if (!blend_config_ok(c, cur.precision, cur.blend_tma_ok)) {
       if (times_ms) times_ms[c] = -1.0f;
       continue;
     }
-    e = launch_blend(s->kp, c, cur, out, s->cs);  // warm-up (and first-use setup)
+    e = launch_blend(s->kp, c, cur, out, s->err, s->cs);  // warm-up (and first-use setup)
     if (e == cudaSuccess) e = cudaEventRecord(e0, s->cs);
-    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_blend(s->kp, c, cur, out, s->cs);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_blend(s->kp, c, cur, out, s->err, s->cs);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s->cs);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.0f;
@@ -430,7 +450,7 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
     if (times_ms) times_ms[c] = ms;
     if (c == 0 || ms < best_ms) { best = c; best_ms = ms; }
   }
-  if (e == cudaSuccess) e = launch_blend(s->kp, best, cur, out, s->cs);
+  if (e == cudaSuccess) e = launch_blend(s->kp, best, cur, out, s->err, s->cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -397,7 +397,7 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
       if (px > most) {
         most = px;
         cfg = blend_sync_config(frames[i].stream->blend_cfg);
-        pipeline = frames[i].stream->pipeline;
+        pipeline = frames[i].stream->pipeline == 3 ? 0 : frames[i].stream->pipeline;
       }
     }
   }

@@ -1,136 +1,230 @@
-// Persistent, software-pipelined blend for the binary32 state.
+// Persistent blend with TMA double-buffered windows (binary32 state).
 //
 // Same arithmetic and neighbour order as k_blend (wrls_tiles.cuh: blend_compute), hence
 // bitwise identical outputs. Each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// and keeps two shared windows: while it blends tile i from one window, the 4-byte cp.async
-// copies of tile i+1's window (12 beta and 3 z planes, written straight into the per-pixel
-// records) are in flight into the other. The copies hold no registers, so the fill latency
-// hides behind the blend arithmetic. When a window has landed, one pass computes each
-// record's 1/(|z|+eps). Window pixels outside the image are written directly as far records
-// (beta = 0, z = kFarZ), whose weights are exactly 0.
+// and keeps two shared windows. While it blends tile i from one window, two bulk tensor
+// copies (cp.async.bulk.tensor.3d: the 12 beta planes and the 3 z planes of the 40 x (TH+4)
+// box around tile i+1) fill the other, completion tracked by that window's mbarrier; no
+// thread spends an instruction or a register per loaded value. When a window has landed, one
+// pass computes every pixel's rk = K / (|z|+eps)^2 (K = log2(e) / h_s^2) and turns pixels outside
+// the image (zero-filled by the copy, or pitch padding) into far records (beta = 0,
+// z = kFarZ, rk = 0), whose blend weights are exactly 0. The blend then reads the window's
+// planes directly (structure of arrays: a warp's loads are 32 consecutive floats).
+// Waits are bounded (kWaitLimit clocks); on expiry the CTA records WRLS_ERR_TIMEOUT, waits
+// (bounded) for its copies in flight and returns.
 #include "wrls_internal.h"
 #include "wrls_tiles.cuh"
 
 namespace wrls {
 
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+template <int TH>
+struct TmaBlendGeom {
+  static constexpr int SH = TH + 2 * kMaxRadius;
+  static constexpr int PLANE = SH * kBlendBoxW;   // floats per plane of a window
+  static constexpr int BUF = 16 * PLANE;          // 12 beta + 3 z + rk planes
+  static constexpr uint32_t kTx = 15u * PLANE * 4u;
+  static constexpr int smem_bytes(int nbuf) { return nbuf * BUF * 4 + 128; }
+};
 
-template <int TH, int NT>
-__device__ __forceinline__ void pipe_fill_issue(float4* __restrict__ sb, float4* __restrict__ szr,
-                                                const StateF32& cur, const int W, const int H,
-                                                const int bx0, const int by0) {
+// Blend from a structure-of-arrays window whose origin is (bx0 - 4, by0 - 2).
+template <int TH, int R, int MODE>
+__device__ __forceinline__ void blend_compute_soa(const float* __restrict__ w, const KParams& kp, const int W,
+                                                  const int H, float* __restrict__ out, const int bx0,
+                                                  const int by0) {
   constexpr int R0 = kMaxRadius;
-  for (int i = threadIdx.x; i < BlendGeom<TH>::kPix; i += NT) {
-    const int ly = i / kBlendSW, lx = i % kBlendSW;
-    const int gx = bx0 - R0 + lx, gy = by0 - R0 + ly;
-    if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-      const float* src = cur.base + (size_t)gy * cur.pitch + gx;
-      float* b = (float*)(sb + 3 * i);
+  constexpr int RW = 2 * R0 + 1;
+  constexpr int SW = kBlendBoxW;
+  constexpr int P = TmaBlendGeom<TH>::PLANE;
+  const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
+  const int x = bx0 + tx, y0 = by0 + ty * R;
+  const bool feat = kp.feature_mode == 0;
+  float zi[R][3], ri[R], den[R];
+  float acc[R][MODE == 0 ? 12 : 3];
 #pragma unroll
-      for (int p = 0; p < 12; ++p) cp_async4(b + p, src + p * cur.plane_stride);
-      float* z = (float*)(szr + i);
+  for (int i = 0; i < R; ++i) {
+    const int idx = (ty * R + i + R0) * SW + tx + 4;
+    zi[i][0] = w[12 * P + idx]; zi[i][1] = w[13 * P + idx]; zi[i][2] = w[14 * P + idx];
+    ri[i] = w[15 * P + idx];
+    den[i] = 0.0f;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async4(z + c, src + (kZ + c) * cur.plane_stride);
-    } else {
-      const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      sb[3 * i + 0] = zero;
-      sb[3 * i + 1] = zero;
-      sb[3 * i + 2] = zero;
-      szr[i] = make_float4(kFarZ, kFarZ, kFarZ, 0.0f);
+    for (int p = 0; p < (MODE == 0 ? 12 : 3); ++p) acc[i][p] = 0.0f;
+  }
+#pragma unroll
+  for (int kr = 0; kr < R + 2 * R0; ++kr) {
+#pragma unroll
+    for (int dx = -R0; dx <= R0; ++dx) {
+      const int idx = (ty * R + kr) * SW + tx + 4 + dx;
+      const float zk0 = w[12 * P + idx], zk1 = w[13 * P + idx], zk2 = w[14 * P + idx], rkk = w[15 * P + idx];
+      float bk[12];
+#pragma unroll
+      for (int p = 0; p < 12; ++p) bk[p] = w[p * P + idx];
+      float pk0 = 0.0f, pk1 = 0.0f, pk2 = 0.0f;
+      if (MODE == 1) {
+        const float a1 = feat ? zk0 : 0.0f, a2 = feat ? zk1 : 0.0f, a3 = feat ? zk2 : 0.0f;
+        pk0 = bk[0] + bk[1] * a1 + bk[2] * a2 + bk[3] * a3;
+        pk1 = bk[4] + bk[5] * a1 + bk[6] * a2 + bk[7] * a3;
+        pk2 = bk[8] + bk[9] * a1 + bk[10] * a2 + bk[11] * a3;
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int dy = kr - R0 - i;
+        if (dy < -R0 || dy > R0) continue;  // compile-time
+        const float e0 = zi[i][0] - zk0, e1 = zi[i][1] - zk1, e2 = zi[i][2] - zk2;
+        const float rk = fmaxf(ri[i], rkk);
+        const float b = ex2_approx(kp.spatial[(dy + R0) * RW + (dx + R0)] - (e0 * e0 + e1 * e1 + e2 * e2) * rk);
+        den[i] += b;
+        if (MODE == 0) {
+#pragma unroll
+          for (int p = 0; p < 12; ++p) acc[i][p] += b * bk[p];
+        } else {
+          acc[i][0] += b * pk0; acc[i][1] += b * pk1; acc[i][2] += b * pk2;
+        }
+      }
     }
   }
-  cp_async_commit();
-}
-
-// 1/(|z|+eps) of every record (far records get a value ~6e-19, below any pixel's own r).
-template <int TH, int NT>
-__device__ __forceinline__ void pipe_recip_pass(float4* __restrict__ szr, const float eps) {
-  for (int i = threadIdx.x; i < BlendGeom<TH>::kPix; i += NT) {
-    float4 q = szr[i];
-    q.w = 1.0f / (sqrtf(q.x * q.x + q.y * q.y + q.z * q.z) + eps);
-    szr[i] = q;
+  if (x >= W) return;
+  const size_t npix = (size_t)W * H;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int y = y0 + i;
+    if (y >= H) break;
+    float o0, o1, o2;
+    if (MODE == 0) {
+      const float p1 = feat ? zi[i][0] : 0.0f, p2 = feat ? zi[i][1] : 0.0f, p3 = feat ? zi[i][2] : 0.0f;
+      o0 = acc[i][0] + acc[i][1] * p1 + acc[i][2] * p2 + acc[i][3] * p3;
+      o1 = acc[i][4] + acc[i][5] * p1 + acc[i][6] * p2 + acc[i][7] * p3;
+      o2 = acc[i][8] + acc[i][9] * p1 + acc[i][10] * p2 + acc[i][11] * p3;
+    } else {
+      o0 = acc[i][0]; o1 = acc[i][1]; o2 = acc[i][2];
+    }
+    const float inv = 1.0f / den[i];
+    const size_t j = (size_t)y * W + x;
+    out[j] = o0 * inv;
+    out[npix + j] = o1 * inv;
+    out[2 * npix + j] = o2 * inv;
   }
 }
 
-template <int TH, int R, int MODE>
+// NBUF = 2: the next tile's window is copied while the current one is blended. NBUF = 1: one
+// window (half the shared memory, twice the CTAs per SM): the next copy starts once the
+// current tile is blended, and other CTAs of the SM compute meanwhile.
+template <int TH, int R, int MODE, int NBUF>
 __global__ void __launch_bounds__(kTW * TH / R)
-    k_blend_pipe(const KParams kp, const int W, const int H, const StateF32 cur, float* __restrict__ out) {
+    k_blend_tma(const KParams kp, const int W, const int H, const __grid_constant__ BlendMaps maps,
+                float* __restrict__ out, int* err) {
+  using G = TmaBlendGeom<TH>;
   constexpr int NT = kTW * TH / R;
-  constexpr int PIX = BlendGeom<TH>::kPix;
-  extern __shared__ float4 smem[];  // two windows, each [3 * PIX beta records][PIX z records]
+  constexpr int P = G::PLANE;
+  extern __shared__ unsigned char dsmem[];
+  float* sm = reinterpret_cast<float*>(align128(dsmem));
+  __shared__ alignas(8) uint64_t bar[2];
+  const CUtensorMap* mb = TH == 16 ? &maps.beta16 : &maps.beta8;
+  const CUtensorMap* mz = TH == 16 ? &maps.z16 : &maps.z8;
   const int tiles_x = (W + kTW - 1) / kTW;
   const int n_tiles = tiles_x * ((H + TH - 1) / TH);
   int tile = blockIdx.x;
   if (tile >= n_tiles) return;
-  pipe_fill_issue<TH, NT>(smem, smem + 3 * PIX, cur, W, H, (tile % tiles_x) * kTW, (tile / tiles_x) * TH);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  uint32_t ph0 = 0u, ph1 = 0u;  // phases of the two windows' mbarriers
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar[0], G::kTx);
+    tma_load_3d(sm, mb, (tile % tiles_x) * kTW - 4, (tile / tiles_x) * TH - 2, 0, &bar[0]);
+    tma_load_3d(sm + 12 * P, mz, (tile % tiles_x) * kTW - 4, (tile / tiles_x) * TH - 2, kZ, &bar[0]);
+  }
   for (int it = 0;; ++it) {
-    float4* sb = smem + (it & 1) * 4 * PIX;
-    float4* sz = sb + 3 * PIX;
+    const int b = NBUF == 2 ? (it & 1) : 0;
+    float* wcur = sm + b * G::BUF;
     const int next = tile + gridDim.x;
-    if (next < n_tiles) {
-      float4* nb = smem + ((it & 1) ^ 1) * 4 * PIX;
-      pipe_fill_issue<TH, NT>(nb, nb + 3 * PIX, cur, W, H, (next % tiles_x) * kTW, (next / tiles_x) * TH);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+    if (NBUF == 2 && next < n_tiles && threadIdx.x == 0) {  // the other window was released by the last barrier
+      float* wn = sm + (b ^ 1) * G::BUF;
+      fence_proxy_async();
+      mbar_expect_tx(&bar[b ^ 1], G::kTx);
+      tma_load_3d(wn, mb, (next % tiles_x) * kTW - 4, (next / tiles_x) * TH - 2, 0, &bar[b ^ 1]);
+      tma_load_3d(wn + 12 * P, mz, (next % tiles_x) * kTW - 4, (next / tiles_x) * TH - 2, kZ, &bar[b ^ 1]);
+    }
+    const uint32_t ph = b ? ph1 : ph0;
+    const bool ok = mbar_wait_bounded(&bar[b], ph);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(err, (int)WRLS_ERR_TIMEOUT);
+      mbar_wait_bounded(&bar[b], ph);  // copies may still be in flight
+      if (NBUF == 2 && next < n_tiles) mbar_wait_bounded(&bar[b ^ 1], b ? ph0 : ph1);
+      return;
+    }
+    if (b) ph1 ^= 1u; else ph0 ^= 1u;
+    const int bx0 = (tile % tiles_x) * kTW, by0 = (tile / tiles_x) * TH;
+    for (int i = threadIdx.x; i < P; i += NT) {
+      const int gx = bx0 - 4 + i % kBlendBoxW, gy = by0 - 2 + i / kBlendBoxW;
+      if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+        const float z0 = wcur[12 * P + i], z1 = wcur[13 * P + i], z2 = wcur[14 * P + i];
+        const float r = 1.0f / (sqrtf(z0 * z0 + z1 * z1 + z2 * z2) + kp.eps);
+        wcur[15 * P + i] = r * r * kp.range_k;
+      } else {
+#pragma unroll
+        for (int p = 0; p < 12; ++p) wcur[p * P + i] = 0.0f;
+        wcur[12 * P + i] = kFarZ;
+        wcur[13 * P + i] = kFarZ;
+        wcur[14 * P + i] = kFarZ;
+        wcur[15 * P + i] = 0.0f;
+      }
     }
     __syncthreads();
-    pipe_recip_pass<TH, NT>(sz, kp.eps);
-    __syncthreads();
-    blend_compute<TH, R, MODE>(sb, sz, kp, W, H, out, (tile % tiles_x) * kTW, (tile / tiles_x) * TH);
+    blend_compute_soa<TH, R, MODE>(wcur, kp, W, H, out, bx0, by0);
     if (next >= n_tiles) break;
-    __syncthreads();  // buf is refilled by the next iteration's copies
+    __syncthreads();  // this window is refilled by a later copy
+    if (NBUF == 1 && threadIdx.x == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar[0], G::kTx);
+      tma_load_3d(sm, mb, (next % tiles_x) * kTW - 4, (next / tiles_x) * TH - 2, 0, &bar[0]);
+      tma_load_3d(sm + 12 * P, mz, (next % tiles_x) * kTW - 4, (next / tiles_x) * TH - 2, kZ, &bar[0]);
+    }
     tile = next;
   }
 }
 
-template <int TH, int R, int MODE>
-static cudaError_t launch_pipe_cfg(const KParams& kp, const StateF32& cur, int W, int H, float* out,
-                                   cudaStream_t cs) {
-  constexpr int bytes = 2 * BlendGeom<TH>::kSmemBytes;
+template <int TH, int R, int MODE, int NBUF>
+static cudaError_t launch_tma_cfg(const KParams& kp, const StateDesc& cur, float* out, int* err, cudaStream_t cs) {
+  constexpr int bytes = TmaBlendGeom<TH>::smem_bytes(NBUF);
   constexpr int nt = kTW * TH / R;
-  static int grid_per_sm = 0;  // per instantiation
-  if (!grid_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_blend_pipe<TH, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         bytes);
+  static int per_sm = 0;  // per instantiation
+  if (!per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_blend_tma<TH, R, MODE, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_pipe<TH, R, MODE>, nt, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_tma<TH, R, MODE, NBUF>, nt, bytes);
     if (e != cudaSuccess) return e;
-    grid_per_sm = occ > 0 ? occ : 1;
+    per_sm = occ > 0 ? occ : 1;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int n_tiles = ((W + kTW - 1) / kTW) * ((H + TH - 1) / TH);
-  int grid = sms * grid_per_sm;
+  const int n_tiles = ((cur.W + kTW - 1) / kTW) * ((cur.H + TH - 1) / TH);
+  int grid = sms * per_sm;
   if (grid > n_tiles) grid = n_tiles;
-  k_blend_pipe<TH, R, MODE><<<grid, nt, bytes, cs>>>(kp, W, H, cur, out);
+  k_blend_tma<TH, R, MODE, NBUF><<<grid, nt, bytes, cs>>>(kp, cur.W, cur.H, cur.bmaps, out, err);
   return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t launch_pipe_mode(const KParams& kp, int cfg, const StateF32& cur, int W, int H, float* out,
-                                    cudaStream_t cs) {
+static cudaError_t launch_tma_mode(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
+                                   cudaStream_t cs) {
   switch (cfg) {
-    case 0: return launch_pipe_cfg<16, 4, MODE>(kp, cur, W, H, out, cs);
-    case 1: return launch_pipe_cfg<8, 4, MODE>(kp, cur, W, H, out, cs);
-    case 2: return launch_pipe_cfg<16, 2, MODE>(kp, cur, W, H, out, cs);
-    case 3: return launch_pipe_cfg<8, 2, MODE>(kp, cur, W, H, out, cs);
+    case 0: return launch_tma_cfg<16, 2, MODE, 2>(kp, cur, out, err, cs);
+    case 1: return launch_tma_cfg<16, 2, MODE, 1>(kp, cur, out, err, cs);
+    case 2: return launch_tma_cfg<8, 2, MODE, 2>(kp, cur, out, err, cs);
+    case 3: return launch_tma_cfg<16, 4, MODE, 1>(kp, cur, out, err, cs);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs) {
-  if (cur.precision != 0) return cudaErrorInvalidValue;
-  return kp.blend_mode == 0 ? launch_pipe_mode<0>(kp, cfg, cur.f32(), cur.W, cur.H, out, cs)
-                            : launch_pipe_mode<1>(kp, cfg, cur.f32(), cur.W, cur.H, out, cs);
+cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
+                                   cudaStream_t cs) {
+  if (cur.precision != 0 || !cur.blend_tma_ok) return cudaErrorInvalidValue;
+  return kp.blend_mode == 0 ? launch_tma_mode<0>(kp, cfg, cur, out, err, cs)
+                            : launch_tma_mode<1>(kp, cfg, cur, out, err, cs);
 }
 
 }  // namespace wrls

@@ -69,6 +69,13 @@ struct StageMaps {
   CUtensorMap scale;
 };
 
+// Tensor maps of the blend windows of a binary32 state copy: the 12 beta planes and the 3 z
+// planes, boxes of kBlendBoxW columns x (TH + 4) rows, for blend tiles of TH = 16 and TH = 8.
+constexpr int kBlendBoxW = 40;
+struct BlendMaps {
+  CUtensorMap beta16, z16, beta8, z8;
+};
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }

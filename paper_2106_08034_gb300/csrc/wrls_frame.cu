@@ -101,8 +101,8 @@ static cudaError_t launch_blend_sv(const KParams& kp, int cfg, const SV& cur, in
                             : launch_blend_mode<SV, 1>(kp, cfg, cur, W, H, out, cs);
 }
 
-cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs) {
-  if (cfg >= kBlendSyncConfigs) return launch_blend_pipelined(kp, cfg - kBlendSyncConfigs, cur, out, cs);
+cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err, cudaStream_t cs) {
+  if (cfg >= kBlendSyncConfigs) return launch_blend_pipelined(kp, cfg - kBlendSyncConfigs, cur, out, err, cs);
   switch (cur.precision) {
     case 0: return launch_blend_sv(kp, cfg, cur.f32(), cur.W, cur.H, out, cs);
     case 1: return launch_blend_sv(kp, cfg, cur.bf16(), cur.W, cur.H, out, cs);

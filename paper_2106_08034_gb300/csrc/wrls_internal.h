@@ -20,6 +20,8 @@ struct StateDesc {
   size_t plane_stride = 0;  // in values
   StageMaps maps{};          // TMA tensor maps of this copy (planes; P scales for 16-bit)
   bool stage_ok = false;     // maps encoded and the image is at least one staging box
+  BlendMaps bmaps{};         // TMA tensor maps of the blend windows (binary32 state)
+  bool blend_tma_ok = false; // bmaps encoded (binary32 state, image at least one box)
 
   StateF32 f32() const { return StateF32{(float*)base, plane_stride, pitch}; }
   StateBF16 bf16() const { return StateBF16{(__nv_bfloat16*)base, scale, plane_stride, pitch}; }
@@ -39,19 +41,24 @@ cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateD
 bool encode_stage_maps(StateDesc& d, const char** why);
 // Blend tile configurations (tile rows TH x output rows per thread R):
 // 0: 16x4 (default), 1: 8x4, 2: 16x2, 3: 32x4 -- one CTA per tile, synchronous fill;
-// 4: 16x4, 5: 8x4, 6: 16x2, 7: 8x2 -- persistent, pipelined fill (binary32 state only).
+// 4: 16x2, 5: 16x2, 6: 8x2, 7: 16x4 -- persistent, TMA-filled windows, double-buffered (4, 6)
+// or single (5, 7) (binary32 state, images of at least 40 x 20 pixels).
 constexpr int kBlendConfigs = 8;
 constexpr int kBlendSyncConfigs = 4;
-inline bool blend_config_ok(int cfg, int precision) {
-  return cfg >= 0 && cfg < kBlendConfigs && (cfg < kBlendSyncConfigs || precision == 0);
+inline bool blend_config_ok(int cfg, int precision, bool tma_ok) {
+  return cfg >= 0 && cfg < kBlendConfigs && (cfg < kBlendSyncConfigs || (precision == 0 && tma_ok));
 }
 // The synchronous configuration with the same tile shape (used by the batched tick).
 inline int blend_sync_config(int cfg) {
-  static const int map[kBlendConfigs] = {0, 1, 2, 3, 0, 1, 2, 1};
+  static const int map[kBlendConfigs] = {0, 1, 2, 3, 2, 2, 1, 0};
   return (cfg >= 0 && cfg < kBlendConfigs) ? map[cfg] : 0;
 }
-cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs);
-cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& cur, float* out, cudaStream_t cs);
+cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err, cudaStream_t cs);
+// Persistent, prefetching variant of the update kernel (pipeline 3).
+cudaError_t launch_update_pipelined(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
+                                    const float* rad, const float* mot, int* err, cudaStream_t cs);
+cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
+                                   cudaStream_t cs);
 cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs);
 // Fused wavefront kernel (update + blend in one persistent launch).
 size_t fused_scratch_bytes(int W, int H);
@@ -74,7 +81,7 @@ struct wrls_stream {
   int* err = nullptr;           // device error word (WRLS_ERR_TIMEOUT from a bounded wait)
   int* work = nullptr;          // fused kernel: item and exit counters (zero between launches)
   int* flags = nullptr;         // fused kernel: per-update-tile done flags (frame epochs)
-  int pipeline = 0;             // 0 = update kernel + blend kernel; 1, 2 = fused kernel variants
+  int pipeline = 0;             // 0, 3 = update kernel + blend kernel (3: prefetching update); 1, 2 = fused
   size_t mem_bytes = 0;
   int cur = 0;                  // copy holding frame t-1
   bool need_reset = true;

@@ -71,13 +71,10 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint64_t* bar, u
     lo_x = x0; hi_x = min(x0 + 1, W - 1);
     lo_y = y0; hi_y = min(y0 + 1, H - 1);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    lo_x = min(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
-    hi_x = max(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
-    lo_y = min(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
-    hi_y = max(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
-  }
+  lo_x = __reduce_min_sync(0xffffffffu, lo_x);
+  hi_x = __reduce_max_sync(0xffffffffu, hi_x);
+  lo_y = __reduce_min_sync(0xffffffffu, lo_y);
+  hi_y = __reduce_max_sync(0xffffffffu, hi_y);
   if (lane == 0) {
     sm.red[warp][0] = lo_x; sm.red[warp][1] = hi_x; sm.red[warp][2] = lo_y; sm.red[warp][3] = hi_y;
   }
@@ -102,16 +99,20 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint64_t* bar, u
       if constexpr (SV::kHasScale) tma_load_2d(sm.stage + SV::kScaleOffset, &maps->scale, X0, Y0, bar);
     }
   }
-  // radiance tile with a 1-pixel halo (out-of-image = NaN, skipped by the clamp)
+  // radiance tile with a 1-pixel halo; a missing sample (a non-finite channel) and a pixel
+  // outside the image are stored as (NaN, NaN, NaN): fminf/fmaxf ignore NaN operands, so the
+  // clamp box below skips them without a test per neighbour
   for (int i = threadIdx.x; i < (kTH + 2) * (kTW + 2); i += kTileThreads) {
     const int ly = i / (kTW + 2), lx = i % (kTW + 2);
     const int gx = bx0 - 1 + lx, gy = by0 - 1 + ly;
-    float r = __int_as_float(0x7fc00000), g = r, b = r;
+    const float nan = __int_as_float(0x7fc00000);
+    float r = nan, g = nan, b = nan;
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
       const size_t jj = (size_t)gy * W + gx;
       r = __ldg(rad + jj);
       g = __ldg(rad + npix + jj);
       b = __ldg(rad + 2 * npix + jj);
+      if (!(isfinite(r) && isfinite(g) && isfinite(b))) r = g = b = nan;
     }
     sm.rad[0][ly][lx] = r;
     sm.rad[1][ly][lx] = g;
@@ -131,22 +132,20 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint64_t* bar, u
   if (!inside) return true;
 
   float I[3] = {sm.rad[0][ty + 1][tx + 1], sm.rad[1][ty + 1][tx + 1], sm.rad[2][ty + 1][tx + 1]};
-  const bool missing = !(isfinite(I[0]) && isfinite(I[1]) && isfinite(I[2]));
+  const bool missing = I[0] != I[0];
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  bool have_box = false;
 #pragma unroll
   for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) {
-      const float a = sm.rad[0][ty + dy][tx + dx], b = sm.rad[1][ty + dy][tx + dx],
-                  c = sm.rad[2][ty + dy][tx + dx];
-      if (isfinite(a) && isfinite(b) && isfinite(c)) {
-        have_box = true;
-        lo[0] = fminf(lo[0], a); hi[0] = fmaxf(hi[0], a);
-        lo[1] = fminf(lo[1], b); hi[1] = fmaxf(hi[1], b);
-        lo[2] = fminf(lo[2], c); hi[2] = fmaxf(hi[2], c);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v = sm.rad[c][ty + dy][tx + dx];
+        lo[c] = fminf(lo[c], v);
+        hi[c] = fmaxf(hi[c], v);
       }
     }
+  const bool have_box = lo[0] <= hi[0];  // some neighbour (possibly the pixel itself) was present
   float st[kNState];
   if (valid) {
     if (fits) gather_bilinear_staged<SV>(sm.stage, X0, Y0, W, H, qx, qy, st);
@@ -167,12 +166,14 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
 // A blend tile is 32 x TH output pixels; each thread produces R vertically adjacent outputs of
 // one column, so a neighbour read from shared memory serves up to 5 of the thread's outputs.
 // Shared memory holds the (32+4) x (TH+4) window of the models after the update as two record
-// arrays: beta[12] per pixel (48-byte stride) and {z[3], 1/(|z|+eps)} per pixel (16 bytes);
-// both strides make a warp's 128-bit loads conflict-free.
+// arrays: beta[12] per pixel (48-byte stride) and {z[3], rk} per pixel (16 bytes), with
+// rk = K / (|z|+eps)^2 and K = log2(e) / h_s^2; both strides make a warp's 128-bit loads
+// conflict-free. With r = 1/(|z|+eps), the range exponent of a pair is
+// |z_i - z_k|^2 max(r_i, r_k)^2 K = |z_i - z_k|^2 max(rk_i, rk_k).
 //
 // No neighbour is tested in the inner loop. A window pixel outside the image gets beta = 0,
-// z = kFarZ and 1/(|z|+eps) = 0, so its feature distance to any pixel of the image is huge and
-// its weight exp2(-huge) is exactly 0; offsets beyond the window radius (radius < 2) get a
+// z = kFarZ and rk = 0, so its feature distance to any pixel of the image is huge and its
+// weight exp2(-huge) is exactly 0; offsets beyond the window radius (radius < 2) get a
 // spatial exponent of -inf, weight exactly 0. Adding exact zeros leaves every sum unchanged,
 // so the result equals skipping those neighbours.
 constexpr int kBlendSW = kTW + 2 * kMaxRadius;
@@ -204,7 +205,7 @@ __device__ __forceinline__ void blend_fill(float4* __restrict__ sb, float4* __re
       sb[3 * i + 0] = make_float4(b[0], b[1], b[2], b[3]);
       sb[3 * i + 1] = make_float4(b[4], b[5], b[6], b[7]);
       sb[3 * i + 2] = make_float4(b[8], b[9], b[10], b[11]);
-      szr[i] = make_float4(z[0], z[1], z[2], r);
+      szr[i] = make_float4(z[0], z[1], z[2], r * r * kp.range_k);
     } else {
       const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       sb[3 * i + 0] = zero;
@@ -218,7 +219,8 @@ __device__ __forceinline__ void blend_fill(float4* __restrict__ sb, float4* __re
 // Blend the outputs of the tile whose window is in shared memory. MODE 0: out_i = sum_k b_ik
 // (p_i . beta_k) / sum_k b_ik (neighbours' models predict pixel i); MODE 1: sum_k b_ik (p_k .
 // beta_k) / sum_k b_ik. b_ik = exp(-|dxy|^2 / (2 sigma_s^2)) exp(-d_z(i,k)^2 / h_s^2) with d_z the
-// Eq. 13 distance of the features; 1 / (min(|z_i|, |z_k|) + eps) = max(r_i, r_k).
+// Eq. 13 distance of the features; 1 / (min(|z_i|, |z_k|) + eps) = max(r_i, r_k), computed in
+// base 2 as exp2(spatial - |z_i - z_k|^2 max(rk_i, rk_k)).
 template <int TH, int R, int MODE>
 __device__ __forceinline__ void blend_compute(const float4* __restrict__ sb,
                                               const float4* __restrict__ szr, const KParams& kp,
@@ -258,9 +260,8 @@ __device__ __forceinline__ void blend_compute(const float4* __restrict__ sb,
         const int dy = kr - R0 - i;
         if (dy < -R0 || dy > R0) continue;  // compile-time
         const float e0 = zi[i][0] - q3.x, e1 = zi[i][1] - q3.y, e2 = zi[i][2] - q3.z;
-        const float rm = fmaxf(ri[i], q3.w);
-        const float d2 = (e0 * e0 + e1 * e1 + e2 * e2) * (rm * rm);
-        const float b = ex2_approx(kp.spatial[(dy + R0) * RW + (dx + R0)] - d2 * kp.range_k);
+        const float rk = fmaxf(ri[i], q3.w);  // K / (min(|z_i|, |z_k|) + eps)^2
+        const float b = ex2_approx(kp.spatial[(dy + R0) * RW + (dx + R0)] - (e0 * e0 + e1 * e1 + e2 * e2) * rk);
         den[i] += b;
         if (MODE == 0) {
           acc[i][0] += b * q0.x; acc[i][1] += b * q0.y; acc[i][2] += b * q0.z; acc[i][3] += b * q0.w;

@@ -197,7 +197,8 @@ def wrls_stream_autotune(stream: int, out, reps: int = 5):
 
 
 def wrls_stream_set_pipeline(stream: int, fused: int) -> None:
-    """0 = update kernel + blend kernel (default), 1 / 2 = fused wavefront kernel variants."""
+    """0 = update kernel + blend kernel (default), 1 / 2 = fused wavefront kernel variants,
+    3 = prefetching persistent update kernel + blend kernel."""
     _check(lib().wrls_stream_set_pipeline(stream, int(fused)))
 
 

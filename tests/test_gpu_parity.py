@@ -88,7 +88,8 @@ def test_degenerate_sizes(wh):
     run_pair(cpu_frames(spec), w, h)
 
 
-def test_missing_samples_and_bad_motion():
+@pytest.mark.parametrize("pipeline", [0, 3])
+def test_missing_samples_and_bad_motion(pipeline):
     spec = synth.SceneSpec(90, 60, 10, seed=35, motion="orbit", firefly_frac=0.05)
 
     def hooks(t, rad, mot):
@@ -102,7 +103,7 @@ def test_missing_samples_and_bad_motion():
         if t == 6:
             rad[:, 10:13, 20:23] = float("nan")    # a 3x3 hole: clamp box of the centre is empty
         return rad, mot
-    run_pair(cpu_frames(spec), 90, 60, hooks=hooks)
+    run_pair(cpu_frames(spec), 90, 60, hooks=hooks, pipeline=pipeline)
 
 
 def test_reset_restarts_every_pixel():
@@ -229,8 +230,9 @@ def test_blend_configs_match_oracle(cfg):
         assert rel_err(out.cpu().numpy(), ref) <= REL_TOL
 
 
+@pytest.mark.parametrize("pipeline", [0, 3])
 @pytest.mark.parametrize("kind", ["uniform", "random"])
-def test_staged_and_global_gather_paths(kind):
+def test_staged_and_global_gather_paths(kind, pipeline):
     """Uniform motion keeps every tile's tap footprint inside the staged window (TMA path);
     per-pixel random motion of a few pixels spreads it beyond (global-gather path)."""
     spec = synth.SceneSpec(160, 96, 8, seed=52, motion="static", firefly_frac=0.05)
@@ -244,10 +246,10 @@ def test_staged_and_global_gather_paths(kind):
         else:
             mot.copy_((torch.rand(2, 96, 160, generator=g) - 0.5) * 12.0)
         return rad, mot
-    run_pair(fr, 160, 96, hooks=hooks)
+    run_pair(fr, 160, 96, hooks=hooks, pipeline=pipeline)
 
 
-@pytest.mark.parametrize("pipeline", [0, 1, 2])
+@pytest.mark.parametrize("pipeline", [0, 1, 2, 3])
 def test_pipelines_match_oracle(pipeline):
     spec = synth.SceneSpec(181, 95, 24, seed=56, motion="pan", firefly_frac=0.05)
     run_pair(cpu_frames(spec), spec.width, spec.height, pipeline=pipeline)
@@ -259,7 +261,7 @@ def test_pipelines_bitwise_identical(precision):
     spec = synth.SceneSpec(333, 200, 6, seed=57, motion="orbit", firefly_frac=0.05)
     fr = cpu_frames(spec)
     res = []
-    for pipeline in (0, 1, 2):
+    for pipeline in (0, 1, 2, 3):
         s = W.Stream(spec.width, spec.height, W.wrls_params_default(state_precision=precision))
         W.wrls_stream_set_pipeline(s.handle, pipeline)
         o = torch.empty(3, spec.height, spec.width, device="cuda")
