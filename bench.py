@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "denoised Mpix/s plain FP32 vs batched BF16-state at stated err; p99 frame latency"
 BYTES_UPDATE_F32 = 220   # per pixel: state read 100 + radiance 12 + motion 8 + state write 100
 BYTES_PATH_F32 = 232     # per pixel and frame for the whole path: + out 12
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_update launch on a
+# 1920x1080 frame, from the ncu capture summarised in profiles/k_update_pan_1080p.md (same
+# kernel build). Writes still held in L2 when the kernel ends are not counted by ncu.
+TRAFFIC_PER_LAUNCH = {"k_update": 248.867584e6 + 168.646400e6}
 
 
 def parse():
@@ -48,6 +52,10 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--batched-passes", type=int, default=3)
+    ap.add_argument("--pipeline", type=int, default=-1,
+                    help="run this pipeline instead of timing them all (profiling captures)")
+    ap.add_argument("--blend-config", type=int, default=-1,
+                    help="use this blend tile configuration instead of autotuning (profiling captures)")
     return ap.parse_args()
 
 
@@ -337,9 +345,13 @@ def run_wrls(args):
     cs.synchronize()
     # tile configuration of the two-kernel pipeline, then the fastest pipeline (untimed)
     W.wrls_stream_set_pipeline(s.handle, 0)
-    blend_times, blend_cfg = W.wrls_stream_autotune(s.handle, out, reps=5)
+    if args.blend_config >= 0:
+        W.wrls_stream_set_blend_config(s.handle, args.blend_config)
+        blend_times, blend_cfg = [], args.blend_config
+    else:
+        blend_times, blend_cfg = W.wrls_stream_autotune(s.handle, out, reps=5)
     pipe_ms = {}
-    for pipeline in (0, 1, 2, 3):
+    for pipeline in ((0, 1, 2, 3) if args.pipeline < 0 else ()):
         W.wrls_stream_set_pipeline(s.handle, pipeline)
         step()
         a = torch.cuda.Event(enable_timing=True)
@@ -349,7 +361,7 @@ def run_wrls(args):
         b.record(cs)
         b.synchronize()
         pipe_ms[pipeline] = a.elapsed_time(b) / T
-    best_pipeline = min(pipe_ms, key=pipe_ms.get)
+    best_pipeline = min(pipe_ms, key=pipe_ms.get) if pipe_ms else args.pipeline
     W.wrls_stream_set_pipeline(s.handle, best_pipeline)
     W.wrls_stream_enable_timing(s.handle, True)
 
@@ -416,16 +428,19 @@ def run_wrls(args):
     peak, peak_kind = measured_peaks()
     upd_per = upd_ms / max(nfr, 1)
     bl_per = bl_ms / max(nfr, 1)
+    traffic = None
     if best_pipeline in (0, 3):
         kname = ("k_update" if best_pipeline == 0 else "k_update_pipe") + \
             " (reproject + Eq. 12-14 update; the blend is a separate kernel)"
         kbytes = BYTES_UPDATE_F32
+        if best_pipeline == 0 and (Wd, Hd) == (1920, 1080):
+            traffic = TRAFFIC_PER_LAUNCH["k_update"]
     else:
         kname, kbytes = "k_fused (reproject + Eq. 12-14 update + 5x5 blend, one launch)", BYTES_PATH_F32
     achieved = kbytes * px / (upd_per / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "bytes_per_px": kbytes,
                 "kernel_ms": {"update" if best_pipeline in (0, 3) else "fused": round(upd_per, 5),

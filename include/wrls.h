@@ -151,14 +151,16 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
  * thread): 0: 16x4, 1: 8x4, 2: 16x2, 3: 32x4 with one CTA per tile; 4: 16x2, 5: 16x2,
  * 6: 8x2, 7: 16x4 with persistent CTAs whose windows are filled by TMA bulk tensor copies,
  * double-buffered (4, 6: the next window arrives while the current one is blended) or single
- * (5, 7: more CTAs per SM) (binary32 state, images of at least 40 x 20 pixels). All configurations give bitwise identical outputs. Requires one
+ * (5, 7: more CTAs per SM) (binary32 state, images of at least 40 x 20 pixels); 8: 16 rows,
+ * 9: 8 rows, with each thread blending 2 adjacent columns x 2 rows from a TMA-filled window
+ * (64-column tiles; binary32 state, images of at least 72 x 20 pixels). All configurations give bitwise identical outputs. Requires one
  * denoised frame; `out` (device, 3 x H x W) is overwritten and ends up holding the current
  * frame's output. times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per
  * launch (-1 for a configuration the state format does not offer) and *chosen (optional)
  * the selected configuration. Synchronises the stream. The batched tick uses the
  * one-CTA-per-tile configuration of the same tile shape.
  */
-#define WRLS_BLEND_CONFIGS 8
+#define WRLS_BLEND_CONFIGS 10
 wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen);
 
 /*

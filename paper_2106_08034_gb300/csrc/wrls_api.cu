@@ -58,6 +58,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 bool encode_stage_maps(StateDesc& d, const char** why) {
   d.stage_ok = false;
   d.blend_tma_ok = false;
+  d.blend_tma2_ok = false;
   memset(&d.maps, 0, sizeof(d.maps));
   memset(&d.bmaps, 0, sizeof(d.bmaps));
   if (d.pitch < kStageW || d.H < kStageH) return true;  // smaller images read taps from global memory
@@ -95,6 +96,19 @@ bool encode_stage_maps(StateDesc& d, const char** why) {
       if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for a blend window"; return false; }
     }
     d.blend_tma_ok = true;
+    if (d.pitch >= kBlendBoxW2) {
+      const cuuint32_t wb16[3] = {(cuuint32_t)kBlendBoxW2, 20, 12}, wz16[3] = {(cuuint32_t)kBlendBoxW2, 20, 3};
+      const cuuint32_t wb8[3] = {(cuuint32_t)kBlendBoxW2, 12, 12}, wz8[3] = {(cuuint32_t)kBlendBoxW2, 12, 3};
+      CUtensorMap* m2[4] = {&d.bmaps.beta16w, &d.bmaps.z16w, &d.bmaps.beta8w, &d.bmaps.z8w};
+      const cuuint32_t* bx2[4] = {wb16, wz16, wb8, wz8};
+      for (int i = 0; i < 4; ++i) {
+        r = enc(m2[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, d.base, dims, strides, bx2[i], es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for a two-wide blend window"; return false; }
+      }
+      d.blend_tma2_ok = true;
+    }
   }
   return true;
 }
@@ -412,7 +426,7 @@ wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused) {
 }
 
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config) {
-  if (!s || !blend_config_ok(config, s->prm.state_precision, s->state[0].blend_tma_ok)) {
+  if (!s || !blend_config_ok(config, s->prm.state_precision, s->state[0].blend_tma_ok, s->state[0].blend_tma2_ok)) {
     set_error("wrls_stream_set_blend_config: bad stream or configuration %d for this state format", config);
     return WRLS_ERR_INVALID_ARG;
   }
@@ -435,7 +449,7 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
   float best_ms = 0.0f;
   cudaError_t e = cudaSuccess;
   for (int c = 0; c < kBlendConfigs && e == cudaSuccess; ++c) {
-    if (!blend_config_ok(c, cur.precision, cur.blend_tma_ok)) {
+    if (!blend_config_ok(c, cur.precision, cur.blend_tma_ok, cur.blend_tma2_ok)) {
       if (times_ms) times_ms[c] = -1.0f;
       continue;
     }

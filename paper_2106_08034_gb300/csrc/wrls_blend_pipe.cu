@@ -228,3 +228,225 @@ cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& 
 }
 
 }  // namespace wrls
+
+// ---- two-wide variant: each thread blends 2 adjacent columns x R rows -----------------------
+//
+// Tiles are 64 x TH; the window is kBlendBoxW2 = 72 columns (64 + 2 x 4) x (TH + 4) rows of the
+// 12 beta and 3 z planes (one TMA box each) plus an rk plane. A thread's two output columns
+// 2tx and 2tx+1 have neighbour columns 2tx-2 .. 2tx+3: three aligned column pairs, each
+// fetched with one 64-bit shared load per plane, so each neighbour value is loaded once for up
+// to two output columns and R rows. Same arithmetic and neighbour order per output as
+// blend_compute, hence bitwise identical outputs.
+namespace wrls {
+
+template <int TH>
+struct TmaBlend2Geom {
+  static constexpr int SH = TH + 2 * kMaxRadius;
+  static constexpr int PLANE = SH * kBlendBoxW2;
+  static constexpr int BUF = 16 * PLANE;
+  static constexpr uint32_t kTx = 15u * PLANE * 4u;
+  static constexpr int kSmemBytes = BUF * 4 + 128;
+};
+
+template <int TH, int R, int MODE>
+__device__ __forceinline__ void blend_compute_soa2(const float* __restrict__ w, const KParams& kp, const int W,
+                                                   const int H, float* __restrict__ out, const int bx0,
+                                                   const int by0) {
+  constexpr int R0 = kMaxRadius;
+  constexpr int RW = 2 * R0 + 1;
+  constexpr int SW = kBlendBoxW2;
+  constexpr int P = TmaBlend2Geom<TH>::PLANE;
+  constexpr int NO = 2 * R;  // outputs per thread: (column o, row i) -> o * R + i
+  const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
+  const int x = bx0 + 2 * tx, y0 = by0 + ty * R;
+  const bool feat = kp.feature_mode == 0;
+  float zi[NO][3], ri[NO], den[NO];
+  float acc[NO][MODE == 0 ? 12 : 3];
+#pragma unroll
+  for (int o = 0; o < 2; ++o)
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int idx = (ty * R + i + R0) * SW + 2 * tx + 4 + o;
+      const int q = o * R + i;
+      zi[q][0] = w[12 * P + idx]; zi[q][1] = w[13 * P + idx]; zi[q][2] = w[14 * P + idx];
+      ri[q] = w[15 * P + idx];
+      den[q] = 0.0f;
+#pragma unroll
+      for (int p = 0; p < (MODE == 0 ? 12 : 3); ++p) acc[q][p] = 0.0f;
+    }
+#pragma unroll
+  for (int kr = 0; kr < R + 2 * R0; ++kr) {
+#pragma unroll
+    for (int pair = 0; pair < 3; ++pair) {
+      // neighbour columns 2tx-2+2pair and 2tx-1+2pair (window columns 2tx+2+2pair, +1)
+      const int idx = (ty * R + kr) * SW + 2 * tx + 2 + 2 * pair;
+      float2 bk2[12];
+#pragma unroll
+      for (int p = 0; p < 12; ++p) bk2[p] = *reinterpret_cast<const float2*>(w + p * P + idx);
+      const float2 z0 = *reinterpret_cast<const float2*>(w + 12 * P + idx);
+      const float2 z1 = *reinterpret_cast<const float2*>(w + 13 * P + idx);
+      const float2 z2 = *reinterpret_cast<const float2*>(w + 14 * P + idx);
+      const float2 rr = *reinterpret_cast<const float2*>(w + 15 * P + idx);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int n = 2 * pair + e;  // neighbour column offset from 2tx - 2
+        const float zk0 = e ? z0.y : z0.x, zk1 = e ? z1.y : z1.x, zk2 = e ? z2.y : z2.x;
+        const float rkk = e ? rr.y : rr.x;
+        float bk[12];
+#pragma unroll
+        for (int p = 0; p < 12; ++p) bk[p] = e ? bk2[p].y : bk2[p].x;
+        float pk0 = 0.0f, pk1 = 0.0f, pk2 = 0.0f;
+        if (MODE == 1) {
+          const float a1 = feat ? zk0 : 0.0f, a2 = feat ? zk1 : 0.0f, a3 = feat ? zk2 : 0.0f;
+          pk0 = bk[0] + bk[1] * a1 + bk[2] * a2 + bk[3] * a3;
+          pk1 = bk[4] + bk[5] * a1 + bk[6] * a2 + bk[7] * a3;
+          pk2 = bk[8] + bk[9] * a1 + bk[10] * a2 + bk[11] * a3;
+        }
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+          const int dx = n - 2 - o;
+          if (dx < -R0 || dx > R0) continue;  // compile-time
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const int dy = kr - R0 - i;
+            if (dy < -R0 || dy > R0) continue;  // compile-time
+            const int q = o * R + i;
+            const float e0 = zi[q][0] - zk0, e1 = zi[q][1] - zk1, e2 = zi[q][2] - zk2;
+            const float rk = fmaxf(ri[q], rkk);
+            const float b =
+                ex2_approx(kp.spatial[(dy + R0) * RW + (dx + R0)] - (e0 * e0 + e1 * e1 + e2 * e2) * rk);
+            den[q] += b;
+            if (MODE == 0) {
+#pragma unroll
+              for (int p = 0; p < 12; ++p) acc[q][p] += b * bk[p];
+            } else {
+              acc[q][0] += b * pk0; acc[q][1] += b * pk1; acc[q][2] += b * pk2;
+            }
+          }
+        }
+      }
+    }
+  }
+  const size_t npix = (size_t)W * H;
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    if (x + o >= W) break;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int y = y0 + i;
+      if (y >= H) break;
+      const int q = o * R + i;
+      float o0, o1, o2;
+      if (MODE == 0) {
+        const float p1 = feat ? zi[q][0] : 0.0f, p2 = feat ? zi[q][1] : 0.0f, p3 = feat ? zi[q][2] : 0.0f;
+        o0 = acc[q][0] + acc[q][1] * p1 + acc[q][2] * p2 + acc[q][3] * p3;
+        o1 = acc[q][4] + acc[q][5] * p1 + acc[q][6] * p2 + acc[q][7] * p3;
+        o2 = acc[q][8] + acc[q][9] * p1 + acc[q][10] * p2 + acc[q][11] * p3;
+      } else {
+        o0 = acc[q][0]; o1 = acc[q][1]; o2 = acc[q][2];
+      }
+      const float inv = 1.0f / den[q];
+      const size_t j = (size_t)y * W + x + o;
+      out[j] = o0 * inv;
+      out[npix + j] = o1 * inv;
+      out[2 * npix + j] = o2 * inv;
+    }
+  }
+}
+
+template <int TH, int R, int MODE>
+__global__ void __launch_bounds__(kTW * TH / R)
+    k_blend_tma2(const KParams kp, const int W, const int H, const __grid_constant__ BlendMaps maps,
+                 float* __restrict__ out, int* err) {
+  using G = TmaBlend2Geom<TH>;
+  constexpr int NT = kTW * TH / R;
+  constexpr int P = G::PLANE;
+  constexpr int TW2 = 2 * kTW;
+  extern __shared__ unsigned char dsmem[];
+  float* sm = reinterpret_cast<float*>(align128(dsmem));
+  __shared__ alignas(8) uint64_t bar;
+  const CUtensorMap* mb = TH == 16 ? &maps.beta16w : &maps.beta8w;
+  const CUtensorMap* mz = TH == 16 ? &maps.z16w : &maps.z8w;
+  const int tiles_x = (W + TW2 - 1) / TW2;
+  const int n_tiles = tiles_x * ((H + TH - 1) / TH);
+  int tile = blockIdx.x;
+  if (tile >= n_tiles) return;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t ph = 0u;
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, G::kTx);
+    tma_load_3d(sm, mb, (tile % tiles_x) * TW2 - 4, (tile / tiles_x) * TH - 2, 0, &bar);
+    tma_load_3d(sm + 12 * P, mz, (tile % tiles_x) * TW2 - 4, (tile / tiles_x) * TH - 2, kZ, &bar);
+  }
+  for (;;) {
+    const int next = tile + gridDim.x;
+    const bool ok = mbar_wait_bounded(&bar, ph);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(err, (int)WRLS_ERR_TIMEOUT);
+      mbar_wait_bounded(&bar, ph);  // the copies may still be in flight
+      return;
+    }
+    ph ^= 1u;
+    const int bx0 = (tile % tiles_x) * TW2, by0 = (tile / tiles_x) * TH;
+    for (int i = threadIdx.x; i < P; i += NT) {
+      const int gx = bx0 - 4 + i % kBlendBoxW2, gy = by0 - 2 + i / kBlendBoxW2;
+      if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+        const float z0 = sm[12 * P + i], z1 = sm[13 * P + i], z2 = sm[14 * P + i];
+        const float r = 1.0f / (sqrtf(z0 * z0 + z1 * z1 + z2 * z2) + kp.eps);
+        sm[15 * P + i] = r * r * kp.range_k;
+      } else {
+#pragma unroll
+        for (int p = 0; p < 12; ++p) sm[p * P + i] = 0.0f;
+        sm[12 * P + i] = kFarZ;
+        sm[13 * P + i] = kFarZ;
+        sm[14 * P + i] = kFarZ;
+        sm[15 * P + i] = 0.0f;
+      }
+    }
+    __syncthreads();
+    blend_compute_soa2<TH, R, MODE>(sm, kp, W, H, out, bx0, by0);
+    if (next >= n_tiles) break;
+    __syncthreads();  // the window is refilled for the next tile
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar, G::kTx);
+      tma_load_3d(sm, mb, (next % tiles_x) * TW2 - 4, (next / tiles_x) * TH - 2, 0, &bar);
+      tma_load_3d(sm + 12 * P, mz, (next % tiles_x) * TW2 - 4, (next / tiles_x) * TH - 2, kZ, &bar);
+    }
+    tile = next;
+  }
+}
+
+template <int TH, int R, int MODE>
+static cudaError_t launch_tma2_cfg(const KParams& kp, const StateDesc& cur, float* out, int* err, cudaStream_t cs) {
+  constexpr int bytes = TmaBlend2Geom<TH>::kSmemBytes;
+  constexpr int nt = kTW * TH / R;
+  static int per_sm = 0;  // per instantiation
+  if (!per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_blend_tma2<TH, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_tma2<TH, R, MODE>, nt, bytes);
+    if (e != cudaSuccess) return e;
+    per_sm = occ > 0 ? occ : 1;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tiles = ((cur.W + 2 * kTW - 1) / (2 * kTW)) * ((cur.H + TH - 1) / TH);
+  int grid = sms * per_sm;
+  if (grid > n_tiles) grid = n_tiles;
+  k_blend_tma2<TH, R, MODE><<<grid, nt, bytes, cs>>>(kp, cur.W, cur.H, cur.bmaps, out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend_two_wide(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
+                                  cudaStream_t cs) {
+  if (cur.precision != 0 || !cur.blend_tma2_ok) return cudaErrorInvalidValue;
+  if (kp.blend_mode == 0)
+    return cfg == 0 ? launch_tma2_cfg<16, 2, 0>(kp, cur, out, err, cs) : launch_tma2_cfg<8, 2, 0>(kp, cur, out, err, cs);
+  return cfg == 0 ? launch_tma2_cfg<16, 2, 1>(kp, cur, out, err, cs) : launch_tma2_cfg<8, 2, 1>(kp, cur, out, err, cs);
+}
+
+}  // namespace wrls

@@ -72,8 +72,10 @@ struct StageMaps {
 // Tensor maps of the blend windows of a binary32 state copy: the 12 beta planes and the 3 z
 // planes, boxes of kBlendBoxW columns x (TH + 4) rows, for blend tiles of TH = 16 and TH = 8.
 constexpr int kBlendBoxW = 40;
+constexpr int kBlendBoxW2 = 72;  // two-wide blend tiles: 64 + 2 x 4 columns
 struct BlendMaps {
-  CUtensorMap beta16, z16, beta8, z8;
+  CUtensorMap beta16, z16, beta8, z8;      // 40-column boxes
+  CUtensorMap beta16w, z16w, beta8w, z8w;  // 72-column boxes
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

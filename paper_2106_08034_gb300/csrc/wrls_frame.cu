@@ -102,6 +102,7 @@ static cudaError_t launch_blend_sv(const KParams& kp, int cfg, const SV& cur, in
 }
 
 cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err, cudaStream_t cs) {
+  if (cfg >= 8) return launch_blend_two_wide(kp, cfg - 8, cur, out, err, cs);
   if (cfg >= kBlendSyncConfigs) return launch_blend_pipelined(kp, cfg - kBlendSyncConfigs, cur, out, err, cs);
   switch (cur.precision) {
     case 0: return launch_blend_sv(kp, cfg, cur.f32(), cur.W, cur.H, out, cs);

@@ -21,7 +21,8 @@ struct StateDesc {
   StageMaps maps{};          // TMA tensor maps of this copy (planes; P scales for 16-bit)
   bool stage_ok = false;     // maps encoded and the image is at least one staging box
   BlendMaps bmaps{};         // TMA tensor maps of the blend windows (binary32 state)
-  bool blend_tma_ok = false; // bmaps encoded (binary32 state, image at least one box)
+  bool blend_tma_ok = false; // 40-column blend maps encoded (binary32 state, image >= one box)
+  bool blend_tma2_ok = false; // 72-column blend maps encoded
 
   StateF32 f32() const { return StateF32{(float*)base, plane_stride, pitch}; }
   StateBF16 bf16() const { return StateBF16{(__nv_bfloat16*)base, scale, plane_stride, pitch}; }
@@ -42,15 +43,19 @@ bool encode_stage_maps(StateDesc& d, const char** why);
 // Blend tile configurations (tile rows TH x output rows per thread R):
 // 0: 16x4 (default), 1: 8x4, 2: 16x2, 3: 32x4 -- one CTA per tile, synchronous fill;
 // 4: 16x2, 5: 16x2, 6: 8x2, 7: 16x4 -- persistent, TMA-filled windows, double-buffered (4, 6)
-// or single (5, 7) (binary32 state, images of at least 40 x 20 pixels).
-constexpr int kBlendConfigs = 8;
+// or single (5, 7) (binary32 state, images of at least 40 x 20 pixels);
+// 8: 16 rows x 2 x 2, 9: 8 rows x 2 x 2 -- persistent, TMA-filled, each thread 2 columns x
+// 2 rows (binary32 state, images of at least 72 x 20 pixels).
+constexpr int kBlendConfigs = 10;
 constexpr int kBlendSyncConfigs = 4;
-inline bool blend_config_ok(int cfg, int precision, bool tma_ok) {
-  return cfg >= 0 && cfg < kBlendConfigs && (cfg < kBlendSyncConfigs || (precision == 0 && tma_ok));
+inline bool blend_config_ok(int cfg, int precision, bool tma_ok, bool tma2_ok) {
+  if (cfg < 0 || cfg >= kBlendConfigs) return false;
+  if (cfg < kBlendSyncConfigs) return true;
+  return precision == 0 && (cfg < 8 ? tma_ok : tma2_ok);
 }
 // The synchronous configuration with the same tile shape (used by the batched tick).
 inline int blend_sync_config(int cfg) {
-  static const int map[kBlendConfigs] = {0, 1, 2, 3, 2, 2, 1, 0};
+  static const int map[kBlendConfigs] = {0, 1, 2, 3, 2, 2, 1, 0, 2, 1};
   return (cfg >= 0 && cfg < kBlendConfigs) ? map[cfg] : 0;
 }
 cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err, cudaStream_t cs);
@@ -59,6 +64,8 @@ cudaError_t launch_update_pipelined(const KParams& kp, const StateDesc& prev, co
                                     const float* rad, const float* mot, int* err, cudaStream_t cs);
 cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
                                    cudaStream_t cs);
+cudaError_t launch_blend_two_wide(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
+                                  cudaStream_t cs);
 cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs);
 // Fused wavefront kernel (update + blend in one persistent launch).
 size_t fused_scratch_bytes(int W, int H);

@@ -185,7 +185,7 @@ def wrls_stream_frames(stream: int) -> int:
     return int(lib().wrls_stream_frames(stream))
 
 
-BLEND_CONFIGS = 8
+BLEND_CONFIGS = 10
 
 
 def wrls_stream_autotune(stream: int, out, reps: int = 5):

@@ -213,9 +213,9 @@ def test_blend_configs_bitwise_identical_and_autotune():
         assert torch.equal(o, outs[0])
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_blend_configs_match_oracle(cfg):
-    spec = synth.SceneSpec(97, 53, 5, seed=51, motion="pan", firefly_frac=0.05)
+    spec = synth.SceneSpec(197, 53, 5, seed=51, motion="pan", firefly_frac=0.05)
     p = W.wrls_params_default()
     fr = cpu_frames(spec)
     s = W.Stream(spec.width, spec.height, p)
