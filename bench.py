@@ -141,6 +141,23 @@ def smi_device_id(torch, dev, local):
     return str(local)
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (x itself when there
+    is none)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpix_per_s(frames_per_rank: int, pixels: int, world: int, t_max_ms: float) -> float:
+    """Whole-job throughput: every rank's pixels over the slowest rank's time."""
+    return frames_per_rank * world * pixels / (t_max_ms / 1e3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -384,13 +401,9 @@ def run_wrls(args):
     ms = e0.elapsed_time(e1)
     upd_ms, bl_ms, nfr = W.wrls_stream_kernel_times(s.handle)
     W.wrls_stream_enable_timing(s.handle, False)
-    t_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms, dev)
     frames_total = args.steps * T * world
-    value = frames_total * px / (t_max / 1e3) / 1e6
+    value = job_mpix_per_s(args.steps * T, px, world, t_max)
 
     # e2e: the same metric through the host-buffer entry point, copies in the timed region
     e2e = None
@@ -415,12 +428,8 @@ def run_wrls(args):
             step_host()
         e1.record(cs)
         e1.synchronize()
-        ms2 = e0.elapsed_time(e1)
-        if world > 1:
-            tt = torch.tensor([ms2], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms2 = float(tt.item())
-        e2e = {"value": round(e2e_steps * T * world * px / (ms2 / 1e3) / 1e6, 2), "unit": "Mpix/s",
+        ms2 = max_over_ranks(e0.elapsed_time(e1), dev)
+        e2e = {"value": round(job_mpix_per_s(e2e_steps * T, px, world, ms2), 2), "unit": "Mpix/s",
                "h2d_bytes_per_step": T * px * 20, "d2h_bytes_per_step": T * px * 12,
                "steps": e2e_steps}
         s2.close()

@@ -183,6 +183,17 @@ wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused);
  * 4-7 need the binary32 state (WRLS_ERR_INVALID_ARG otherwise). */
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config);
 
+/*
+ * Test hook for the failure path of the bounded device-side waits. With
+ * WRLS_DEBUG_WITHHOLD_STAGE_COPY set, the update kernel of the two-kernel pipeline arms the
+ * mbarrier of each tile's state-window copy but does not issue the copy, so the tile's
+ * bounded wait runs out (about one second of SM clocks); the kernel then records
+ * WRLS_ERR_TIMEOUT in the stream's error word (read by wrls_stream_check) and returns. The
+ * frame's output and state are unreliable; the CUDA context stays usable. 0 clears it.
+ */
+#define WRLS_DEBUG_WITHHOLD_STAGE_COPY 1u
+wrls_status wrls_stream_set_debug(wrls_stream* s, uint32_t flags);
+
 /* Synchronise the stream's CUDA stream and report device-side failures of the frames
  * since the last check: WRLS_ERR_TIMEOUT if a kernel's bounded wait for its own bulk
  * copy gave up (that frame's output and state are then unreliable). Clears the record. */

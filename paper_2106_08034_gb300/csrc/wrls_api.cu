@@ -151,6 +151,7 @@ bool make_kparams(const wrls_params& p, KParams* kp, const char** why) {
   kp->blend_mode = p.blend_mode;
   kp->feature_mode = p.feature_mode;
   kp->init_mode = p.init_mode;
+  kp->debug_withhold_copy = 0;
   return true;
 }
 
@@ -471,6 +472,15 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
   if (e != cudaSuccess) { set_error("wrls_stream_autotune: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
   s->blend_cfg = best;
   if (chosen) *chosen = best;
+  return WRLS_OK;
+}
+
+wrls_status wrls_stream_set_debug(wrls_stream* s, uint32_t flags) {
+  if (!s || (flags & ~WRLS_DEBUG_WITHHOLD_STAGE_COPY)) {
+    set_error("wrls_stream_set_debug: bad stream or unknown flags 0x%x", flags);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  s->kp.debug_withhold_copy = (flags & WRLS_DEBUG_WITHHOLD_STAGE_COPY) ? 1 : 0;
   return WRLS_OK;
 }
 

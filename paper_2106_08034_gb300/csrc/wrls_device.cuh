@@ -41,6 +41,7 @@ struct KParams {
   int blend_mode;
   int feature_mode;
   int init_mode;
+  int debug_withhold_copy;  // test hook: arm the state-window barrier without issuing the copy
 };
 
 // 2^x on the SFU (PTX ex2.approx, max relative error about 2^-22).

@@ -95,8 +95,10 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint64_t* bar, u
     if (fits) {
       fence_proxy_async();
       mbar_expect_tx(bar, SV::kTxBytes);
-      tma_load_3d(sm.stage, &maps->planes, X0, Y0, 0, bar);
-      if constexpr (SV::kHasScale) tma_load_2d(sm.stage + SV::kScaleOffset, &maps->scale, X0, Y0, bar);
+      if (!kp.debug_withhold_copy) {
+        tma_load_3d(sm.stage, &maps->planes, X0, Y0, 0, bar);
+        if constexpr (SV::kHasScale) tma_load_2d(sm.stage + SV::kScaleOffset, &maps->scale, X0, Y0, bar);
+      }
     }
   }
   // radiance tile with a 1-pixel halo; a missing sample (a non-finite channel) and a pixel

@@ -1,0 +1,65 @@
+"""Quality harness: the paper's ablations and a noise sweep on synthetic sequences, run on
+the GPU through the C ABI, scored against the generator's clean truth.
+
+Modes (Sec. 5.3, Fig. 8-9): wRLS vs RLS (w = 1), feature p = [1, z] ("F") vs no feature
+p = [1] ("NF"), 5x5 spatio-temporal blend vs temporal-only output. Scores per sequence:
+relMSE = mean((out - I)^2 / (I^2 + 0.01)), PSNR on colours clipped to [0, 1], and temporal
+flicker = mean over frames of mean |(out_t - out_{t-1}) - (I_t - I_{t-1})| (the part of the
+frame-to-frame change not explained by the truth). The first `skip` frames are excluded.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Optional
+
+import torch
+
+from . import synth
+from . import wrls as W
+
+MODES = {
+    "wRLS-F-5x5": {},
+    "RLS-F-5x5": {"weight_mode": 1},
+    "wRLS-NF-5x5": {"feature_mode": 1},
+    "wRLS-F-temporal": {"radius": 0},
+}
+
+
+def score_sequence(spec: synth.SceneSpec, overrides: Optional[dict] = None, device="cuda",
+                   skip: int = 4, frames: Optional[list] = None) -> Dict[str, float]:
+    p = W.wrls_params_default(**(overrides or {}))
+    s = W.Stream(spec.width, spec.height, p)
+    sc = synth.Scene(spec)
+    out = torch.empty(3, spec.height, spec.width, device=device)
+    prev_o = prev_t = None
+    rel, mse, flick, n = 0.0, 0.0, 0.0, 0
+    rel_in = 0.0
+    for t in range(spec.frames):
+        f = frames[t] if frames is not None else sc.frame(t, device=device)
+        rad, mot, truth = f["radiance"].to(device), f["motion"].to(device), f["truth"].to(device)
+        s.denoise(rad, mot, out)
+        if t >= skip:
+            rel += float(((out - truth) ** 2 / (truth * truth + 1e-2)).mean())
+            rel_in += float(((rad - truth) ** 2 / (truth * truth + 1e-2)).mean())
+            mse += float(((out.clamp(0, 1) - truth) ** 2).mean())
+            if prev_o is not None:
+                flick += float(((out - prev_o) - (truth - prev_t)).abs().mean())
+            n += 1
+        prev_o, prev_t = out.clone(), truth
+    W.wrls_stream_check(s.handle)
+    s.close()
+    mse /= max(n, 1)
+    return {"relmse": rel / max(n, 1), "relmse_input": rel_in / max(n, 1),
+            "psnr_db": 10 * math.log10(1.0 / max(mse, 1e-12)), "flicker": flick / max(n - 1, 1)}
+
+
+def ablation_report(spec: synth.SceneSpec, device="cuda") -> Dict[str, Dict[str, float]]:
+    frames = [synth.Scene(spec).frame(t, device=device) for t in range(spec.frames)]
+    return {name: score_sequence(spec, ov, device, frames=frames) for name, ov in MODES.items()}
+
+
+def noise_sweep(spec: synth.SceneSpec, mus=(-7.0, -5.5, -4.0, -2.5), device="cuda") -> Dict[float, Dict[str, float]]:
+    """Output error against the input noise level (log-variance mean mu), the analogue of
+    varying samples per pixel (Sec. 7.4, Fig. 16-17)."""
+    import dataclasses
+    return {mu: score_sequence(dataclasses.replace(spec, noise_mu=mu), None, device) for mu in mus}

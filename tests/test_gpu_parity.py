@@ -292,6 +292,37 @@ def test_pipelined_blend_rejected_for_16bit_state():
     s.close()
 
 
+def test_bounded_wait_expiry_is_reported_and_the_context_stays_usable():
+    """Withhold the state-window copy: each tile's bounded mbarrier wait runs out (about a
+    second), the kernel records WRLS_ERR_TIMEOUT and returns; the next frames work."""
+    import time
+    spec = synth.SceneSpec(64, 48, 4, seed=58, motion="pan", firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    p = W.wrls_params_default()
+    s = W.Stream(64, 48, p)
+    st = O.OracleStream(64, 48, oracle_params_from(p))
+    o = torch.empty(3, 48, 64, device="cuda")
+    s.denoise(fr[0]["radiance"].cuda(), fr[0]["motion"].cuda(), o)   # frame 0 restarts (no copy)
+    st.frame(fr[0]["radiance"].numpy(), fr[0]["motion"].numpy())
+    W.wrls_stream_check(s.handle)
+    W.wrls_stream_set_debug(s.handle, W.WRLS_DEBUG_WITHHOLD_STAGE_COPY)
+    t0 = time.time()
+    s.denoise(fr[1]["radiance"].cuda(), fr[1]["motion"].cuda(), o)
+    with pytest.raises(W.WrlsError) as e:
+        W.wrls_stream_check(s.handle)
+    assert e.value.status == W.WRLS_ERR_TIMEOUT and time.time() - t0 > 0.3
+    W.wrls_stream_set_debug(s.handle, 0)
+    s.reset()                                      # the timed-out frame left an unreliable state
+    s2 = O.OracleStream(64, 48, oracle_params_from(p))
+    for f in fr[2:]:
+        s.denoise(f["radiance"].cuda(), f["motion"].cuda(), o)
+        ref, _, _ = s2.frame(f["radiance"].numpy(), f["motion"].numpy())
+        torch.cuda.synchronize()
+        assert rel_err(o.cpu().numpy(), ref) <= REL_TOL
+    W.wrls_stream_check(s.handle)
+    s.close()
+
+
 def test_stream_check_reports_ok():
     spec = synth.SceneSpec(64, 64, 3, seed=53, motion="orbit")
     s = W.Stream(64, 64)
