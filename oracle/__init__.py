@@ -4,8 +4,11 @@ Test infrastructure only. Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this package.
 It shares no code with the CUDA library and never imports it.
 
-``build()`` compiles ``wrls_oracle.c`` with gcc (``-O2 -ffp-contract=off -fopenmp``) into
-``oracle/_build/libwrls_oracle.so``; ``OracleStream`` runs frames through it.
+``build()`` compiles ``wrls_oracle.c`` (the paper's predictor p = [1, z], d = 4) and
+``wrls_oracle_ext.c`` (any d <= 8: G-buffer predictor entries, sample-variance weight,
+nearest-pixel reprojection) with gcc (``-O2 -ffp-contract=off -fopenmp``) into
+``oracle/_build/libwrls_oracle.so``; ``OracleStream`` and ``OracleExtStream`` run frames
+through them.
 The constants in ``OracleParams`` defaults are the paper's where it gives one
 (lambda = 0.998 in Sec. 5.2, h = 0.75 in Sec. 5.3, alpha = 0.75 in Sec. 6, a 5x5 blend
 window in Sec. 5.3) and the readings of the C file's header elsewhere.
@@ -22,17 +25,19 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wrls_oracle.c")
+_SRC_EXT = os.path.join(_HERE, "wrls_oracle_ext.c")
 _LIB = os.path.join(_HERE, "_build", "libwrls_oracle.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle (plain C, gcc) if missing or older than its source."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_EXT))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, _SRC, _SRC_EXT, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -68,6 +73,25 @@ class OracleParams:
         return _Params(*dataclasses.astuple(self))
 
 
+class _ExtParams(ctypes.Structure):
+    _fields_ = _Params._fields_ + [("n_gbuf", ctypes.c_int), ("reproj_filter", ctypes.c_int)]
+
+
+@dataclasses.dataclass
+class OracleExtParams(OracleParams):
+    """Parameters of ``wrls_oracle_ext.c``: the paper's plus the alternatives it sets aside."""
+    n_gbuf: int = 0            # G-buffer planes appended to the predictor (0..4)
+    reproj_filter: int = 0     # 0 bilinear, 1 nearest pixel
+    # weight_mode 2: sample-variance weight
+
+    def c(self) -> _ExtParams:
+        return _ExtParams(*dataclasses.astuple(self))
+
+    @property
+    def dim(self) -> int:
+        return (4 if self.feature_mode == 0 else 1) + self.n_gbuf
+
+
 def lib():
     """Load the oracle library (``WRLS_ORACLE_LIB`` selects another build of the same
     source, which the mutation tests use to load deliberately broken copies)."""
@@ -84,6 +108,15 @@ def lib():
         _lib.wrls_oracle_blend.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
                                            dp, dp, dp]
         _lib.wrls_oracle_blend.restype = ctypes.c_int
+        _lib.wrls_oracle_ext_frame.argtypes = [ctypes.POINTER(_ExtParams), ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, dp, dp, dp, fp, fp, fp, fp, dp, dp, dp, dp,
+                                               dp, ctypes.POINTER(ctypes.c_ubyte)]
+        _lib.wrls_oracle_ext_frame.restype = ctypes.c_int
+        _lib.wrls_oracle_ext_blend.argtypes = [ctypes.POINTER(_ExtParams), ctypes.c_int, ctypes.c_int,
+                                               dp, dp, fp, dp]
+        _lib.wrls_oracle_ext_blend.restype = ctypes.c_int
+        _lib.wrls_oracle_ext_dim.argtypes = [ctypes.POINTER(_ExtParams)]
+        _lib.wrls_oracle_ext_dim.restype = ctypes.c_int
         _lib.wrls_oracle_set_threads.argtypes = [ctypes.c_int]
         _lib.wrls_oracle_get_threads.restype = ctypes.c_int
     return _lib
@@ -163,3 +196,55 @@ def blend(params: OracleParams, beta: np.ndarray, z: np.ndarray, width: int, hei
     if rc != 0:
         raise ValueError("wrls_oracle_blend rejected its arguments")
     return out
+
+
+def _fptr_opt(a: Optional[np.ndarray]):
+    return None if a is None else _fptr(a)
+
+
+class OracleExtStream:
+    """Per-stream state of the extended oracle: beta [n,3,d], full P [n,d,d], z [n,3]."""
+
+    def __init__(self, width: int, height: int, params: Optional[OracleExtParams] = None):
+        self.W, self.H = int(width), int(height)
+        self.params = params or OracleExtParams()
+        d, n = self.params.dim, self.W * self.H
+        self.beta = np.zeros((n, 3, d))
+        self.P = np.zeros((n, d, d))
+        self.z = np.zeros((n, 3))
+        self.need_reset = True
+
+    def reset(self) -> None:
+        self.need_reset = True
+
+    def frame(self, radiance: np.ndarray, motion: np.ndarray, variance: Optional[np.ndarray] = None,
+              gbuf: Optional[np.ndarray] = None):
+        """One frame. radiance (3,H,W), motion (2,H,W), variance (H,W) or None, gbuf
+        (>= n_gbuf,H,W) or None, all f32. Returns (out (3,H,W) f64, w (H,W), valid (H,W))."""
+        W, H, prm = self.W, self.H, self.params
+        d, n = prm.dim, W * H
+        rad = np.ascontiguousarray(radiance, dtype=np.float32)
+        mot = np.ascontiguousarray(motion, dtype=np.float32)
+        var = None if variance is None else np.ascontiguousarray(variance, dtype=np.float32).reshape(H, W)
+        g = None
+        if gbuf is not None and prm.n_gbuf > 0:
+            g = np.ascontiguousarray(np.asarray(gbuf, dtype=np.float32)[:prm.n_gbuf])
+            assert g.shape == (prm.n_gbuf, H, W)
+        bn, Pn, zn = np.empty((n, 3, d)), np.empty((n, d, d)), np.empty((n, 3))
+        out = np.empty((3, H, W))
+        w = np.empty((H, W))
+        valid = np.empty((H, W), dtype=np.uint8)
+        c = prm.c()
+        rc = lib().wrls_oracle_ext_frame(ctypes.byref(c), W, H, int(self.need_reset),
+                                         _dptr(self.beta), _dptr(self.P), _dptr(self.z),
+                                         _fptr(rad), _fptr(mot), _fptr_opt(var), _fptr_opt(g),
+                                         _dptr(bn), _dptr(Pn), _dptr(zn), _dptr(out), _dptr(w),
+                                         valid.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        if rc != 0:
+            raise ValueError("wrls_oracle_ext_frame rejected its arguments")
+        self.beta, self.P, self.z = bn, Pn, zn
+        self.need_reset = False
+        return out, w, valid.astype(bool)
+
+    def z_planes(self) -> np.ndarray:
+        return self.z.reshape(self.H, self.W, 3).transpose(2, 0, 1)

@@ -11,6 +11,7 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(ROOT, "oracle", "wrls_oracle.c")
+SRC_EXT = os.path.join(ROOT, "oracle", "wrls_oracle_ext.c")
 
 MUTANTS = {
     "eq8_residual_sign": ("double e = missing ? 0.0 : I[c] - pred;",
@@ -35,19 +36,42 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_planted_mistake(name, tmp_path):
-    old, new = MUTANTS[name]
-    src = open(SRC).read()
+# Mistakes planted in the extended oracle (d-generic predictor, variance weight, nearest
+# reprojection); caught by test_oracle_ext_pins.py.
+MUTANTS_EXT = {
+    "variance_weight_channel_factor": ("double dv2 = 3.0 * v / (m * m);", "double dv2 = v / (m * m);"),
+    "gbuffer_entries_reversed": ("if (isfinite(g[i])) p[a + i] = g[i];",
+                                 "if (isfinite(g[i])) p[a + prm->n_gbuf - 1 - i] = g[i];"),
+    "nearest_truncates": ("int xn = (int)floorf(qx + 0.5f)", "int xn = (int)floorf(qx)"),
+    "beta_stride_transposed": ("acc += wt[k] * beta_prev[tap[k] * 3 * d + c * d + a];",
+                               "acc += wt[k] * beta_prev[tap[k] * 3 * d + a * 3 + c];"),
+    "blend_neighbours_gbuffer": ("const double* pu = prm->blend_mode == 0 ? pi_ : pk;",
+                                 "const double* pu = pk;"),
+    "nonfinite_gbuffer_kept": ("if (missing || !g_ok) {\n                w = 0.0;",
+                               "if (missing) {\n                w = 0.0;"),
+    "ext_eq11_no_forgetting": ("Pn[a][b] = (P[a][b] - q[a] * pP[b]) / prm->lambda;",
+                               "Pn[a][b] = (P[a][b] - q[a] * pP[b]);"),
+    "ext_eq14_lambda_times_w": ("double denom = prm->lambda / w + pPp;", "double denom = prm->lambda * w + pPp;"),
+}
+
+_CASES = [(n, SRC, "test_oracle_pins.py") for n in sorted(MUTANTS)] + \
+         [(n, SRC_EXT, "test_oracle_ext_pins.py") for n in sorted(MUTANTS_EXT)]
+
+
+@pytest.mark.parametrize("name,src_path,pins", _CASES, ids=[c[0] for c in _CASES])
+def test_pins_catch_planted_mistake(name, src_path, pins, tmp_path):
+    old, new = (MUTANTS if src_path == SRC else MUTANTS_EXT)[name]
+    src = open(src_path).read()
     assert src.count(old) >= 1, "mutant anchor not found: " + name
     mutated = src.replace(old, new, 1)
-    c_path = tmp_path / "mutant.c"
+    c_path = tmp_path / os.path.basename(src_path)
     so_path = tmp_path / "libmutant.so"
     c_path.write_text(mutated)
+    other = SRC_EXT if src_path == SRC else SRC
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-                           "-o", str(so_path), str(c_path), "-lm"])
+                           "-o", str(so_path), str(c_path), other, "-lm"])
     env = dict(os.environ, WRLS_ORACLE_LIB=str(so_path), OMP_NUM_THREADS="2")
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                          os.path.join(HERE, "test_oracle_pins.py")],
+                          os.path.join(HERE, pins)],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, "no pin caught mutant %s:\n%s" % (name, res.stdout[-2000:])
