@@ -66,7 +66,13 @@ typedef struct wrls_params {
     float p_trace_max;   /* wind-up guard: P <- P0 when trace(P) > p_trace_max or a
                             diagonal entry <= 0; 0 (default) = off */
     int32_t radius;      /* blend window radius: 2 = 5x5 (Sec. 5.3, default); 0 = temporal only */
-    int32_t weight_mode; /* 0 = wRLS weight Eq. 13 (default); 1 = RLS, w = 1 (Eq. 10) */
+    int32_t weight_mode; /* 0 = wRLS weight Eq. 13 (default); 1 = RLS, w = 1 (Eq. 10);
+                            2 = sample-variance weight, the alternative Sec. 5.3 sets aside:
+                            w = exp(-3 sigma_j^2 / ((min(|I~_j|, |z_j|) + eps)^2 h^2)), the
+                            Eq. 13 form with ||I~ - z||^2 replaced by its expectation
+                            3 sigma^2 under the caller's per-pixel variance sigma_j^2 (the
+                            variance plane is then required; a negative or non-finite
+                            variance gives w = 0) */
     int32_t clamp_mode;  /* 0 = clamp history to the 3x3 min/max of I~ (Eq. 12 Psi); 1 = off */
     int32_t blend_mode;  /* 0 = neighbour k's model predicts pixel i: p_i . beta_k (default);
                             1 = bilateral average of the neighbours' own predictions */
@@ -74,9 +80,25 @@ typedef struct wrls_params {
     int32_t init_mode;   /* 0 = restarted pixels start from beta = 0 (default);
                             1 = feature pass-through, beta_c = e_{c+1} (prediction = z_c) */
     int32_t state_precision; /* wrls_state_precision; default WRLS_STATE_F32 */
-    int32_t n_features;  /* feature planes the caller may pass; the paper's predictor uses
-                            none of them (Sec. 4, 5.3); accepted and ignored */
+    int32_t n_features;  /* G-buffer feature planes the caller passes (features argument);
+                            the paper's predictor uses none of them (Sec. 4, 5.3) */
+    int32_t n_gbuf;      /* 0 (default, the paper's predictor) .. 4: the first n_gbuf feature
+                            planes are appended to the predictor, p = [1, z, g_1..g_n]
+                            (d = 4 + n), or [1, g_1..g_n] (d = 1 + n) with feature_mode 1 --
+                            the G-buffer regression of RLS denoisers that Sec. 2.1 and
+                            Sec. 5.2-5.3 discuss. Requires n_features >= n_gbuf. A non-finite
+                            G-buffer value enters p as 0 and gives the sample weight 0 */
+    int32_t reproj_filter; /* 0 = bilinear fetch of the reprojected model (default);
+                              1 = the model of the nearest pixel, floor(q + 0.5) per axis */
 } wrls_params;
+
+/*
+ * Extended path. Parameters with n_gbuf > 0, weight_mode 2 or reproj_filter 1 run on a
+ * separate pair of kernels (one thread per pixel, binary32 state of 3d + d(d+1)/2 + 3 planes
+ * per pixel: beta[c][a] at plane c*d + a, the upper triangle of P row by row, then z). They
+ * need state_precision WRLS_STATE_F32 (WRLS_ERR_INVALID_ARG otherwise), take no blend tile
+ * configuration or pipeline other than 0, and are not accepted by the batched ticks.
+ */
 
 typedef struct wrls_stream wrls_stream;
 
@@ -104,9 +126,10 @@ wrls_status wrls_stream_set_cuda_stream(wrls_stream* s, void* cuda_stream);
  *   radiance  3 x H x W, noisy linear HDR colour I~(t); required. A pixel with a
  *             non-finite channel is a missing sample (weight 0, it leaves its model
  *             unchanged apart from the forgetting factor).
- *   variance  H x W per-pixel variance, or NULL; not used by the paper's weight.
- *   features  n_features x H x W G-buffer planes, or NULL; not used by the paper's
- *             predictor.
+ *   variance  H x W per-pixel variance sigma^2 of the sample, or NULL; used only by
+ *             weight_mode 2 (required there).
+ *   features  n_features x H x W G-buffer planes, or NULL; the first n_gbuf planes enter
+ *             the predictor (required when n_gbuf > 0).
  *   motion    2 x H x W (v_x plane, then v_y plane) in pixels, backward: the previous
  *             position of pixel j is j + v_j (Table 2). Non-finite or out-of-image
  *             previous positions restart the pixel.
@@ -121,7 +144,8 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
  * copies radiance and motion to device buffers the stream owns (allocated on the first
  * call and kept until destroy), denoises, and copies the result back to `out`. Returns
  * after enqueuing; `out` is valid once the stream's CUDA stream is synchronised.
- * variance and features may be NULL (they are not used by the paper's method).
+ * variance and features may be NULL unless weight_mode 2 or n_gbuf > 0 needs them (then
+ * the variance plane and the first n_gbuf feature planes are copied as well).
  */
 wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const float* variance,
                                     const float* features, const float* motion, float* out);
@@ -136,7 +160,8 @@ void wrls_stream_destroy(wrls_stream* s);
  * Copy the current per-pixel state, decoded to binary32, into `dst` (device,
  * 25 x H x W planar): planes 0-11 beta[c][a] (channel c, coefficient a, plane c*4+a),
  * planes 12-21 the upper triangle of P row by row (00,01,02,03,11,12,13,22,23,33),
- * planes 22-24 z. WRLS_ERR_STATE before the first frame.
+ * planes 22-24 z. Streams on the extended path write 3d + d(d+1)/2 + 3 planes in the
+ * same order (beta[c][a] at plane c*d + a). WRLS_ERR_STATE before the first frame.
  */
 wrls_status wrls_stream_read_state(wrls_stream* s, float* dst);
 
@@ -158,7 +183,8 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
  * frame's output. times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per
  * launch (-1 for a configuration the state format does not offer) and *chosen (optional)
  * the selected configuration. Synchronises the stream. The batched tick uses the
- * one-CTA-per-tile configuration of the same tile shape.
+ * one-CTA-per-tile configuration of the same tile shape. Streams on the extended path have
+ * one blend configuration: every time is reported as -1 and 0 is chosen, without a launch.
  */
 #define WRLS_BLEND_CONFIGS 10
 wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen);
@@ -241,7 +267,8 @@ wrls_status wrls_batch_create(int max_streams, wrls_batch** out);
 wrls_status wrls_batch_set_cuda_stream(wrls_batch* b, void* cuda_stream);
 
 /* Run one tick over n frames (1 <= n <= max_streams; each stream at most once, all
- * streams of the same state precision and blend mode). The blend tile configuration is the
+ * streams of the same state precision and blend mode, none on the extended path). The
+ * blend tile configuration is the
  * one tuned for the largest stream of the tick. Asynchronous. */
 wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n);
 

@@ -26,11 +26,11 @@ void set_error(const char* fmt, ...) {
 static size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_stride,
-                         size_t* scale_offset_bytes) {
+                         size_t* scale_offset_bytes, int nplanes) {
   const size_t p = round_up((size_t)W, 32);
   const size_t ps = round_up(p * (size_t)H, 64);
   const size_t elem = precision == 0 ? 4 : 2;
-  size_t bytes = ps * elem * kNState;
+  size_t bytes = ps * elem * (size_t)nplanes;
   size_t scale_off = 0;
   if (precision != 0) {
     scale_off = round_up(bytes, 256);
@@ -122,10 +122,18 @@ bool make_kparams(const wrls_params& p, KParams* kp, const char** why) {
     return false;
   }
   if (p.radius < 0 || p.radius > kMaxRadius) { *why = "radius must be in [0, 2]"; return false; }
-  if ((unsigned)p.weight_mode > 1u || (unsigned)p.clamp_mode > 1u || (unsigned)p.blend_mode > 1u ||
+  if ((unsigned)p.weight_mode > 2u || (unsigned)p.clamp_mode > 1u || (unsigned)p.blend_mode > 1u ||
       (unsigned)p.feature_mode > 1u || (unsigned)p.init_mode > 1u || (unsigned)p.state_precision > 2u ||
-      p.n_features < 0) {
+      p.n_features < 0 || (unsigned)p.reproj_filter > 1u) {
     *why = "a mode field is out of range";
+    return false;
+  }
+  if (p.n_gbuf < 0 || p.n_gbuf > 4 || p.n_gbuf > p.n_features) {
+    *why = "n_gbuf must be in [0, 4] and at most n_features";
+    return false;
+  }
+  if (uses_ext(p) && p.state_precision != WRLS_STATE_F32) {
+    *why = "G-buffer predictor entries, weight_mode 2 and reproj_filter 1 need the binary32 state";
     return false;
   }
   const double log2e = 1.4426950408889634;
@@ -219,11 +227,15 @@ void wrls_params_default(wrls_params* p) {
   p->init_mode = 0;
   p->state_precision = WRLS_STATE_F32;
   p->n_features = 0;
+  p->n_gbuf = 0;
+  p->reproj_filter = 0;
 }
 
 size_t wrls_state_bytes(int width, int height, const wrls_params* p) {
   if (!p || !dims_ok(width, height) || (unsigned)p->state_precision > 2u) return 0;
-  return 2 * state_copy_layout(width, height, p->state_precision, nullptr, nullptr, nullptr);
+  if (p->struct_size != sizeof(wrls_params)) return 0;
+  const int np = uses_ext(*p) ? ext_planes(ext_dim(*p)) : kNState;
+  return 2 * state_copy_layout(width, height, p->state_precision, nullptr, nullptr, nullptr, np);
 }
 
 const char* wrls_last_error(void) { return g_err; }
@@ -241,13 +253,22 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
   if (!make_kparams(*p, &kp, &why)) { set_error("wrls_stream_create: %s", why); return WRLS_ERR_INVALID_ARG; }
   int pitch;
   size_t ps, scale_off;
-  const size_t copy = state_copy_layout(width, height, p->state_precision, &pitch, &ps, &scale_off);
+  const bool ext = uses_ext(*p);
+  const int dim = ext ? ext_dim(*p) : 4;
+  const int nplanes = ext ? ext_planes(dim) : kNState;
+  const size_t copy = state_copy_layout(width, height, p->state_precision, &pitch, &ps, &scale_off, nplanes);
   wrls_stream* s = new (std::nothrow) wrls_stream();
   if (!s) { set_error("wrls_stream_create: host allocation failed"); return WRLS_ERR_OOM; }
   s->W = width;
   s->H = height;
   s->prm = *p;
   s->kp = kp;
+  s->ext = ext;
+  s->dim = dim;
+  s->ep.kp = kp;
+  s->ep.n_gbuf = p->n_gbuf;
+  s->ep.reproj_filter = p->reproj_filter;
+  s->ep.wv_k = (float)(3.0 * 1.4426950408889634 / ((double)p->h * (double)p->h));
   cudaGetDevice(&s->device);
   // both state copies, then the error word (+0), the fused kernel's counters (+64) and tile
   // flags (+256)
@@ -280,7 +301,8 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
     d.H = height;
     d.pitch = pitch;
     d.plane_stride = ps;
-    if (!encode_stage_maps(d, &why)) {
+    d.nplanes = nplanes;
+    if (!ext && !encode_stage_maps(d, &why)) {
       cudaFree(s->mem);
       set_error("wrls_stream_create: %s", why);
       delete s;
@@ -299,8 +321,6 @@ wrls_status wrls_stream_set_cuda_stream(wrls_stream* s, void* cuda_stream) {
 
 wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const float* variance,
                                const float* features, const float* motion, float* out) {
-  (void)variance;
-  (void)features;
   if (!s || !radiance || !motion || !out) {
     set_error("wrls_denoise_frame: stream, radiance, motion and out must be non-NULL");
     return WRLS_ERR_INVALID_ARG;
@@ -317,6 +337,21 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
     set_error("wrls_denoise_frame: out overlaps an input");
     return WRLS_ERR_INVALID_ARG;
   }
+  if (s->ext) {
+    const bool need_var = s->prm.weight_mode == 2, need_g = s->prm.n_gbuf > 0;
+    if ((need_var && (!variance || !aligned4(variance))) || (need_g && (!features || !aligned4(features)))) {
+      set_error("wrls_denoise_frame: weight_mode 2 needs the variance plane and n_gbuf > 0 the feature "
+                "planes (4-byte aligned device pointers)");
+      return WRLS_ERR_INVALID_ARG;
+    }
+    const char* v = (const char*)variance;
+    const char* f = (const char*)features;
+    if ((need_var && o < v + n * 4 && v < o + 3 * n * 4) ||
+        (need_g && o < f + (size_t)s->prm.n_gbuf * n * 4 && f < o + 3 * n * 4)) {
+      set_error("wrls_denoise_frame: out overlaps an input");
+      return WRLS_ERR_INVALID_ARG;
+    }
+  }
   const StateDesc& prev = s->state[s->cur];
   const StateDesc& next = s->state[s->cur ^ 1];
   cudaEvent_t* ev = nullptr;
@@ -328,7 +363,15 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
     ev = s->tev + 3 * s->t_pending;
     WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
   }
-  if (s->pipeline == 1 || s->pipeline == 2) {
+  if (s->ext) {
+    const float* var = s->prm.weight_mode == 2 ? variance : nullptr;
+    const float* gb = s->prm.n_gbuf > 0 ? features : nullptr;
+    WRLS_CHECK_CUDA(launch_ext_update(s->ep, s->dim, prev, next, s->need_reset, radiance, motion, var, gb, s->cs),
+                    "wrls_denoise_frame: extended update kernel launch");
+    if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
+    WRLS_CHECK_CUDA(launch_ext_blend(s->ep, s->dim, next, gb, out, s->cs),
+                    "wrls_denoise_frame: extended blend kernel launch");
+  } else if (s->pipeline == 1 || s->pipeline == 2) {
     WRLS_CHECK_CUDA(launch_fused(s->pipeline, s->kp, prev, next, s->need_reset, radiance, motion, out, s->err, s->work,
                                  s->flags, (int)((s->frames + 1) & 0x7fffffff), s->cs),
                     "wrls_denoise_frame: fused kernel launch");
@@ -357,15 +400,21 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
 
 wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const float* variance,
                                     const float* features, const float* motion, float* out) {
-  (void)variance;
-  (void)features;
   if (!s || !radiance || !motion || !out) {
     set_error("wrls_denoise_frame_host: stream, radiance, motion and out must be non-NULL");
     return WRLS_ERR_INVALID_ARG;
   }
+  const bool need_var = s->prm.weight_mode == 2, need_g = s->prm.n_gbuf > 0;
+  if ((need_var && !variance) || (need_g && !features)) {
+    set_error("wrls_denoise_frame_host: weight_mode 2 needs the variance plane and n_gbuf > 0 the feature planes");
+    return WRLS_ERR_INVALID_ARG;
+  }
   const size_t n = (size_t)s->W * s->H;
+  // radiance 3, motion 2, output 3 planes, then the variance plane and the predictor's
+  // G-buffer planes of the extended path
+  const size_t extra = (size_t)(s->ext ? 1 + s->prm.n_gbuf : 0);
   if (!s->staging) {
-    cudaError_t e = cudaMalloc(&s->staging, 8 * n * sizeof(float));
+    cudaError_t e = cudaMalloc(&s->staging, (8 + extra) * n * sizeof(float));
     if (e != cudaSuccess) {
       cudaGetLastError();
       s->staging = nullptr;
@@ -376,11 +425,20 @@ wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const
   float* d_rad = s->staging;
   float* d_mot = s->staging + 3 * n;
   float* d_out = s->staging + 5 * n;
+  float* d_var = need_var ? s->staging + 8 * n : nullptr;
+  float* d_g = need_g ? s->staging + 9 * n : nullptr;
   WRLS_CHECK_CUDA(cudaMemcpyAsync(d_rad, radiance, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s->cs),
                   "wrls_denoise_frame_host: radiance copy");
   WRLS_CHECK_CUDA(cudaMemcpyAsync(d_mot, motion, 2 * n * sizeof(float), cudaMemcpyHostToDevice, s->cs),
                   "wrls_denoise_frame_host: motion copy");
-  wrls_status st = wrls_denoise_frame(s, d_rad, nullptr, nullptr, d_mot, d_out);
+  if (d_var)
+    WRLS_CHECK_CUDA(cudaMemcpyAsync(d_var, variance, n * sizeof(float), cudaMemcpyHostToDevice, s->cs),
+                    "wrls_denoise_frame_host: variance copy");
+  if (d_g)
+    WRLS_CHECK_CUDA(cudaMemcpyAsync(d_g, features, (size_t)s->prm.n_gbuf * n * sizeof(float),
+                                    cudaMemcpyHostToDevice, s->cs),
+                    "wrls_denoise_frame_host: feature copy");
+  wrls_status st = wrls_denoise_frame(s, d_rad, d_var, d_g, d_mot, d_out);
   if (st != WRLS_OK) return st;
   WRLS_CHECK_CUDA(cudaMemcpyAsync(out, d_out, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, s->cs),
                   "wrls_denoise_frame_host: output copy");
@@ -411,15 +469,20 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst) {
   if (!s || !dst) { set_error("wrls_stream_read_state: NULL argument"); return WRLS_ERR_INVALID_ARG; }
   if (!aligned4(dst)) { set_error("wrls_stream_read_state: dst must be 4-byte aligned"); return WRLS_ERR_INVALID_ARG; }
   if (!s->has_frame) { set_error("wrls_stream_read_state: no frame denoised yet"); return WRLS_ERR_STATE; }
-  WRLS_CHECK_CUDA(launch_read_state(s->state[s->cur], dst, s->cs), "wrls_stream_read_state: launch");
+  if (s->ext)
+    WRLS_CHECK_CUDA(launch_read_state_ext(s->state[s->cur], s->state[s->cur].nplanes, dst, s->cs),
+                    "wrls_stream_read_state: launch");
+  else
+    WRLS_CHECK_CUDA(launch_read_state(s->state[s->cur], dst, s->cs), "wrls_stream_read_state: launch");
   return WRLS_OK;
 }
 
 uint64_t wrls_stream_frames(const wrls_stream* s) { return s ? s->frames : 0; }
 
 wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused) {
-  if (!s || fused < 0 || fused > 3) {
-    set_error("wrls_stream_set_pipeline: bad stream or value %d (0, 3 = two kernels, 1, 2 = fused)", fused);
+  if (!s || fused < 0 || fused > 3 || (s->ext && fused != 0)) {
+    set_error("wrls_stream_set_pipeline: bad stream or value %d (0, 3 = two kernels, 1, 2 = fused; "
+              "extended path: 0 only)", fused);
     return WRLS_ERR_INVALID_ARG;
   }
   s->pipeline = fused;
@@ -427,7 +490,8 @@ wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused) {
 }
 
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config) {
-  if (!s || !blend_config_ok(config, s->prm.state_precision, s->state[0].blend_tma_ok, s->state[0].blend_tma2_ok)) {
+  if (!s || !blend_config_ok(config, s->prm.state_precision, s->state[0].blend_tma_ok, s->state[0].blend_tma2_ok) ||
+      (s->ext && config != 0)) {
     set_error("wrls_stream_set_blend_config: bad stream or configuration %d for this state format", config);
     return WRLS_ERR_INVALID_ARG;
   }
@@ -438,6 +502,12 @@ wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config) {
 wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen) {
   if (!s || !out || reps < 1) { set_error("wrls_stream_autotune: bad argument"); return WRLS_ERR_INVALID_ARG; }
   if (!s->has_frame) { set_error("wrls_stream_autotune: no frame denoised yet"); return WRLS_ERR_STATE; }
+  if (s->ext) {  // one blend configuration on the extended path
+    if (times_ms)
+      for (int c = 0; c < kBlendConfigs; ++c) times_ms[c] = -1.0f;
+    if (chosen) *chosen = 0;
+    return WRLS_OK;
+  }
   const StateDesc& cur = s->state[s->cur];
   cudaEvent_t e0, e1;
   WRLS_CHECK_CUDA(cudaEventCreate(&e0), "wrls_stream_autotune: event");

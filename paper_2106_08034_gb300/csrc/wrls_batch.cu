@@ -378,6 +378,11 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
       set_error("wrls_batch_tick: all streams of a tick must share one state precision and blend mode");
       return WRLS_ERR_INVALID_ARG;
     }
+    if (io.stream->ext) {
+      set_error("wrls_batch_tick: streams on the extended path (G-buffer predictor, variance weight, "
+                "nearest reprojection) are not batched");
+      return WRLS_ERR_INVALID_ARG;
+    }
     for (int k = 0; k < i; ++k)
       if (frames[k].stream == io.stream) {
         set_error("wrls_batch_tick: stream of frame %d appears twice", i);
@@ -589,6 +594,10 @@ extern "C" wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n
     }
     if (io.stream->prm.state_precision != prec || io.stream->prm.blend_mode != mode) {
       set_error("wrls_batch_tick_static: all streams of a call must share one state precision and blend mode");
+      return WRLS_ERR_INVALID_ARG;
+    }
+    if (io.stream->ext) {
+      set_error("wrls_batch_tick_static: streams on the extended path are not batched");
       return WRLS_ERR_INVALID_ARG;
     }
     for (int k = 0; k < i; ++k)

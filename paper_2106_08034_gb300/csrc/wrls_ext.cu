@@ -1,0 +1,401 @@
+// Extended predictor and weights (streams whose parameters select them):
+//   - G-buffer entries in the predictor, p = [1, z, g_1..g_n] (or [1, g_1..g_n] without the
+//     temporal feature), d up to 8: the regression on auxiliary G-buffer features of RLS
+//     denoisers that Sec. 2.1 and Sec. 5.2-5.3 discuss (and argue against for noisy
+//     path-traced G-buffers);
+//   - the sample-variance weight that Sec. 5.3 sets aside: Eq. 13 with the squared colour
+//     distance replaced by its expectation 3 sigma^2 under the per-pixel variance;
+//   - nearest-pixel reprojection (floor(q + 0.5) per axis, binary32).
+// Everything else is the paper's step for step: reprojection, Eq. 12 feature with the 3x3
+// clamp, Eq. 13 / Eq. 14 / Eq. 8 / Eq. 9 / Eq. 11, restarts, missing samples, the wind-up
+// guard and the 5x5 bilateral cross-prediction blend (Sec. 5.3).
+//
+// State: binary32 planes, d = predictor dimension: beta[c][a] (plane c*d + a), the upper
+// triangle of P row by row (d(d+1)/2 planes), z (3 planes). With d = 4 and the temporal
+// feature this is the paper layout of the fast kernels.
+//
+// These kernels are one thread per pixel with plain cached loads (32 x 8 tiles); the blend
+// stages the 36 x 12 window of beta, z and the per-pixel range factor in shared memory.
+#include "wrls_internal.h"
+
+namespace wrls {
+
+template <int D, bool F>
+struct ExtDim {
+  static constexpr int kG = D - (F ? 4 : 1);  // G-buffer entries of p
+  static constexpr int kNP = D * (D + 1) / 2;
+  static constexpr int kBeta = 0;
+  static constexpr int kP = 3 * D;
+  static constexpr int kZ = 3 * D + kNP;
+  static constexpr int kNS = kZ + 3;
+  static constexpr int kG0 = F ? 4 : 1;  // index of the first G-buffer entry in p
+};
+
+// Index of P(a, b), a <= b, in the packed upper triangle (row by row).
+__host__ __device__ constexpr int sym_index(int d, int a, int b) { return a * d - a * (a - 1) / 2 + (b - a); }
+
+__device__ __forceinline__ bool finite3(const float v[3]) {
+  return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+}
+
+constexpr int kExtTW = 32, kExtTH = 8;
+
+template <int D, bool F>
+__global__ void __launch_bounds__(kExtTW * kExtTH)
+    k_update_ext(const ExtParams ep, const int W, const int H, const int reset, const float* __restrict__ prev,
+                 float* __restrict__ next, const int pitch, const size_t ps, const float* __restrict__ rad,
+                 const float* __restrict__ mot, const float* __restrict__ var, const float* __restrict__ gbuf) {
+  using L = ExtDim<D, F>;
+  const KParams& kp = ep.kp;
+  const int x = blockIdx.x * kExtTW + threadIdx.x, y = blockIdx.y * kExtTH + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
+  const float I[3] = {__ldg(rad + j), __ldg(rad + npix + j), __ldg(rad + 2 * npix + j)};
+  const bool missing = !finite3(I);
+
+  // reprojection q = j + v_j (Table 2), binary32; NaN motion fails every comparison
+  const float qx = (float)x + __ldg(mot + j), qy = (float)y + __ldg(mot + npix + j);
+  const bool valid = !reset && qx >= 0.0f && qx <= (float)(W - 1) && qy >= 0.0f && qy <= (float)(H - 1);
+
+  float st[L::kNS];
+  if (valid) {
+    if (ep.reproj_filter == 1) {
+      const int xn = (int)floorf(qx + 0.5f), yn = (int)floorf(qy + 0.5f);
+      const float* src = prev + (size_t)yn * pitch + xn;
+#pragma unroll
+      for (int p = 0; p < L::kNS; ++p) st[p] = __ldg(src + p * ps);
+    } else {
+      const int x0 = (int)floorf(qx), y0 = (int)floorf(qy);
+      const float fx = qx - (float)x0, fy = qy - (float)y0;
+      const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
+      const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy);
+      const float w01 = (1.0f - fx) * fy, w11 = fx * fy;
+      const float* s00 = prev + (size_t)y0 * pitch + x0;
+      const float* s10 = prev + (size_t)y0 * pitch + x1;
+      const float* s01 = prev + (size_t)y1 * pitch + x0;
+      const float* s11 = prev + (size_t)y1 * pitch + x1;
+#pragma unroll
+      for (int p = 0; p < L::kNS; ++p) {
+        const size_t o = p * ps;
+        st[p] = w00 * __ldg(s00 + o) + w10 * __ldg(s10 + o) + (w01 * __ldg(s01 + o) + w11 * __ldg(s11 + o));
+      }
+    }
+  }
+
+  // Eq. 12 temporal feature (Psi = clamp to the 3x3 min/max of the finite samples)
+  float z[3];
+  if (valid) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool any = false;
+    if (kp.clamp_mode == 0) {
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = y + dy;
+        if (yy < 0 || yy >= H) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = x + dx;
+          if (xx < 0 || xx >= W) continue;
+          const size_t jj = (size_t)yy * W + xx;
+          const float In[3] = {__ldg(rad + jj), __ldg(rad + npix + jj), __ldg(rad + 2 * npix + jj)};
+          if (!finite3(In)) continue;
+          any = true;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            lo[c] = fminf(lo[c], In[c]);
+            hi[c] = fmaxf(hi[c], In[c]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float zc = st[L::kZ + c];
+      if (any) zc = fminf(fmaxf(zc, lo[c]), hi[c]);
+      z[c] = missing ? zc : fmaf(kp.alpha, zc, kp.one_m_alpha * I[c]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z[c] = missing ? 0.0f : I[c];
+#pragma unroll
+    for (int p = 0; p < L::kZ; ++p) st[p] = 0.0f;
+    if (kp.init_mode == 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (F) st[L::kBeta + c * D + c + 1] = 1.0f;
+        else st[L::kBeta + c * D] = z[c];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) st[L::kP + sym_index(D, a, a)] = kp.p0_delta;
+  }
+
+  // predictor p = [1, z, g] of frame t; a non-finite G-buffer value enters as 0, weight 0
+  float p[D];
+  p[0] = 1.0f;
+  if (F) {
+    p[1] = z[0];
+    p[2] = z[1];
+    p[3] = z[2];
+  }
+  bool g_ok = true;
+#pragma unroll
+  for (int i = 0; i < L::kG; ++i) {
+    const float g = __ldg(gbuf + (size_t)i * npix + j);
+    const bool f = isfinite(g);
+    p[L::kG0 + i] = f ? g : 0.0f;
+    g_ok = g_ok && f;
+  }
+
+  // weight: Eq. 13, RLS (w = 1) or the sample-variance weight
+  float w;
+  if (missing || !g_ok) {
+    w = 0.0f;
+  } else if (kp.weight_mode == 1) {
+    w = 1.0f;
+  } else {
+    const float nI = sqrtf(I[0] * I[0] + I[1] * I[1] + I[2] * I[2]);
+    const float nz = sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+    const float m = fminf(nI, nz) + kp.eps;
+    if (kp.weight_mode == 2) {
+      const float v = __ldg(var + j);
+      w = (isfinite(v) && v >= 0.0f) ? ex2_approx(-(v / (m * m)) * ep.wv_k) : 0.0f;
+    } else {
+      const float d0 = I[0] - z[0], d1 = I[1] - z[1], d2 = I[2] - z[2];
+      w = ex2_approx(-((d0 * d0 + d1 * d1 + d2 * d2) / (m * m)) * kp.w_k);
+    }
+  }
+
+  // k = P p, s = p^T P p; Eq. 14 gain q^w = (w / (lambda + w s)) k
+  float* P = st + L::kP;
+  float k[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int b = 0; b < D; ++b) acc = fmaf(P[a <= b ? sym_index(D, a, b) : sym_index(D, b, a)], p[b], acc);
+    k[a] = acc;
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) s = fmaf(p[a], k[a], s);
+  const float gain = w / (kp.lambda + w * s);
+  const bool use = !(missing || !g_ok);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float* beta = st + L::kBeta + c * D;
+    float pred = 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) pred = fmaf(p[a], beta[a], pred);
+    const float ge = gain * (use ? I[c] - pred : 0.0f);  // Eq. 8, Eq. 9
+#pragma unroll
+    for (int a = 0; a < D; ++a) beta[a] = fmaf(ge, k[a], beta[a]);
+  }
+  // Eq. 11: P <- (P - q^w p^T P) / lambda, p^T P = k^T
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = a; b < D; ++b) {
+      const int e = sym_index(D, a, b);
+      P[e] = (P[e] - gain * k[a] * k[b]) * kp.inv_lambda;
+    }
+  if (kp.p_trace_max > 0.0f) {
+    float tr = 0.0f;
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const float v = P[sym_index(D, a, a)];
+      tr += v;
+      bad = bad || !(v > 0.0f);
+    }
+    if (bad || tr > kp.p_trace_max) {
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b) P[sym_index(D, a, b)] = a == b ? kp.p0_delta : 0.0f;
+    }
+  }
+  st[L::kZ + 0] = z[0];
+  st[L::kZ + 1] = z[1];
+  st[L::kZ + 2] = z[2];
+  float* dst = next + (size_t)y * pitch + x;
+#pragma unroll
+  for (int q = 0; q < L::kNS; ++q) dst[q * ps] = st[q];
+}
+
+constexpr int kExtSW = kExtTW + 4, kExtSH = kExtTH + 4, kExtSP = kExtSW * kExtSH;
+constexpr float kExtFarZ = 1e18f;  // feature of an out-of-image neighbour: its blend weight is 0
+
+// 5x5 blend: out_i = sum_k b_ik (p_i beta_k) / sum_k b_ik (blend_mode 1: p_k beta_k), with
+// b_ik = 2^(spatial_ik - |z_i - z_k|^2 max(r_i, r_k)), r = log2(e) / (h_s^2 (|z| + eps)^2):
+// the Eq. 13 distance of the two features, min(|z_i|, |z_k|) taken through max(r_i, r_k).
+template <int D, bool F>
+__global__ void __launch_bounds__(kExtTW * kExtTH)
+    k_blend_ext(const ExtParams ep, const int W, const int H, const float* __restrict__ cur, const int pitch,
+                const size_t ps, const float* __restrict__ gbuf, float* __restrict__ out) {
+  using L = ExtDim<D, F>;
+  constexpr int NPL = 3 * D + 4;  // beta planes, z (3), range factor
+  static_assert(NPL * kExtSP * 4 <= 48 * 1024, "blend window exceeds static shared memory");
+  __shared__ float sm[NPL * kExtSP];
+  const KParams& kp = ep.kp;
+  const int bx0 = blockIdx.x * kExtTW, by0 = blockIdx.y * kExtTH;
+  const int tid = threadIdx.y * kExtTW + threadIdx.x;
+  for (int e = tid; e < kExtSP; e += kExtTW * kExtTH) {
+    const int gx = bx0 - 2 + e % kExtSW, gy = by0 - 2 + e / kExtSW;
+    if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+      const float* src = cur + (size_t)gy * pitch + gx;
+#pragma unroll
+      for (int a = 0; a < 3 * D; ++a) sm[a * kExtSP + e] = __ldg(src + (L::kBeta + a) * ps);
+      const float z0 = __ldg(src + (L::kZ + 0) * ps), z1 = __ldg(src + (L::kZ + 1) * ps),
+                  z2 = __ldg(src + (L::kZ + 2) * ps);
+      sm[(3 * D + 0) * kExtSP + e] = z0;
+      sm[(3 * D + 1) * kExtSP + e] = z1;
+      sm[(3 * D + 2) * kExtSP + e] = z2;
+      const float nz = sqrtf(z0 * z0 + z1 * z1 + z2 * z2) + kp.eps;
+      sm[(3 * D + 3) * kExtSP + e] = kp.range_k / (nz * nz);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3 * D; ++a) sm[a * kExtSP + e] = 0.0f;
+      sm[(3 * D + 0) * kExtSP + e] = kExtFarZ;
+      sm[(3 * D + 1) * kExtSP + e] = kExtFarZ;
+      sm[(3 * D + 2) * kExtSP + e] = kExtFarZ;
+      sm[(3 * D + 3) * kExtSP + e] = 0.0f;
+    }
+  }
+  __syncthreads();
+  const int x = bx0 + threadIdx.x, y = by0 + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
+  const int ei = (threadIdx.y + 2) * kExtSW + threadIdx.x + 2;
+  const float zi0 = sm[(3 * D + 0) * kExtSP + ei], zi1 = sm[(3 * D + 1) * kExtSP + ei],
+              zi2 = sm[(3 * D + 2) * kExtSP + ei];
+  const float ri = sm[(3 * D + 3) * kExtSP + ei];
+  float pi[D];
+  pi[0] = 1.0f;
+  if (F) {
+    pi[1] = zi0;
+    pi[2] = zi1;
+    pi[3] = zi2;
+  }
+#pragma unroll
+  for (int i = 0; i < L::kG; ++i) {
+    const float g = __ldg(gbuf + (size_t)i * npix + j);
+    pi[L::kG0 + i] = isfinite(g) ? g : 0.0f;
+  }
+  float num0 = 0.0f, num1 = 0.0f, num2 = 0.0f, den = 0.0f;
+#pragma unroll
+  for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 5; ++dx) {
+      const int e = ei + (dy - 2) * kExtSW + (dx - 2);
+      const float zk0 = sm[(3 * D + 0) * kExtSP + e], zk1 = sm[(3 * D + 1) * kExtSP + e],
+                  zk2 = sm[(3 * D + 2) * kExtSP + e];
+      const float rk = sm[(3 * D + 3) * kExtSP + e];
+      const float a0 = zi0 - zk0, a1 = zi1 - zk1, a2 = zi2 - zk2;
+      const float b = ex2_approx(kp.spatial[dy * 5 + dx] - (a0 * a0 + a1 * a1 + a2 * a2) * fmaxf(ri, rk));
+      float pu[D];
+      if (kp.blend_mode == 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) pu[a] = pi[a];
+      } else {
+        const int xx = x + dx - 2, yy = y + dy - 2;
+        const bool in = xx >= 0 && xx < W && yy >= 0 && yy < H;
+        pu[0] = 1.0f;
+        if (F) {
+          pu[1] = in ? zk0 : 0.0f;
+          pu[2] = in ? zk1 : 0.0f;
+          pu[3] = in ? zk2 : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < L::kG; ++i) {
+          const float g = in ? __ldg(gbuf + (size_t)i * npix + (size_t)yy * W + xx) : 0.0f;
+          pu[L::kG0 + i] = isfinite(g) ? g : 0.0f;
+        }
+      }
+      float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        p0 = fmaf(pu[a], sm[(0 * D + a) * kExtSP + e], p0);
+        p1 = fmaf(pu[a], sm[(1 * D + a) * kExtSP + e], p1);
+        p2 = fmaf(pu[a], sm[(2 * D + a) * kExtSP + e], p2);
+      }
+      num0 = fmaf(b, p0, num0);
+      num1 = fmaf(b, p1, num1);
+      num2 = fmaf(b, p2, num2);
+      den += b;
+    }
+  const float inv = 1.0f / den;
+  out[j] = num0 * inv;
+  out[npix + j] = num1 * inv;
+  out[2 * npix + j] = num2 * inv;
+}
+
+__global__ void k_read_state_ext(const int W, const int H, const float* __restrict__ cur, const int pitch,
+                                 const size_t ps, const int nplanes, float* __restrict__ dst) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W || y >= H) return;
+  const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
+  const float* src = cur + (size_t)y * pitch + x;
+  for (int p = 0; p < nplanes; ++p) dst[p * npix + j] = src[p * ps];
+}
+
+template <int D, bool F>
+static cudaError_t launch_ext_t(const ExtParams& ep, const StateDesc& prev, const StateDesc& next, bool reset,
+                                const float* rad, const float* mot, const float* var, const float* gbuf,
+                                float* out, cudaStream_t cs) {
+  const dim3 grid((prev.W + kExtTW - 1) / kExtTW, (prev.H + kExtTH - 1) / kExtTH), block(kExtTW, kExtTH);
+  k_update_ext<D, F><<<grid, block, 0, cs>>>(ep, prev.W, prev.H, reset ? 1 : 0, (const float*)prev.base,
+                                             (float*)next.base, prev.pitch, prev.plane_stride, rad, mot, var, gbuf);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !out) return e;
+  k_blend_ext<D, F><<<grid, block, 0, cs>>>(ep, next.W, next.H, (const float*)next.base, next.pitch,
+                                            next.plane_stride, gbuf, out);
+  return cudaGetLastError();
+}
+
+template <int D, bool F>
+static cudaError_t launch_ext_blend_t(const ExtParams& ep, const StateDesc& cur, const float* gbuf, float* out,
+                                      cudaStream_t cs) {
+  const dim3 grid((cur.W + kExtTW - 1) / kExtTW, (cur.H + kExtTH - 1) / kExtTH), block(kExtTW, kExtTH);
+  k_blend_ext<D, F><<<grid, block, 0, cs>>>(ep, cur.W, cur.H, (const float*)cur.base, cur.pitch,
+                                            cur.plane_stride, gbuf, out);
+  return cudaGetLastError();
+}
+
+int ext_dim(const wrls_params& p) { return (p.feature_mode == 0 ? 4 : 1) + p.n_gbuf; }
+
+int ext_planes(int d) { return 3 * d + d * (d + 1) / 2 + 3; }
+
+#define WRLS_EXT_DISPATCH(FN, ...)                                 \
+  switch ((ep.kp.feature_mode == 0 ? 0 : 16) + d) {                \
+    case 4: return FN<4, true>(__VA_ARGS__);                       \
+    case 5: return FN<5, true>(__VA_ARGS__);                       \
+    case 6: return FN<6, true>(__VA_ARGS__);                       \
+    case 7: return FN<7, true>(__VA_ARGS__);                       \
+    case 8: return FN<8, true>(__VA_ARGS__);                       \
+    case 17: return FN<1, false>(__VA_ARGS__);                     \
+    case 18: return FN<2, false>(__VA_ARGS__);                     \
+    case 19: return FN<3, false>(__VA_ARGS__);                     \
+    case 20: return FN<4, false>(__VA_ARGS__);                     \
+    case 21: return FN<5, false>(__VA_ARGS__);                     \
+    default: return cudaErrorInvalidValue;                         \
+  }
+
+// Update of frame t into `next`, then (out != NULL) the blend of `next` into out.
+cudaError_t launch_ext_update(const ExtParams& ep, int d, const StateDesc& prev, const StateDesc& next, bool reset,
+                              const float* rad, const float* mot, const float* var, const float* gbuf,
+                              cudaStream_t cs) {
+  WRLS_EXT_DISPATCH(launch_ext_t, ep, prev, next, reset, rad, mot, var, gbuf, nullptr, cs)
+}
+
+cudaError_t launch_ext_blend(const ExtParams& ep, int d, const StateDesc& cur, const float* gbuf, float* out,
+                             cudaStream_t cs) {
+  WRLS_EXT_DISPATCH(launch_ext_blend_t, ep, cur, gbuf, out, cs)
+}
+
+cudaError_t launch_read_state_ext(const StateDesc& cur, int nplanes, float* dst, cudaStream_t cs) {
+  const dim3 grid((cur.W + 127) / 128, cur.H);
+  k_read_state_ext<<<grid, 128, 0, cs>>>(cur.W, cur.H, (const float*)cur.base, cur.pitch, cur.plane_stride, nplanes,
+                                         dst);
+  return cudaGetLastError();
+}
+
+}  // namespace wrls

@@ -16,6 +16,7 @@ struct StateDesc {
   void* base = nullptr;
   float* scale = nullptr;
   int precision = 0;
+  int nplanes = kNState;
   int W = 0, H = 0, pitch = 0;
   size_t plane_stride = 0;  // in values
   StageMaps maps{};          // TMA tensor maps of this copy (planes; P scales for 16-bit)
@@ -29,9 +30,29 @@ struct StateDesc {
   StateF16 f16() const { return StateF16{(__half*)base, scale, plane_stride, pitch}; }
 };
 
-// Bytes of one state copy and its geometry.
+// Bytes of one state copy of `nplanes` planes and its geometry.
 size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_stride,
-                         size_t* scale_offset_bytes);
+                         size_t* scale_offset_bytes, int nplanes = kNState);
+
+// ---- extended predictor and weights (wrls_ext.cu) ----
+// Kernel parameters of a stream whose predictor has G-buffer entries, that weights by the
+// sample variance, or that reprojects to the nearest pixel.
+struct ExtParams {
+  KParams kp;
+  int n_gbuf;         // G-buffer entries of p
+  int reproj_filter;  // 0 bilinear, 1 nearest pixel
+  float wv_k;         // 3 log2(e) / h^2: exponent of the sample-variance weight in base 2
+};
+// True if the parameters need the extended kernels.
+inline bool uses_ext(const wrls_params& p) { return p.n_gbuf > 0 || p.weight_mode == 2 || p.reproj_filter == 1; }
+int ext_dim(const wrls_params& p);  // predictor dimension d
+int ext_planes(int d);              // state planes of dimension d: 3d + d(d+1)/2 + 3
+cudaError_t launch_ext_update(const ExtParams& ep, int d, const StateDesc& prev, const StateDesc& next, bool reset,
+                              const float* rad, const float* mot, const float* var, const float* gbuf,
+                              cudaStream_t cs);
+cudaError_t launch_ext_blend(const ExtParams& ep, int d, const StateDesc& cur, const float* gbuf, float* out,
+                             cudaStream_t cs);
+cudaError_t launch_read_state_ext(const StateDesc& cur, int nplanes, float* dst, cudaStream_t cs);
 
 // Host-side conversion of the public parameters (validated) into kernel parameters.
 bool make_kparams(const wrls_params& p, KParams* kp, const char** why);
@@ -83,6 +104,9 @@ struct wrls_stream {
   int W = 0, H = 0;
   wrls_params prm{};
   wrls::KParams kp{};
+  bool ext = false;             // extended predictor / weights (wrls_ext.cu kernels)
+  int dim = 4;                  // predictor dimension of the extended kernels
+  wrls::ExtParams ep{};
   wrls::StateDesc state[2];
   void* mem = nullptr;          // both state copies, then the device error word
   int* err = nullptr;           // device error word (WRLS_ERR_TIMEOUT from a bounded wait)

@@ -58,6 +58,7 @@ class wrls_params(ctypes.Structure):
         ("radius", ctypes.c_int32), ("weight_mode", ctypes.c_int32), ("clamp_mode", ctypes.c_int32),
         ("blend_mode", ctypes.c_int32), ("feature_mode", ctypes.c_int32), ("init_mode", ctypes.c_int32),
         ("state_precision", ctypes.c_int32), ("n_features", ctypes.c_int32),
+        ("n_gbuf", ctypes.c_int32), ("reproj_filter", ctypes.c_int32),
     ]
 
 
@@ -294,6 +295,16 @@ class Stream:
 
     def read_state(self, dst) -> None:
         wrls_stream_read_state(self.handle, dst)
+
+    @property
+    def state_planes(self) -> int:
+        """Planes written by read_state: 25 on the paper's path, 3d + d(d+1)/2 + 3 with the
+        extended predictor of dimension d."""
+        p = self.params
+        if p.n_gbuf > 0 or p.weight_mode == 2 or p.reproj_filter == 1:
+            d = (4 if p.feature_mode == 0 else 1) + p.n_gbuf
+            return 3 * d + d * (d + 1) // 2 + 3
+        return 25
 
     def close(self) -> None:
         if self.handle:

@@ -67,3 +67,27 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.wrls_denoise_frame(None, None, None, None, None, None) == W.WRLS_ERR_INVALID_ARG
     W.wrls_stream_destroy(0)
     W.wrls_batch_destroy(0)
+
+
+def test_extended_path_parameters_are_checked_on_the_host(lib):
+    """G-buffer predictor entries need n_features >= n_gbuf and at most 4 entries; the
+    extended path needs the binary32 state; weight_mode and reproj_filter are range-checked."""
+    bad = [dict(n_gbuf=2, n_features=1), dict(n_gbuf=5, n_features=7), dict(n_gbuf=-1),
+           dict(weight_mode=3), dict(reproj_filter=2),
+           dict(n_gbuf=1, n_features=1, state_precision=W.WRLS_STATE_BF16),
+           dict(weight_mode=2, state_precision=W.WRLS_STATE_F16),
+           dict(reproj_filter=1, state_precision=W.WRLS_STATE_BF16)]
+    for kw in bad:
+        with pytest.raises(W.WrlsError) as e:
+            W.wrls_stream_create(8, 8, W.wrls_params_default(**kw))
+        assert e.value.status == W.WRLS_ERR_INVALID_ARG, kw
+
+
+def test_extended_state_bytes(lib):
+    """3d + d(d+1)/2 + 3 binary32 planes per pixel and copy: d = 8 -> 63 planes (252 B/px)."""
+    base = W.wrls_state_bytes(640, 360, W.wrls_params_default())
+    for kw, planes in [(dict(n_gbuf=4, n_features=7), 63), (dict(n_gbuf=1, n_features=1), 33),
+                       (dict(weight_mode=2), 25), (dict(reproj_filter=1), 25),
+                       (dict(n_gbuf=2, n_features=2, feature_mode=1), 18)]:
+        b = W.wrls_state_bytes(640, 360, W.wrls_params_default(**kw))
+        assert abs(b / base - planes / 25) < 1e-3, (kw, b, base)
