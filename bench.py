@@ -35,6 +35,10 @@ BYTES_PATH_F32 = 232     # per pixel and frame for the whole path: + out 12
 # 1920x1080 frame, from the ncu capture summarised in profiles/k_update_pan_1080p.md (same
 # kernel build). Writes still held in L2 when the kernel ends are not counted by ncu.
 TRAFFIC_PER_LAUNCH = {"k_update": 248.867584e6 + 168.646400e6}
+# Extended path with the G-buffer predictor p = [1, z, g_1..g_4] (d = 8): the state is
+# 3d + d(d+1)/2 + 3 = 63 binary32 values (252 B) per pixel.
+BYTES_UPDATE_D8 = 252 + 12 + 8 + 16 + 252   # state read, radiance, motion, 4 G-buffer planes, state write
+BYTES_PATH_D8 = BYTES_UPDATE_D8 + 12         # + output
 
 
 def parse():
@@ -50,10 +54,15 @@ def parse():
                     help="use only the first N frames of the sequence (small profiling captures)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched BF16 16-stream leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-gbuf", action="store_true", help="skip the d = 8 G-buffer predictor leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--batched-passes", type=int, default=3)
     ap.add_argument("--pipeline", type=int, default=-1,
                     help="run this pipeline instead of timing them all (profiling captures)")
+    ap.add_argument("--seq", action="store_true",
+                    help="time only the sequence entry (with --pipeline, default 0, and --overlap)")
+    ap.add_argument("--overlap", type=int, default=1, help="blend CTAs per SM with --seq")
+    ap.add_argument("--no-seq", action="store_true", help="do not try the sequence entry")
     ap.add_argument("--blend-config", type=int, default=-1,
                     help="use this blend tile configuration instead of autotuning (profiling captures)")
     return ap.parse_args()
@@ -316,6 +325,51 @@ def run_reference(args):
     return 0
 
 
+def gbuf_leg(torch, W, synth, dev, peak, passes=3):
+    """The extended path with the G-buffer predictor p = [1, z, g_1..g_4] (d = 8) on the
+    1920x1080 pan workload: 30 resident frames, `passes` timed passes after one untimed."""
+    spec = synth.SceneSpec(1920, 1080, 30, seed=5, motion="pan", firefly_frac=0.05)
+    sc = synth.Scene(spec)
+    frames = []
+    for t in range(spec.frames):
+        f = sc.frame(t, device=dev)
+        frames.append((f["radiance"], f["motion"], f["features"]))
+    p = W.wrls_params_default(n_features=synth.N_FEATURES, n_gbuf=4)
+    cs = torch.cuda.Stream(device=dev)
+    s = W.Stream(spec.width, spec.height, p, cuda_stream=cs)
+    out = torch.empty(3, spec.height, spec.width, device=dev)
+
+    def one_pass():
+        for rad, mot, g in frames:
+            W.wrls_denoise_frame(s.handle, rad, None, g, mot, out)
+    torch.cuda.synchronize()
+    one_pass()
+    W.wrls_stream_enable_timing(s.handle, True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(cs)
+    for _ in range(passes):
+        one_pass()
+    b.record(cs)
+    b.synchronize()
+    upd, bl, n = W.wrls_stream_kernel_times(s.handle)
+    W.wrls_stream_check(s.handle)
+    s.close()
+    ms_frame = a.elapsed_time(b) / (passes * spec.frames)
+    px = spec.width * spec.height
+    upd_ms = upd / max(n, 1)
+    ach = BYTES_UPDATE_D8 * px / (upd_ms / 1e3) / 1e9
+    return {"workload": "1920x1080 pan, 30 frames, 5% x50 fireflies; predictor [1, z, depth, normal] (d = 8), "
+                        "f32 state (63 values/px)",
+            "value": round(px / (ms_frame / 1e3) / 1e6, 1), "unit": "Mpix/s", "ms_per_frame": round(ms_frame, 5),
+            "kernel_ms": {"update": round(upd_ms, 5), "blend": round(bl / max(n, 1), 5)},
+            "roofline": {"bound": "hbm", "kernel": "k_update_ext<8>", "bytes_per_px": BYTES_UPDATE_D8,
+                         "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4)},
+            "path": {"bytes_per_px": BYTES_PATH_D8,
+                     "frac": round(BYTES_PATH_D8 * px / (ms_frame / 1e3) / 1e9 / peak, 4)},
+            "frames_timed": passes * spec.frames}
+
+
 def run_wrls(args):
     import torch
     import torch.distributed as dist
@@ -352,7 +406,14 @@ def run_wrls(args):
     s = W.Stream(Wd, Hd, p, cuda_stream=cs)
     out = torch.empty(3, Hd, Wd, device=dev)
 
+    outs = [out] + [torch.empty(3, Hd, Wd, device=dev) for _ in range(2)]
+    seq_io = [(rad[t], None, None, mot[t], outs[t % 3]) for t in range(T)]
+    mode = {"seq": False}
+
     def step():
+        if mode["seq"]:  # one call: blend of frame t overlaps the update of frame t+1
+            W.wrls_denoise_sequence(s.handle, seq_io)
+            return
         for t in range(T):
             W.wrls_denoise_frame(s.handle, rad[t], None, None, mot[t], out)
 
@@ -367,9 +428,7 @@ def run_wrls(args):
         blend_times, blend_cfg = [], args.blend_config
     else:
         blend_times, blend_cfg = W.wrls_stream_autotune(s.handle, out, reps=5)
-    pipe_ms = {}
-    for pipeline in ((0, 1, 2, 3) if args.pipeline < 0 else ()):
-        W.wrls_stream_set_pipeline(s.handle, pipeline)
+    def time_step():
         step()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -377,8 +436,33 @@ def run_wrls(args):
         step()
         b.record(cs)
         b.synchronize()
-        pipe_ms[pipeline] = a.elapsed_time(b) / T
-    best_pipeline = min(pipe_ms, key=pipe_ms.get) if pipe_ms else args.pipeline
+        return a.elapsed_time(b) / T
+
+    pipe_ms = {}
+    for pipeline in ((0, 1, 2, 3) if args.pipeline < 0 else ()):
+        W.wrls_stream_set_pipeline(s.handle, pipeline)
+        pipe_ms[str(pipeline)] = time_step()
+    # the sequence entry over the two-kernel pipelines, with 1 or 2 blend CTAs per SM
+    seq_choices = [(pl, ov) for pl in (0, 3) for ov in (1, 2)] if args.pipeline < 0 and not args.no_seq else []
+    if args.seq:
+        seq_choices = [(max(args.pipeline, 0), args.overlap)]
+    mode["seq"] = True
+    for pl, ov in seq_choices:
+        W.wrls_stream_set_pipeline(s.handle, pl)
+        W.wrls_stream_set_overlap(s.handle, ov)
+        pipe_ms["seq%d/%d" % (pl, ov)] = time_step()
+    mode["seq"] = False
+    if pipe_ms:
+        best = min(pipe_ms, key=pipe_ms.get)
+    else:
+        best = str(args.pipeline)
+    if best.startswith("seq"):
+        mode["seq"] = True
+        pl, ov = best[3:].split("/")
+        best_pipeline = int(pl)
+        W.wrls_stream_set_overlap(s.handle, int(ov))
+    else:
+        best_pipeline = int(best)
     W.wrls_stream_set_pipeline(s.handle, best_pipeline)
     W.wrls_stream_enable_timing(s.handle, True)
 
@@ -444,6 +528,8 @@ def run_wrls(args):
         kbytes = BYTES_UPDATE_F32
         if best_pipeline == 0 and (Wd, Hd) == (1920, 1080):
             traffic = TRAFFIC_PER_LAUNCH["k_update"]
+        if mode["seq"]:
+            kname += "; timed while overlapping the previous frame's blend"
     else:
         kname, kbytes = "k_fused (reproject + Eq. 12-14 update + 5x5 blend, one launch)", BYTES_PATH_F32
     achieved = kbytes * px / (upd_per / 1e3) / 1e9
@@ -454,7 +540,8 @@ def run_wrls(args):
                 "bytes_per_px": kbytes,
                 "kernel_ms": {"update" if best_pipeline in (0, 3) else "fused": round(upd_per, 5),
                               "blend": round(bl_per, 5)},
-                "pipeline": best_pipeline, "pipeline_ms_per_frame": {str(k): round(v, 5) for k, v in pipe_ms.items()},
+                "pipeline": best_pipeline, "entry": "wrls_denoise_sequence" if mode["seq"] else "wrls_denoise_frame",
+                "pipeline_ms_per_frame": {str(k): round(v, 5) for k, v in pipe_ms.items()},
                 "blend_autotune_ms": [round(t, 5) for t in blend_times], "blend_config": blend_cfg,
                 "path": {"bytes_per_px": BYTES_PATH_F32,
                          "achieved": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9, 1),
@@ -464,12 +551,17 @@ def run_wrls(args):
     if not args.no_batched:
         batched = batched_leg(args, torch, W, synth, dev)
         batched["error"] = bf16_error_statement(torch, W, synth, dev)
+    gbuf = None
+    if not args.no_gbuf:
+        gbuf = gbuf_leg(torch, W, synth, dev, peak)
     serving = None
     if not args.no_serve:
         from paper_2106_08034_gb300 import serve
-        serving = serve.simulate(duration_s=args.serve_seconds)
+        serving = serve.simulate(duration_s=args.serve_seconds, rate_budget_mpix_s="auto")
         serving["workload"] = ("Poisson viewer sessions (2/s, lifetime U[10,60] s, 720p/1080p/1440p/2160p, "
-                               "30-60 fps, <= 64 resident, BF16 state), warm-started at the stationary population")
+                               "30-60 fps, <= 64 resident, BF16 state), warm-started at the stationary population; "
+                               "admission by device memory and by a pixel-rate budget of 0.75 x the calibrated "
+                               "batched throughput")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -489,7 +581,7 @@ def run_wrls(args):
                        "l2": "inputs larger than L2: state ping-pong 2 x 207 MB per frame",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched_bf16": batched, "serving": serving,
+            "batched_bf16": batched, "gbuf_predictor_d8": gbuf, "serving": serving,
             "gpu_launches": (2 if best_pipeline in (0, 3) else 1) * T * args.steps, "clocks": ck,
         }
         print(json.dumps(line), flush=True)

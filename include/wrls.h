@@ -101,6 +101,7 @@ typedef struct wrls_params {
  */
 
 typedef struct wrls_stream wrls_stream;
+struct wrls_frame_io; /* one frame's buffers, defined with the batched tick below */
 
 /* Fill *p with the defaults above. */
 void wrls_params_default(wrls_params* p);
@@ -149,6 +150,28 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
  */
 wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const float* variance,
                                     const float* features, const float* motion, float* out);
+
+/*
+ * Denoise n consecutive frames of one stream in one call, for callers that hold several
+ * frames at once (offline denoising of a recorded sequence, throughput runs). Results are
+ * those of n calls of wrls_denoise_frame. The frames' updates run in order on the stream's
+ * CUDA stream; the blend of frame t runs on a second CUDA stream that the library creates
+ * on the first call, so it overlaps the update of frame t+1 (both read the state of frame t;
+ * the update of frame t+2, which overwrites it, waits for that blend through an event).
+ * The memory-bound update and the arithmetic-bound blend then share the GPU. Before
+ * returning, the stream's CUDA stream is made to wait for the last blend, so all n outputs
+ * are complete once it is synchronised. frames[i].stream must be s or NULL; each frame
+ * follows the rules of wrls_denoise_frame, and the output of frame i must not overlap any
+ * buffer of frame i+1. With a fused pipeline (1, 2) or n = 1 the frames run one after
+ * another. Kernel timing (wrls_stream_enable_timing) records each kernel on the CUDA stream
+ * it runs on. Asynchronous.
+ */
+wrls_status wrls_denoise_sequence(wrls_stream* s, const struct wrls_frame_io* frames, int n);
+
+/* CTAs per SM of the persistent blend kernels (blend configurations 4-9) when they overlap
+ * an update in wrls_denoise_sequence: fewer leave the update room on every SM. 0 = as many
+ * as fit; default 1. */
+wrls_status wrls_stream_set_overlap(wrls_stream* s, int blend_ctas_per_sm);
 
 /* The next frame restarts every pixel (frame-0 behaviour). */
 wrls_status wrls_stream_reset(wrls_stream* s);
@@ -249,7 +272,7 @@ const char* wrls_last_error(void);
  * the launch is captured once in a CUDA graph per batch shape and replayed. Results are
  * identical to calling wrls_denoise_frame on each stream alone.
  */
-typedef struct {
+typedef struct wrls_frame_io {
     wrls_stream* stream;
     const float* radiance;  /* device, 3 x H x W */
     const float* variance;  /* device or NULL (unused) */

@@ -160,6 +160,7 @@ bool make_kparams(const wrls_params& p, KParams* kp, const char** why) {
   kp->feature_mode = p.feature_mode;
   kp->init_mode = p.init_mode;
   kp->debug_withhold_copy = 0;
+  kp->blend_ctas_cap = 0;
   return true;
 }
 
@@ -183,11 +184,12 @@ static bool dims_ok(int w, int h) { return w >= 1 && h >= 1 && w <= 16384 && h <
 // Add the durations of the recorded frames to the totals and clear the record.
 static wrls_status fold_timing(wrls_stream* s) {
   for (int i = 0; i < s->t_pending; ++i) {
-    cudaEvent_t* ev = s->tev + 3 * i;
+    cudaEvent_t* ev = s->tev + 4 * i;
     float a = 0.0f, b = 0.0f;
-    WRLS_CHECK_CUDA(cudaEventSynchronize(ev[2]), "kernel timing: event synchronize");
+    WRLS_CHECK_CUDA(cudaEventSynchronize(ev[1]), "kernel timing: event synchronize");
+    WRLS_CHECK_CUDA(cudaEventSynchronize(ev[3]), "kernel timing: event synchronize");
     WRLS_CHECK_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]), "kernel timing: elapsed time");
-    WRLS_CHECK_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]), "kernel timing: elapsed time");
+    WRLS_CHECK_CUDA(cudaEventElapsedTime(&b, ev[2], ev[3]), "kernel timing: elapsed time");
     s->t_update_ms += a;
     s->t_blend_ms += b;
     s->t_frames++;
@@ -198,11 +200,109 @@ static wrls_status fold_timing(wrls_stream* s) {
 
 static void free_timing(wrls_stream* s) {
   if (!s->tev) return;
-  for (int i = 0; i < 3 * wrls_stream::kTimingCap; ++i)
+  for (int i = 0; i < 4 * wrls_stream::kTimingCap; ++i)
     if (s->tev[i]) cudaEventDestroy(s->tev[i]);
   delete[] s->tev;
   s->tev = nullptr;
   s->t_pending = 0;
+}
+
+static bool overlaps(const void* a, size_t a_floats, const void* b, size_t b_floats) {
+  if (!a || !b) return false;
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + b_floats * 4 && y < x + a_floats * 4;
+}
+
+// Argument checks of one frame (per-frame and sequence entries).
+static wrls_status check_frame(const wrls_stream* s, const float* radiance, const float* variance,
+                               const float* features, const float* motion, const float* out, const char* who) {
+  if (!radiance || !motion || !out) {
+    set_error("%s: radiance, motion and out must be non-NULL", who);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  if (!aligned4(radiance) || !aligned4(motion) || !aligned4(out)) {
+    set_error("%s: buffers must be 4-byte aligned", who);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  const size_t n = (size_t)s->W * s->H;
+  if (overlaps(out, 3 * n, radiance, 3 * n) || overlaps(out, 3 * n, motion, 2 * n)) {
+    set_error("%s: out overlaps an input", who);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  if (s->ext) {
+    const bool need_var = s->prm.weight_mode == 2, need_g = s->prm.n_gbuf > 0;
+    if ((need_var && (!variance || !aligned4(variance))) || (need_g && (!features || !aligned4(features)))) {
+      set_error("%s: weight_mode 2 needs the variance plane and n_gbuf > 0 the feature planes "
+                "(4-byte aligned device pointers)", who);
+      return WRLS_ERR_INVALID_ARG;
+    }
+    if ((need_var && overlaps(out, 3 * n, variance, n)) ||
+        (need_g && overlaps(out, 3 * n, features, (size_t)s->prm.n_gbuf * n))) {
+      set_error("%s: out overlaps an input", who);
+      return WRLS_ERR_INVALID_ARG;
+    }
+  }
+  return WRLS_OK;
+}
+
+// The timing events of the next frame (NULL when timing is off).
+static wrls_status timing_slot(wrls_stream* s, cudaEvent_t** ev) {
+  *ev = nullptr;
+  if (!s->tev) return WRLS_OK;
+  if (s->t_pending == wrls_stream::kTimingCap) {
+    wrls_status st = fold_timing(s);
+    if (st != WRLS_OK) return st;
+  }
+  *ev = s->tev + 4 * s->t_pending;
+  return WRLS_OK;
+}
+
+// Update of the next frame (state copy cur -> cur ^ 1) on the stream's CUDA stream.
+static wrls_status enqueue_update(wrls_stream* s, const float* radiance, const float* variance,
+                                  const float* features, const float* motion, const char* who) {
+  const StateDesc& prev = s->state[s->cur];
+  const StateDesc& next = s->state[s->cur ^ 1];
+  cudaError_t e;
+  if (s->ext)
+    e = launch_ext_update(s->ep, s->dim, prev, next, s->need_reset, radiance, motion,
+                          s->prm.weight_mode == 2 ? variance : nullptr, s->prm.n_gbuf > 0 ? features : nullptr,
+                          s->cs);
+  else if (s->pipeline == 3)
+    e = launch_update_pipelined(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs);
+  else
+    e = launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs);
+  if (e != cudaSuccess) {
+    set_error("%s: update kernel launch: %s", who, cudaGetErrorString(e));
+    return WRLS_ERR_CUDA;
+  }
+  return WRLS_OK;
+}
+
+// Blend of the state copy the last update wrote (cur ^ 1) into out, on CUDA stream cs.
+static wrls_status enqueue_blend(wrls_stream* s, const KParams& kp, const float* features, float* out,
+                                 cudaStream_t cs, const char* who) {
+  const StateDesc& next = s->state[s->cur ^ 1];
+  cudaError_t e;
+  if (s->ext) {
+    ExtParams ep = s->ep;
+    ep.kp = kp;
+    e = launch_ext_blend(ep, s->dim, next, s->prm.n_gbuf > 0 ? features : nullptr, out, cs);
+  } else {
+    e = launch_blend(kp, s->blend_cfg, next, out, s->err, cs);
+  }
+  if (e != cudaSuccess) {
+    set_error("%s: blend kernel launch: %s", who, cudaGetErrorString(e));
+    return WRLS_ERR_CUDA;
+  }
+  return WRLS_OK;
+}
+
+static void advance(wrls_stream* s) {
+  s->cur ^= 1;
+  s->need_reset = false;
+  s->has_frame = true;
+  s->frames++;
 }
 
 extern "C" {
@@ -321,80 +421,135 @@ wrls_status wrls_stream_set_cuda_stream(wrls_stream* s, void* cuda_stream) {
 
 wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const float* variance,
                                const float* features, const float* motion, float* out) {
-  if (!s || !radiance || !motion || !out) {
-    set_error("wrls_denoise_frame: stream, radiance, motion and out must be non-NULL");
-    return WRLS_ERR_INVALID_ARG;
-  }
-  if (!aligned4(radiance) || !aligned4(motion) || !aligned4(out)) {
-    set_error("wrls_denoise_frame: buffers must be 4-byte aligned");
-    return WRLS_ERR_INVALID_ARG;
-  }
-  const size_t n = (size_t)s->W * s->H;
-  const char* o = (const char*)out;
-  const char* r = (const char*)radiance;
-  const char* m = (const char*)motion;
-  if ((o < r + 3 * n * 4 && r < o + 3 * n * 4) || (o < m + 2 * n * 4 && m < o + 3 * n * 4)) {
-    set_error("wrls_denoise_frame: out overlaps an input");
-    return WRLS_ERR_INVALID_ARG;
-  }
-  if (s->ext) {
-    const bool need_var = s->prm.weight_mode == 2, need_g = s->prm.n_gbuf > 0;
-    if ((need_var && (!variance || !aligned4(variance))) || (need_g && (!features || !aligned4(features)))) {
-      set_error("wrls_denoise_frame: weight_mode 2 needs the variance plane and n_gbuf > 0 the feature "
-                "planes (4-byte aligned device pointers)");
-      return WRLS_ERR_INVALID_ARG;
-    }
-    const char* v = (const char*)variance;
-    const char* f = (const char*)features;
-    if ((need_var && o < v + n * 4 && v < o + 3 * n * 4) ||
-        (need_g && o < f + (size_t)s->prm.n_gbuf * n * 4 && f < o + 3 * n * 4)) {
-      set_error("wrls_denoise_frame: out overlaps an input");
-      return WRLS_ERR_INVALID_ARG;
-    }
-  }
-  const StateDesc& prev = s->state[s->cur];
-  const StateDesc& next = s->state[s->cur ^ 1];
+  if (!s) { set_error("wrls_denoise_frame: stream is NULL"); return WRLS_ERR_INVALID_ARG; }
+  wrls_status st = check_frame(s, radiance, variance, features, motion, out, "wrls_denoise_frame");
+  if (st != WRLS_OK) return st;
   cudaEvent_t* ev = nullptr;
-  if (s->tev) {
-    if (s->t_pending == wrls_stream::kTimingCap) {
-      wrls_status st = fold_timing(s);
-      if (st != WRLS_OK) return st;
-    }
-    ev = s->tev + 3 * s->t_pending;
-    WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
-  }
-  if (s->ext) {
-    const float* var = s->prm.weight_mode == 2 ? variance : nullptr;
-    const float* gb = s->prm.n_gbuf > 0 ? features : nullptr;
-    WRLS_CHECK_CUDA(launch_ext_update(s->ep, s->dim, prev, next, s->need_reset, radiance, motion, var, gb, s->cs),
-                    "wrls_denoise_frame: extended update kernel launch");
-    if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
-    WRLS_CHECK_CUDA(launch_ext_blend(s->ep, s->dim, next, gb, out, s->cs),
-                    "wrls_denoise_frame: extended blend kernel launch");
-  } else if (s->pipeline == 1 || s->pipeline == 2) {
+  st = timing_slot(s, &ev);
+  if (st != WRLS_OK) return st;
+  if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
+  if (!s->ext && (s->pipeline == 1 || s->pipeline == 2)) {
+    const StateDesc& prev = s->state[s->cur];
+    const StateDesc& next = s->state[s->cur ^ 1];
     WRLS_CHECK_CUDA(launch_fused(s->pipeline, s->kp, prev, next, s->need_reset, radiance, motion, out, s->err, s->work,
                                  s->flags, (int)((s->frames + 1) & 0x7fffffff), s->cs),
                     "wrls_denoise_frame: fused kernel launch");
-    if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
+    if (ev) {
+      WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
+      WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
+    }
   } else {
-    if (s->pipeline == 3)
-      WRLS_CHECK_CUDA(launch_update_pipelined(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs),
-                      "wrls_denoise_frame: update kernel launch");
-    else
-      WRLS_CHECK_CUDA(launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs),
-                      "wrls_denoise_frame: update kernel launch");
-    if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
-    WRLS_CHECK_CUDA(launch_blend(s->kp, s->blend_cfg, next, out, s->err, s->cs),
-                    "wrls_denoise_frame: blend kernel launch");
+    st = enqueue_update(s, radiance, variance, features, motion, "wrls_denoise_frame");
+    if (st != WRLS_OK) return st;
+    if (ev) {
+      WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
+      WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
+    }
+    st = enqueue_blend(s, s->kp, features, out, s->cs, "wrls_denoise_frame");
+    if (st != WRLS_OK) return st;
   }
   if (ev) {
-    WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
+    WRLS_CHECK_CUDA(cudaEventRecord(ev[3], s->cs), "wrls_denoise_frame: event record");
     s->t_pending++;
   }
-  s->cur ^= 1;
-  s->need_reset = false;
-  s->has_frame = true;
-  s->frames++;
+  advance(s);
+  return WRLS_OK;
+}
+
+wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, int n) {
+  if (!s || !frames || n < 1) {
+    set_error("wrls_denoise_sequence: NULL stream or frames, or n < 1");
+    return WRLS_ERR_INVALID_ARG;
+  }
+  const size_t np = (size_t)s->W * s->H;
+  for (int i = 0; i < n; ++i) {
+    const wrls_frame_io& f = frames[i];
+    if (f.stream && f.stream != s) {
+      set_error("wrls_denoise_sequence: frame %d names another stream", i);
+      return WRLS_ERR_INVALID_ARG;
+    }
+    wrls_status st = check_frame(s, f.radiance, f.variance, f.features, f.motion, f.out, "wrls_denoise_sequence");
+    if (st != WRLS_OK) return st;
+    if (i + 1 < n) {  // the blend of frame i runs while the update of frame i+1 reads its inputs
+      const wrls_frame_io& g = frames[i + 1];
+      const bool need_var = s->ext && s->prm.weight_mode == 2, need_g = s->ext && s->prm.n_gbuf > 0;
+      if (overlaps(f.out, 3 * np, g.radiance, 3 * np) || overlaps(f.out, 3 * np, g.motion, 2 * np) ||
+          (need_var && overlaps(f.out, 3 * np, g.variance, np)) ||
+          (need_g && overlaps(f.out, 3 * np, g.features, (size_t)s->prm.n_gbuf * np)) ||
+          overlaps(f.out, 3 * np, g.out, 3 * np)) {
+        set_error("wrls_denoise_sequence: the output of frame %d overlaps a buffer of frame %d", i, i + 1);
+        return WRLS_ERR_INVALID_ARG;
+      }
+    }
+  }
+  const bool overlap = s->ext || s->pipeline == 0 || s->pipeline == 3;
+  if (!overlap || n == 1) {
+    for (int i = 0; i < n; ++i) {
+      const wrls_frame_io& f = frames[i];
+      wrls_status st = wrls_denoise_frame(s, f.radiance, f.variance, f.features, f.motion, f.out);
+      if (st != WRLS_OK) return st;
+    }
+    return WRLS_OK;
+  }
+  if (!s->side) {
+    WRLS_CHECK_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking), "wrls_denoise_sequence: stream");
+    cudaError_t e = cudaEventCreateWithFlags(&s->ev_u, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_b[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_b[1], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("wrls_denoise_sequence: event creation failed: %s", cudaGetErrorString(e));
+      return WRLS_ERR_CUDA;
+    }
+  }
+  KParams kpo = s->kp;
+  kpo.blend_ctas_cap = s->overlap_ctas;
+  wrls_status st = WRLS_OK;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == WRLS_OK) {
+      set_error("wrls_denoise_sequence: %s: %s", what, cudaGetErrorString(e));
+      st = WRLS_ERR_CUDA;
+    }
+    return st == WRLS_OK;
+  };
+  int last = -1;  // last frame whose blend was enqueued on the side stream
+  for (int i = 0; i < n && st == WRLS_OK; ++i) {
+    const wrls_frame_io& f = frames[i];
+    // The update of frame i overwrites the state copy that the blend of frame i-2 reads.
+    if (i >= 2 && !ck(cudaStreamWaitEvent(s->cs, s->ev_b[i & 1], 0), "wait")) break;
+    cudaEvent_t* ev = nullptr;
+    if ((st = timing_slot(s, &ev)) != WRLS_OK) break;
+    if (ev && !ck(cudaEventRecord(ev[0], s->cs), "event record")) break;
+    if ((st = enqueue_update(s, f.radiance, f.variance, f.features, f.motion, "wrls_denoise_sequence")) != WRLS_OK)
+      break;
+    if (ev && !ck(cudaEventRecord(ev[1], s->cs), "event record")) break;
+    if (!ck(cudaEventRecord(s->ev_u, s->cs), "event record")) break;
+    if (!ck(cudaStreamWaitEvent(s->side, s->ev_u, 0), "wait")) break;
+    if (ev && !ck(cudaEventRecord(ev[2], s->side), "event record")) break;
+    if ((st = enqueue_blend(s, kpo, f.features, f.out, s->side, "wrls_denoise_sequence")) != WRLS_OK) break;
+    last = i;
+    if (ev) {
+      if (!ck(cudaEventRecord(ev[3], s->side), "event record")) break;
+      s->t_pending++;
+    }
+    if (!ck(cudaEventRecord(s->ev_b[i & 1], s->side), "event record")) break;
+    advance(s);
+  }
+  // join: later work on the stream's CUDA stream sees every output (also after an error)
+  if (last >= 0) {
+    cudaError_t e = cudaEventRecord(s->ev_b[last & 1], s->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_b[last & 1], 0);
+    ck(e, "join");
+  }
+  return st;
+}
+
+wrls_status wrls_stream_set_overlap(wrls_stream* s, int blend_ctas_per_sm) {
+  if (!s || blend_ctas_per_sm < 0 || blend_ctas_per_sm > 32) {
+    set_error("wrls_stream_set_overlap: bad stream or value %d (0..32)", blend_ctas_per_sm);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  s->overlap_ctas = blend_ctas_per_sm;
   return WRLS_OK;
 }
 
@@ -457,7 +612,12 @@ void wrls_stream_destroy(wrls_stream* s) {
   cudaGetDevice(&prev_dev);
   if (prev_dev != s->device) cudaSetDevice(s->device);
   cudaStreamSynchronize(s->cs);
+  if (s->side) cudaStreamSynchronize(s->side);
   free_timing(s);
+  if (s->ev_u) cudaEventDestroy(s->ev_u);
+  for (int i = 0; i < 2; ++i)
+    if (s->ev_b[i]) cudaEventDestroy(s->ev_b[i]);
+  if (s->side) cudaStreamDestroy(s->side);
   cudaFree(s->mem);
   if (s->staging) cudaFree(s->staging);
   cudaGetLastError();
@@ -575,9 +735,9 @@ wrls_status wrls_stream_enable_timing(wrls_stream* s, int enable) {
     return WRLS_OK;
   }
   if (s->tev) return WRLS_OK;
-  s->tev = new (std::nothrow) cudaEvent_t[3 * wrls_stream::kTimingCap]();
+  s->tev = new (std::nothrow) cudaEvent_t[4 * wrls_stream::kTimingCap]();
   if (!s->tev) { set_error("wrls_stream_enable_timing: host allocation failed"); return WRLS_ERR_OOM; }
-  for (int i = 0; i < 3 * wrls_stream::kTimingCap; ++i) {
+  for (int i = 0; i < 4 * wrls_stream::kTimingCap; ++i) {
     cudaError_t e = cudaEventCreate(&s->tev[i]);
     if (e != cudaSuccess) {
       free_timing(s);

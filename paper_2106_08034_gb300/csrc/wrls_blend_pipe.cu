@@ -202,7 +202,8 @@ static cudaError_t launch_tma_cfg(const KParams& kp, const StateDesc& cur, float
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int n_tiles = ((cur.W + kTW - 1) / kTW) * ((cur.H + TH - 1) / TH);
-  int grid = sms * per_sm;
+  const int use = (kp.blend_ctas_cap > 0 && kp.blend_ctas_cap < per_sm) ? kp.blend_ctas_cap : per_sm;
+  int grid = sms * use;
   if (grid > n_tiles) grid = n_tiles;
   k_blend_tma<TH, R, MODE, NBUF><<<grid, nt, bytes, cs>>>(kp, cur.W, cur.H, cur.bmaps, out, err);
   return cudaGetLastError();
@@ -435,7 +436,8 @@ static cudaError_t launch_tma2_cfg(const KParams& kp, const StateDesc& cur, floa
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int n_tiles = ((cur.W + 2 * kTW - 1) / (2 * kTW)) * ((cur.H + TH - 1) / TH);
-  int grid = sms * per_sm;
+  const int use = (kp.blend_ctas_cap > 0 && kp.blend_ctas_cap < per_sm) ? kp.blend_ctas_cap : per_sm;
+  int grid = sms * use;
   if (grid > n_tiles) grid = n_tiles;
   k_blend_tma2<TH, R, MODE><<<grid, nt, bytes, cs>>>(kp, cur.W, cur.H, cur.bmaps, out, err);
   return cudaGetLastError();

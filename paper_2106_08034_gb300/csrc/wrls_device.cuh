@@ -42,6 +42,7 @@ struct KParams {
   int feature_mode;
   int init_mode;
   int debug_withhold_copy;  // test hook: arm the state-window barrier without issuing the copy
+  int blend_ctas_cap;       // host-side launch hint: CTAs per SM of the persistent blends (0 = all that fit)
 };
 
 // 2^x on the SFU (PTX ex2.approx, max relative error about 2^-22).

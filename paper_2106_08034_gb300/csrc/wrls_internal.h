@@ -122,9 +122,14 @@ struct wrls_stream {
   uint64_t frames = 0;
   float* staging = nullptr;     // device I/O buffers of wrls_denoise_frame_host
   int blend_cfg = 0;            // blend tile configuration
+  // wrls_denoise_sequence: blends on a second CUDA stream, ordered by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_u = nullptr;          // update of frame t done (side stream waits)
+  cudaEvent_t ev_b[2] = {nullptr, nullptr};  // blend of frame t done (update t+2 waits), by t & 1
+  int overlap_ctas = 1;                // CTAs per SM of a persistent blend that overlaps an update
   // kernel tracing
   static constexpr int kTimingCap = 8192;
-  cudaEvent_t* tev = nullptr;   // 3 events per recorded frame
+  cudaEvent_t* tev = nullptr;   // 4 events per recorded frame: update start/end, blend start/end
   int t_pending = 0;
   double t_update_ms = 0.0, t_blend_ms = 0.0;
   uint64_t t_frames = 0;

@@ -2,7 +2,10 @@
 the GPU through the C ABI, scored against the generator's clean truth.
 
 Modes (Sec. 5.3, Fig. 8-9): wRLS vs RLS (w = 1), feature p = [1, z] ("F") vs no feature
-p = [1] ("NF"), 5x5 spatio-temporal blend vs temporal-only output. Scores per sequence:
+p = [1] ("NF"), 5x5 spatio-temporal blend vs temporal-only output; and the alternatives the
+paper argues against (Sec. 2.1, 5.2-5.3): an RLS regression on the noisy G-buffers
+p = [1, depth, normal] ("RLS-G"), the same G-buffers appended to the paper's predictor
+("F+G", d = 8), and the sample-variance weight ("varW"). Scores per sequence:
 relMSE = mean((out - I)^2 / (I^2 + 0.01)), PSNR on colours clipped to [0, 1], and temporal
 flicker = mean over frames of mean |(out_t - out_{t-1}) - (I_t - I_{t-1})| (the part of the
 frame-to-frame change not explained by the truth). The first `skip` frames are excluded.
@@ -22,6 +25,9 @@ MODES = {
     "RLS-F-5x5": {"weight_mode": 1},
     "wRLS-NF-5x5": {"feature_mode": 1},
     "wRLS-F-temporal": {"radius": 0},
+    "RLS-G-5x5": {"weight_mode": 1, "feature_mode": 1, "n_gbuf": 4, "n_features": synth.N_FEATURES},
+    "wRLS-F+G-5x5": {"n_gbuf": 4, "n_features": synth.N_FEATURES},
+    "varW-F-5x5": {"weight_mode": 2},
 }
 
 
@@ -37,7 +43,7 @@ def score_sequence(spec: synth.SceneSpec, overrides: Optional[dict] = None, devi
     for t in range(spec.frames):
         f = frames[t] if frames is not None else sc.frame(t, device=device)
         rad, mot, truth = f["radiance"].to(device), f["motion"].to(device), f["truth"].to(device)
-        s.denoise(rad, mot, out)
+        s.denoise(rad, mot, out, variance=f["variance"].to(device), features=f["features"].to(device))
         if t >= skip:
             rel += float(((out - truth) ** 2 / (truth * truth + 1e-2)).mean())
             rel_in += float(((rad - truth) ** 2 / (truth * truth + 1e-2)).mean())

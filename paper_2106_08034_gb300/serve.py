@@ -1,9 +1,12 @@
 """Serving loop for interactive viewer sessions (continuous batching over the C ABI).
 
 A session is one viewer: a resolution, a frame rate and a lifetime. It is admitted when a
-session slot is free and the device memory its persistent per-pixel state needs
-(``wrls_state_bytes``) plus its output buffer fits the budget; otherwise it waits in the
-queue until a departure frees memory. Admitted sessions keep their state resident on the
+session slot is free, the device memory its persistent per-pixel state needs
+(``wrls_state_bytes``) plus its output buffer fits the memory budget, and (when a rate
+budget is set) the pixel rate of the admitted sessions plus its own width x height x fps
+stays within the rate budget -- a fraction of the throughput the GPU sustains, so that
+frames keep their deadline instead of queueing on the device; otherwise it waits in the
+queue until a departure frees room. Admitted sessions keep their state resident on the
 device across frames. Each round of the loop takes every session whose next frame is due,
 and denoises all of them with one ``wrls_batch_tick`` (one persistent, graph-captured
 launch pair over the (stream, tile) work list). Up to ``depth`` ticks are in flight, so
@@ -60,8 +63,12 @@ class Server:
     def __init__(self, hbm_budget_bytes: int, max_sessions: int = 64,
                  params: Optional[W.wrls_params] = None, depth: int = 2, deadline_s: float = 1 / 60,
                  rings: Optional[Dict[Tuple[int, int], Tuple[torch.Tensor, torch.Tensor]]] = None,
-                 cuda_stream: Optional[torch.cuda.Stream] = None):
+                 cuda_stream: Optional[torch.cuda.Stream] = None, rate_budget_px_s: Optional[float] = None,
+                 device="cuda"):
         self.budget = int(hbm_budget_bytes)
+        self.rate_budget = None if rate_budget_px_s is None else float(rate_budget_px_s)
+        self.rate = 0.0              # pixel rate (px/s) of the admitted sessions
+        self.device = device
         self.max_sessions = int(max_sessions)
         self.params = params if params is not None else W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
         self.depth = int(depth)
@@ -81,6 +88,7 @@ class Server:
         self.admitted_total = 0
         self.max_concurrent = 0
         self.rejected_budget = 0
+        self.waited_rate = 0         # admission attempts deferred by the rate budget
 
     # --- admission --------------------------------------------------------------------
     def session_bytes(self, w: int, h: int) -> int:
@@ -94,17 +102,22 @@ class Server:
         keep = []
         for s in self.queue:
             need = self.session_bytes(s.width, s.height)
-            if len(self.active) < self.max_sessions and self.used + need <= self.budget:
+            rate = s.width * s.height * s.fps
+            rate_ok = self.rate_budget is None or self.rate + rate <= self.rate_budget
+            if len(self.active) < self.max_sessions and self.used + need <= self.budget and rate_ok:
                 s.bytes = need
                 s.stream = W.Stream(s.width, s.height, self.params, cuda_stream=self.cs)
-                s.out = torch.empty(3, s.height, s.width, device="cuda")
+                s.out = torch.empty(3, s.height, s.width, device=self.device)
                 s.next_due = max(now, s.arrive)
                 self.active[s.sid] = s
                 self.used += need
+                self.rate += rate
                 self.admitted_total += 1
             else:
                 if self.used + need > self.budget:
                     self.rejected_budget += 1
+                if not rate_ok:
+                    self.waited_rate += 1
                 keep.append(s)
         self.queue = keep
         self.max_concurrent = max(self.max_concurrent, len(self.active))
@@ -119,6 +132,7 @@ class Server:
             return
         del self.active[sid]
         self.used -= s.bytes
+        self.rate -= s.width * s.height * s.fps
         s.stream.close()
         s.stream = None
         self._admit(now)
@@ -204,22 +218,61 @@ def make_rings(resolutions: Sequence[Tuple[int, int]], frames: int = 4, seed: in
     return rings
 
 
+def calibrate_throughput(rings, params: Optional[W.wrls_params] = None, per_res: int = 2,
+                         ticks: int = 20) -> float:
+    """Pixels per second that batched ticks sustain on this GPU: `per_res` streams of every
+    ring resolution in each tick, after a warm-up tick."""
+    p = params if params is not None else W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
+    cs = torch.cuda.Stream()
+    b = W.wrls_batch_create(per_res * len(rings))
+    W.wrls_batch_set_cuda_stream(b, cs)
+    streams, io, px = [], [], 0
+    for (w, h), (rad, mot) in rings.items():
+        for _ in range(per_res):
+            st = W.Stream(w, h, p, cuda_stream=cs)
+            out = torch.empty(3, h, w, device="cuda")
+            streams.append((st, out))
+            io.append((st.handle, rad[0], None, None, mot[0], out))
+            px += w * h
+    W.wrls_batch_tick(b, io)
+    cs.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record(cs)
+    for _ in range(ticks):
+        W.wrls_batch_tick(b, io)
+    e.record(cs)
+    e.synchronize()
+    rate = px * ticks / (a.elapsed_time(e) / 1e3)
+    W.wrls_batch_destroy(b)
+    for st, _ in streams:
+        st.close()
+    return rate
+
+
 def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0, 60.0),
              resolutions=synth.SERVING_RESOLUTIONS, fps_range=(30.0, 60.0), max_sessions: int = 64,
              hbm_budget_bytes: Optional[int] = None, deadline_s: float = 1 / 60, depth: int = 2,
              seed: int = 5, warm_start: bool = True, params: Optional[W.wrls_params] = None,
-             rings=None) -> dict:
+             rings=None, rate_budget_mpix_s=None, rate_fraction: float = 0.75) -> dict:
     """Run the serving loop in real time for `duration_s`. Sessions arrive as a Poisson
     process; with warm_start the run starts from the stationary population (Poisson count
-    with mean arrival_rate * mean lifetime, residual lifetimes uniform)."""
+    with mean arrival_rate * mean lifetime, residual lifetimes uniform).
+    rate_budget_mpix_s: None = admission by memory and slots only; "auto" = rate_fraction x
+    the throughput calibrate_throughput measures; a number = that budget in Mpix/s."""
     rng = random.Random(seed)
     if rings is None:
         rings = make_rings(resolutions)
     if hbm_budget_bytes is None:
         free, _ = torch.cuda.mem_get_info()
         hbm_budget_bytes = int(0.5 * free)
+    capacity = None
+    if rate_budget_mpix_s == "auto":
+        capacity = calibrate_throughput(rings, params)
+        rate_budget_mpix_s = rate_fraction * capacity / 1e6
     srv = Server(hbm_budget_bytes, max_sessions=max_sessions, params=params, depth=depth,
-                 deadline_s=deadline_s, rings=rings)
+                 deadline_s=deadline_s, rings=rings,
+                 rate_budget_px_s=None if rate_budget_mpix_s is None else rate_budget_mpix_s * 1e6)
     t0 = time.perf_counter()
     sid = 0
     initial = []
@@ -281,6 +334,9 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
         "missed_or_dropped": srv.missed, "admitted": srv.admitted_total,
         "max_concurrent": srv.max_concurrent, "queued_at_end": len(srv.queue),
         "hbm_budget_gb": round(hbm_budget_bytes / 1e9, 2), "hbm_used_gb_at_end": round(srv.used / 1e9, 3),
+        "rate_budget_mpix_s": None if srv.rate_budget is None else round(srv.rate_budget / 1e6, 1),
+        "calibrated_mpix_s": None if capacity is None else round(capacity / 1e6, 1),
+        "admitted_rate_mpix_s_at_end": round(srv.rate / 1e6, 1),
     }
     srv.close()
     return res

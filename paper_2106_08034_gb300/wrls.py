@@ -39,7 +39,7 @@ EXPORTED = [
     "wrls_stream_autotune", "wrls_stream_set_blend_config", "wrls_stream_set_pipeline",
     "wrls_stream_set_debug",
     "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
-    "wrls_batch_tick_static",
+    "wrls_batch_tick_static", "wrls_denoise_sequence", "wrls_stream_set_overlap",
 ]
 
 
@@ -105,6 +105,8 @@ def lib():
         "wrls_batch_tick": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
         "wrls_batch_destroy": (None, [vp]),
         "wrls_batch_tick_static": (i, [ctypes.POINTER(wrls_frame_io), i, vp]),
+        "wrls_denoise_sequence": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
+        "wrls_stream_set_overlap": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -169,6 +171,18 @@ def wrls_denoise_frame(stream: int, radiance, variance, features, motion, out) -
 def wrls_denoise_frame_host(stream: int, radiance, variance, features, motion, out) -> None:
     _check(lib().wrls_denoise_frame_host(stream, _ptr(radiance), _ptr(variance), _ptr(features),
                                          _ptr(motion), _ptr(out)))
+
+
+def wrls_denoise_sequence(stream: int, frames: Sequence[tuple]) -> None:
+    """frames: sequence of (radiance, variance, features, motion, out) of consecutive frames."""
+    arr = (wrls_frame_io * max(1, len(frames)))()
+    for k, (rad, var, feat, mot, out) in enumerate(frames):
+        arr[k] = wrls_frame_io(stream, _ptr(rad), _ptr(var), _ptr(feat), _ptr(mot), _ptr(out))
+    _check(lib().wrls_denoise_sequence(stream, arr, len(frames)))
+
+
+def wrls_stream_set_overlap(stream: int, blend_ctas_per_sm: int) -> None:
+    _check(lib().wrls_stream_set_overlap(stream, int(blend_ctas_per_sm)))
 
 
 def wrls_stream_reset(stream: int) -> None:

@@ -1,0 +1,128 @@
+"""wrls_denoise_sequence (blend of frame t overlapping the update of frame t+1 on a second
+CUDA stream) gives bitwise the outputs of per-frame wrls_denoise_frame calls, and of the
+oracle within the parity tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2106_08034_gb300 import synth
+from paper_2106_08034_gb300 import wrls as W
+
+from helpers import REL_TOL, cpu_frames, oracle_params_from, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2106_08034_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    W.lib()
+
+
+def _inputs(spec):
+    fr = cpu_frames(spec)
+    return ([f["radiance"].cuda() for f in fr], [f["motion"].cuda() for f in fr],
+            [f["variance"].cuda() for f in fr], [f["features"].cuda() for f in fr], fr)
+
+
+def _per_frame(spec, p, ins, pipeline=0, cfg=None):
+    rad, mot, var, feat, _ = ins
+    s = W.Stream(spec.width, spec.height, p)
+    W.wrls_stream_set_pipeline(s.handle, pipeline)
+    outs = []
+    for t in range(spec.frames):
+        o = torch.empty(3, spec.height, spec.width, device="cuda")
+        s.denoise(rad[t], mot[t], o, variance=var[t], features=feat[t])
+        if t == 0 and cfg is not None:
+            W.wrls_stream_set_blend_config(s.handle, cfg)
+        outs.append(o)
+    torch.cuda.synchronize()
+    s.close()
+    return [o.cpu() for o in outs]
+
+
+def _sequence(spec, p, ins, pipeline=0, cfg=None, chunk=None, overlap=None, cs=None):
+    rad, mot, var, feat, _ = ins
+    s = W.Stream(spec.width, spec.height, p, cuda_stream=cs)
+    W.wrls_stream_set_pipeline(s.handle, pipeline)
+    if overlap is not None:
+        W.wrls_stream_set_overlap(s.handle, overlap)
+    outs = [torch.empty(3, spec.height, spec.width, device="cuda") for _ in range(spec.frames)]
+    io = [(rad[t], var[t], feat[t], mot[t], outs[t]) for t in range(spec.frames)]
+    # frame 0 alone, so that the blend configuration applies from frame 1 as in _per_frame
+    W.wrls_denoise_sequence(s.handle, io[:1])
+    if cfg is not None:
+        W.wrls_stream_set_blend_config(s.handle, cfg)
+    step = chunk or spec.frames
+    for a in range(1, spec.frames, step):
+        W.wrls_denoise_sequence(s.handle, io[a:a + step])
+    W.wrls_stream_check(s.handle)  # synchronises the stream's CUDA stream (joined with the blends)
+    res = [o.cpu() for o in outs]
+    s.close()
+    return res
+
+
+@pytest.mark.parametrize("prec,pipeline,cfg", [(0, 0, None), (0, 0, 8), (0, 0, 9), (0, 0, 4), (0, 3, 8),
+                                               (0, 1, None), (1, 0, None), (2, 3, 2)])
+def test_sequence_equals_per_frame(prec, pipeline, cfg):
+    spec = synth.SceneSpec(200, 120, 14, seed=61, motion="orbit", firefly_frac=0.05)
+    ins = _inputs(spec)
+    p = W.wrls_params_default(state_precision=prec)
+    ref = _per_frame(spec, p, ins, pipeline, cfg)
+    for chunk, overlap in ((None, None), (5, 0), (3, 2)):
+        got = _sequence(spec, p, ins, pipeline, cfg, chunk, overlap)
+        for t in range(spec.frames):
+            assert torch.equal(got[t], ref[t]), (t, chunk, overlap)
+
+
+def test_sequence_extended_path_equals_per_frame():
+    spec = synth.SceneSpec(150, 90, 10, seed=62, motion="pan", firefly_frac=0.05)
+    ins = _inputs(spec)
+    p = W.wrls_params_default(n_features=synth.N_FEATURES, n_gbuf=3, weight_mode=2)
+    ref = _per_frame(spec, p, ins)
+    got = _sequence(spec, p, ins, chunk=4)
+    for t in range(spec.frames):
+        assert torch.equal(got[t], ref[t]), t
+
+
+def test_sequence_matches_oracle_full_hd():
+    """1920 x 1080 through the sequence entry on a non-default CUDA stream (the benchmark's
+    launch configuration): every pixel of 5 frames within the parity tolerance."""
+    spec = synth.SceneSpec(1920, 1080, 5, seed=63, motion="pan", firefly_frac=0.05)
+    ins = _inputs(spec)
+    p = W.wrls_params_default()
+    got = _sequence(spec, p, ins, cfg=8, cs=torch.cuda.Stream())
+    st = O.OracleStream(spec.width, spec.height, oracle_params_from(p))
+    for t, f in enumerate(ins[4]):
+        ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
+        assert rel_err(got[t].numpy(), ref) <= REL_TOL, t
+
+
+def test_sequence_kernel_timing_and_rejections():
+    spec = synth.SceneSpec(128, 64, 6, seed=64, motion="pan")
+    rad, mot, var, feat, _ = _inputs(spec)
+    s = W.Stream(spec.width, spec.height)
+    W.wrls_stream_enable_timing(s.handle, True)
+    outs = [torch.empty(3, spec.height, spec.width, device="cuda") for _ in range(spec.frames)]
+    W.wrls_denoise_sequence(s.handle, [(rad[t], None, None, mot[t], outs[t]) for t in range(spec.frames)])
+    u, b, n = W.wrls_stream_kernel_times(s.handle)
+    assert n == spec.frames and u > 0 and b > 0
+    # the output of frame i may not overlap a buffer of frame i+1
+    with pytest.raises(W.WrlsError) as e:
+        W.wrls_denoise_sequence(s.handle, [(rad[0], None, None, mot[0], outs[0]),
+                                           (rad[1], None, None, mot[1], outs[0])])
+    assert e.value.status == W.WRLS_ERR_INVALID_ARG
+    with pytest.raises(W.WrlsError):
+        W.wrls_denoise_sequence(s.handle, [])
+    with pytest.raises(W.WrlsError):
+        W.wrls_stream_set_overlap(s.handle, -1)
+    other = W.Stream(spec.width, spec.height)
+    arr = (W.wrls_frame_io * 1)()
+    arr[0] = W.wrls_frame_io(other.handle, rad[0].data_ptr(), None, None, mot[0].data_ptr(), outs[0].data_ptr())
+    assert W.lib().wrls_denoise_sequence(s.handle, arr, 1) == W.WRLS_ERR_INVALID_ARG
+    W.wrls_stream_check(s.handle)
+    other.close()
+    s.close()

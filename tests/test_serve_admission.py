@@ -1,0 +1,65 @@
+"""Admission of the serving loop (paper_2106_08034_gb300.serve.Server) on the CPU: session
+slots, the device-memory budget (wrls_state_bytes, a host-only call) and the pixel-rate
+budget. Stream and batch objects are replaced by fakes, so no GPU is touched."""
+import pytest
+
+from paper_2106_08034_gb300 import build as B
+from paper_2106_08034_gb300 import serve
+from paper_2106_08034_gb300 import wrls as W
+
+
+class _FakeStream:
+    def __init__(self, w, h, params=None, cuda_stream=None):
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+@pytest.fixture
+def fake_gpu(monkeypatch):
+    B.build()
+    W.lib()
+    monkeypatch.setattr(serve.W, "Stream", _FakeStream)
+    monkeypatch.setattr(serve.W, "wrls_batch_create", lambda n: 1)
+    monkeypatch.setattr(serve.W, "wrls_batch_set_cuda_stream", lambda b, c: None)
+
+
+def _server(**kw):
+    kw.setdefault("hbm_budget_bytes", 10 ** 12)
+    return serve.Server(cuda_stream=object(), device="cpu", **kw)
+
+
+def test_rate_budget_defers_and_releases(fake_gpu):
+    r1080 = 1920 * 1080 * 60.0
+    srv = _server(max_sessions=8, rate_budget_px_s=2.5 * r1080)
+    for i in range(3):
+        srv.request(serve.Session(i, 1920, 1080, 60.0, 0.0, 100.0), 0.0)
+    assert sorted(srv.active) == [0, 1] and [s.sid for s in srv.queue] == [2]
+    assert srv.waited_rate >= 1 and abs(srv.rate - 2 * r1080) < 1
+    # a 720p30 session fits in the half 1080p60 that is left, ahead of the queued 1080p60
+    srv.request(serve.Session(3, 1280, 720, 30.0, 0.0, 100.0), 0.0)
+    assert 3 in srv.active and [s.sid for s in srv.queue] == [2]
+    srv.depart(0, 1.0)
+    assert 2 in srv.active and not srv.queue
+    assert abs(srv.rate - (2 * r1080 + 1280 * 720 * 30.0)) < 1
+
+
+def test_memory_budget_and_slots(fake_gpu):
+    p = W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
+    one = W.wrls_state_bytes(1920, 1080, p) + 3 * 1920 * 1080 * 4
+    srv = _server(hbm_budget_bytes=2 * one + 10, max_sessions=8, params=p)
+    for i in range(3):
+        srv.request(serve.Session(i, 1920, 1080, 30.0, 0.0, 100.0), 0.0)
+    assert len(srv.active) == 2 and srv.rejected_budget >= 1 and srv.used == 2 * one
+    srv = _server(max_sessions=2)
+    for i in range(3):
+        srv.request(serve.Session(i, 640, 360, 30.0, 0.0, 100.0), 0.0)
+    assert len(srv.active) == 2 and len(srv.queue) == 1
+
+
+def test_no_rate_budget_admits_by_memory_only(fake_gpu):
+    srv = _server(max_sessions=64)
+    for i in range(10):
+        srv.request(serve.Session(i, 3840, 2160, 60.0, 0.0, 100.0), 0.0)
+    assert len(srv.active) == 10 and srv.waited_rate == 0
