@@ -6,7 +6,8 @@ It shares no code with the CUDA library and never imports it.
 
 ``build()`` compiles ``wrls_oracle.c`` (the paper's predictor p = [1, z], d = 4) and
 ``wrls_oracle_ext.c`` (any d <= 8: G-buffer predictor entries, sample-variance weight,
-nearest-pixel reprojection) with gcc (``-O2 -ffp-contract=off -fopenmp``) into
+nearest-pixel reprojection) and ``wrls_oracle_upstream.c`` (pixel reconstruction filter,
+velocity from first-collision world positions) with gcc (``-O2 -ffp-contract=off -fopenmp``) into
 ``oracle/_build/libwrls_oracle.so``; ``OracleStream`` and ``OracleExtStream`` run frames
 through them.
 The constants in ``OracleParams`` defaults are the paper's where it gives one
@@ -26,18 +27,20 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wrls_oracle.c")
 _SRC_EXT = os.path.join(_HERE, "wrls_oracle_ext.c")
+_SRC_UP = os.path.join(_HERE, "wrls_oracle_upstream.c")
+SOURCES = (_SRC, _SRC_EXT, _SRC_UP)
 _LIB = os.path.join(_HERE, "_build", "libwrls_oracle.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle (plain C, gcc) if missing or older than its source."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_EXT))
+    newest = max(os.path.getmtime(p) for p in SOURCES)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, _SRC_EXT, "-lm"])
+                               "-o", tmp, *SOURCES, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -117,6 +120,11 @@ def lib():
         _lib.wrls_oracle_ext_blend.restype = ctypes.c_int
         _lib.wrls_oracle_ext_dim.argtypes = [ctypes.POINTER(_ExtParams)]
         _lib.wrls_oracle_ext_dim.restype = ctypes.c_int
+        _lib.wrls_oracle_reconstruct.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, ctypes.c_double,
+                                                 ctypes.c_double, dp, dp]
+        _lib.wrls_oracle_reconstruct.restype = ctypes.c_int
+        _lib.wrls_oracle_velocity.argtypes = [ctypes.c_int, ctypes.c_int, fp, dp, ctypes.c_int, dp]
+        _lib.wrls_oracle_velocity.restype = ctypes.c_int
         _lib.wrls_oracle_set_threads.argtypes = [ctypes.c_int]
         _lib.wrls_oracle_get_threads.restype = ctypes.c_int
     return _lib
@@ -248,3 +256,30 @@ class OracleExtStream:
 
     def z_planes(self) -> np.ndarray:
         return self.z.reshape(self.H, self.W, 3).transpose(2, 0, 1)
+
+
+def reconstruct(samples: np.ndarray, sigma: float = 0.5, radius: float = 1.5, with_variance: bool = True):
+    """Pixel reconstruction filter. samples (spp, 5, H, W) f32 (r, g, b, ox, oy).
+    Returns (radiance (3,H,W) f64, variance (H,W) f64 or None)."""
+    smp = np.ascontiguousarray(samples, dtype=np.float32)
+    spp, five, H, W = smp.shape
+    assert five == 5
+    out = np.empty((3, H, W))
+    var = np.empty((H, W)) if with_variance else None
+    rc = lib().wrls_oracle_reconstruct(W, H, spp, _fptr(smp), float(sigma), float(radius), _dptr(out), _dptr(var))
+    if rc != 0:
+        raise ValueError("wrls_oracle_reconstruct rejected its arguments")
+    return out, var
+
+
+def velocity(world: np.ndarray, prev_view_proj: np.ndarray, miss_policy: int = 0) -> np.ndarray:
+    """Backward motion (2,H,W) f64 from first-collision world positions (3,H,W) f32 and the
+    previous frame's 4x4 view-projection matrix (row-major)."""
+    wd = np.ascontiguousarray(world, dtype=np.float32)
+    _, H, W = wd.shape
+    M = np.ascontiguousarray(prev_view_proj, dtype=np.float64).reshape(16)
+    mot = np.empty((2, H, W))
+    rc = lib().wrls_oracle_velocity(W, H, _fptr(wd), _dptr(M), int(miss_policy), _dptr(mot))
+    if rc != 0:
+        raise ValueError("wrls_oracle_velocity rejected its arguments")
+    return mot

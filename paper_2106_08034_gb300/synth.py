@@ -273,3 +273,78 @@ class Scene:
             for k in keys:
                 acc[k].append(f[k])
         return {k: torch.stack(v) for k, v in acc.items()}
+
+
+# ---- raw samples and camera geometry (inputs of the reconstruction and velocity steps) ----
+
+def raw_samples(scene: "Scene", t: int, spp: int, device="cpu") -> torch.Tensor:
+    """spp light-path samples per pixel of frame t: (spp, 5, H, W) f32 planes r, g, b, ox, oy.
+    Offsets uniform in [-0.5, 0.5) from the pixel centre; each sample is the pixel's clean
+    colour plus Gaussian noise of variance spp * sigma_j^2 (so the pixel mean has the frame's
+    variance sigma_j^2), times the firefly gain with the scene's firefly probability."""
+    sp = scene.spec
+    H, W = sp.height, sp.width
+    truth, _ = scene._clean(t, device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed((sp.seed * 2_000_003 + t * 104_729 + spp * 31 + 777) & 0x7FFFFFFFFFFF)
+    g_var = torch.randn(H, W, generator=gen, device=device, dtype=torch.float32)
+    var = torch.exp(sp.noise_mu + sp.noise_sigma * g_var)
+    out = torch.empty(spp, 5, H, W, device=device, dtype=torch.float32)
+    for s in range(spp):
+        noise = torch.randn(3, H, W, generator=gen, device=device, dtype=torch.float32)
+        col = truth + torch.sqrt(var * spp)[None] * noise
+        if sp.firefly_frac > 0 and not sp.noiseless:
+            u = torch.rand(H, W, generator=gen, device=device, dtype=torch.float32)
+            col = torch.where((u < sp.firefly_frac)[None], col * sp.firefly_gain, col)
+        if sp.noiseless:
+            col = truth.clone()
+        out[s, 0:3] = col
+        out[s, 3:5] = torch.rand(2, H, W, generator=gen, device=device, dtype=torch.float32) - 0.5
+    return out
+
+
+def perspective_view_proj(eye, target, fov_y_deg: float, aspect: float, near: float = 0.1,
+                          far: float = 100.0) -> np.ndarray:
+    """Row-major 4x4 view-projection matrix (right-handed view, OpenGL-style clip space)."""
+    eye, target = np.asarray(eye, np.float64), np.asarray(target, np.float64)
+    f = target - eye
+    f /= np.linalg.norm(f)
+    up = np.array([0.0, 1.0, 0.0])
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    view = np.eye(4)
+    view[0, :3], view[1, :3], view[2, :3] = r, u, -f
+    view[:3, 3] = -view[:3, :3] @ eye
+    k = 1.0 / math.tan(math.radians(fov_y_deg) / 2)
+    proj = np.zeros((4, 4))
+    proj[0, 0], proj[1, 1] = k / aspect, k
+    proj[2, 2], proj[2, 3] = (far + near) / (near - far), 2 * far * near / (near - far)
+    proj[3, 2] = -1.0
+    return proj @ view
+
+
+def orbit_camera(t: int, width: int, height: int, deg_per_frame: float = 0.5) -> np.ndarray:
+    """View-projection of frame t of a camera orbiting the origin at radius 4, 45 deg fov."""
+    a = math.radians(30.0 + deg_per_frame * t)
+    eye = (4.0 * math.sin(a), 1.5, 4.0 * math.cos(a))
+    return perspective_view_proj(eye, (0.0, 0.0, 0.0), 45.0, width / height)
+
+
+def first_collision_world(width: int, height: int, view_proj: np.ndarray, seed: int = 0,
+                          miss_frac: float = 0.1) -> np.ndarray:
+    """World positions (3, H, W) f32 of points seen through the pixel centres of a camera:
+    each pixel's ray (through its centre) is cut at a smooth pseudo-random depth (NDC z in
+    [0.90, 0.98]); a seeded `miss_frac` of pixels (blobs) have no collision (NaN)."""
+    rng = np.random.default_rng(seed)
+    ys, xs = np.mgrid[0:height, 0:width].astype(np.float64)
+    ndc_x = (xs + 0.5) / width * 2 - 1
+    ndc_y = 1 - (ys + 0.5) / height * 2
+    ph = rng.uniform(0, 2 * np.pi, 4)
+    zn = 0.94 + 0.04 * np.sin(xs / width * 6.0 + ph[0]) * np.cos(ys / height * 5.0 + ph[1])
+    clip = np.stack([ndc_x, ndc_y, zn, np.ones_like(zn)], 0).reshape(4, -1)
+    X = np.linalg.inv(view_proj) @ clip
+    X = (X[:3] / X[3]).reshape(3, height, width)
+    blob = np.sin(xs / width * 9.0 + ph[2]) * np.sin(ys / height * 7.0 + ph[3])
+    X[:, blob > np.quantile(blob, 1 - miss_frac)] = np.nan
+    return X.astype(np.float32)

@@ -54,22 +54,38 @@ MUTANTS_EXT = {
     "ext_eq14_lambda_times_w": ("double denom = prm->lambda / w + pPp;", "double denom = prm->lambda * w + pPp;"),
 }
 
+# Mistakes planted in the oracle of the input steps; caught by test_oracle_upstream_pins.py.
+MUTANTS_UP = {
+    "recon_sigma_factor": ("exp(-((double)dx * dx) / (2.0 * sigma * sigma))", "exp(-((double)dx * dx) / (sigma * sigma))"),
+    "recon_offset_sign": ("float dx = (float)(px - x) + base[3 * np + p];", "float dx = (float)(px - x) - base[3 * np + p];"),
+    "recon_variance_of_samples_not_mean": ("var[j] = ss / (3.0 * (n - 1)) / n;", "var[j] = ss / (3.0 * (n - 1));"),
+    "velocity_y_not_flipped": ("double py = (1.0 - clip[1] / clip[3]) * 0.5 * H - 0.5;",
+                               "double py = (1.0 + clip[1] / clip[3]) * 0.5 * H - 0.5;"),
+    "velocity_no_half_pixel": ("double px = (clip[0] / clip[3] + 1.0) * 0.5 * W - 0.5;",
+                               "double px = (clip[0] / clip[3] + 1.0) * 0.5 * W;"),
+    "velocity_forward_not_backward": ("vx = px - x;", "vx = x - px;"),
+    "velocity_matrix_transposed": ("clip[r] += M[r * 4 + c] * X[c];", "clip[r] += M[c * 4 + r] * X[c];"),
+}
+SRC_UP = os.path.join(ROOT, "oracle", "wrls_oracle_upstream.c")
+_SOURCES = {SRC: MUTANTS, SRC_EXT: MUTANTS_EXT, SRC_UP: MUTANTS_UP}
+
 _CASES = [(n, SRC, "test_oracle_pins.py") for n in sorted(MUTANTS)] + \
-         [(n, SRC_EXT, "test_oracle_ext_pins.py") for n in sorted(MUTANTS_EXT)]
+         [(n, SRC_EXT, "test_oracle_ext_pins.py") for n in sorted(MUTANTS_EXT)] + \
+         [(n, SRC_UP, "test_oracle_upstream_pins.py") for n in sorted(MUTANTS_UP)]
 
 
 @pytest.mark.parametrize("name,src_path,pins", _CASES, ids=[c[0] for c in _CASES])
 def test_pins_catch_planted_mistake(name, src_path, pins, tmp_path):
-    old, new = (MUTANTS if src_path == SRC else MUTANTS_EXT)[name]
+    old, new = _SOURCES[src_path][name]
     src = open(src_path).read()
     assert src.count(old) >= 1, "mutant anchor not found: " + name
     mutated = src.replace(old, new, 1)
     c_path = tmp_path / os.path.basename(src_path)
     so_path = tmp_path / "libmutant.so"
     c_path.write_text(mutated)
-    other = SRC_EXT if src_path == SRC else SRC
+    others = [p for p in _SOURCES if p != src_path]
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-                           "-o", str(so_path), str(c_path), other, "-lm"])
+                           "-o", str(so_path), str(c_path), *others, "-lm"])
     env = dict(os.environ, WRLS_ORACLE_LIB=str(so_path), OMP_NUM_THREADS="2")
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(HERE, pins)],
