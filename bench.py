@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched BF16 16-stream leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-gbuf", action="store_true", help="skip the d = 8 G-buffer predictor leg")
+    ap.add_argument("--no-inputs", action="store_true", help="skip the reconstruction / velocity leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--batched-passes", type=int, default=3)
     ap.add_argument("--pipeline", type=int, default=-1,
@@ -370,6 +371,43 @@ def gbuf_leg(torch, W, synth, dev, peak, passes=3):
             "frames_timed": passes * spec.frames}
 
 
+def inputs_leg(torch, W, synth, dev, peak, reps=24):
+    """The denoiser's input steps at 1920x1080: the pixel reconstruction filter (2 samples per
+    pixel, with the variance output) and the velocity from first-collision world positions.
+    Rings of inputs larger than L2 (4 x 83 MB of samples, 8 x 25 MB of positions)."""
+    import numpy as np
+    Wd, Hd, spp = 1920, 1080, 2
+    px = Wd * Hd
+    sc = synth.Scene(synth.SceneSpec(Wd, Hd, 4, seed=9, motion="pan", firefly_frac=0.05))
+    smp = [synth.raw_samples(sc, t, spp, device=dev) for t in range(4)]
+    worlds = [torch.from_numpy(synth.first_collision_world(Wd, Hd, synth.orbit_camera(t, Wd, Hd), seed=t)).to(dev)
+              for t in range(8)]
+    M_prev = synth.orbit_camera(-1, Wd, Hd)
+    rad = torch.empty(3, Hd, Wd, device=dev)
+    var = torch.empty(Hd, Wd, device=dev)
+    mot = torch.empty(2, Hd, Wd, device=dev)
+    cs = torch.cuda.Stream(device=dev)
+    res = {}
+    for name, fn, nbytes in (
+            ("reconstruct", lambda i: W.wrls_reconstruct(smp[i % 4], rad, var, cuda_stream=cs), spp * 20 + 16),
+            ("velocity", lambda i: W.wrls_velocity_from_world(worlds[i % 8], M_prev, mot, cuda_stream=cs), 20)):
+        for i in range(4):
+            fn(i)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(cs)
+        for i in range(reps):
+            fn(i)
+        b.record(cs)
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        gbs = nbytes * px / (ms / 1e3) / 1e9
+        res[name] = {"ms": round(ms, 5), "mpix_s": round(px / (ms / 1e3) / 1e6, 1), "bytes_per_px": nbytes,
+                     "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    res["workload"] = "1920x1080; reconstruction with 2 samples/px (samples 40 B/px in, radiance + variance 16 B/px out); velocity 12 B/px in, 8 B/px out"
+    return res
+
+
 def run_wrls(args):
     import torch
     import torch.distributed as dist
@@ -554,6 +592,9 @@ def run_wrls(args):
     gbuf = None
     if not args.no_gbuf:
         gbuf = gbuf_leg(torch, W, synth, dev, peak)
+    inputs = None
+    if not args.no_inputs:
+        inputs = inputs_leg(torch, W, synth, dev, peak)
     serving = None
     if not args.no_serve:
         from paper_2106_08034_gb300 import serve
@@ -581,7 +622,7 @@ def run_wrls(args):
                        "l2": "inputs larger than L2: state ping-pong 2 x 207 MB per frame",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched_bf16": batched, "gbuf_predictor_d8": gbuf, "serving": serving,
+            "batched_bf16": batched, "gbuf_predictor_d8": gbuf, "input_steps": inputs, "serving": serving,
             "gpu_launches": (2 if best_pipeline in (0, 3) else 1) * T * args.steps, "clocks": ck,
         }
         print(json.dumps(line), flush=True)

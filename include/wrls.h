@@ -328,6 +328,61 @@ void wrls_batch_destroy(wrls_batch* b);
 #define WRLS_STATIC_BATCH_MAX 16
 wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n, void* cuda_stream);
 
+/*
+ * ---- The denoiser's inputs from the renderer's raw data (stateless calls) ----
+ */
+
+/* Pixel reconstruction filter parameters. Fill with wrls_recon_params_default. */
+typedef struct wrls_recon_params {
+    uint32_t struct_size;  /* must equal sizeof(wrls_recon_params) */
+    float sigma;           /* Gaussian std in pixels; default 0.5 */
+    float radius;          /* support half-width in pixels, (0, 1.5]; default 1.5 */
+} wrls_recon_params;
+
+void wrls_recon_params_default(wrls_recon_params* p);
+
+/*
+ * Pixel reconstruction filter (Sec. 4, Table 2: a pixel's light-path samples are filtered
+ * into its estimate I~_j; Sec. 6: a separable Gaussian kernel):
+ *   I~_j = sum_k g(x_k - x_j) g(y_k - y_j) f_k / sum_k g(x_k - x_j) g(y_k - y_j)
+ * over the samples k of the 3 x 3 pixels around j at their positions (pixel centre plus
+ * offset), g(d) = exp(-d^2 / (2 sigma^2)) for |d| <= radius (tested in binary32), else 0.
+ *   samples   device, spp x 5 x H x W planar: element (s, k, y, x) at
+ *             ((s * 5 + k) * H + y) * W + x with k = r, g, b, ox, oy; (ox, oy) is the
+ *             sample's offset from the pixel centre in pixels, in [-0.5, 0.5]. A sample
+ *             with a non-finite colour or offset is skipped.
+ *   radiance  device, 3 x H x W output; a pixel whose window holds no weight gets NaN
+ *             (the denoiser treats it as a missing sample).
+ *   variance  device, H x W output or NULL: the unbiased sample variance of the pixel's own
+ *             valid samples, averaged over the channels and divided by their count (the
+ *             variance of the pixel's sample mean, an input of weight_mode 2); NaN with
+ *             fewer than two valid samples.
+ * 1 <= spp <= 1024; outputs must not overlap the samples or each other; 4-byte aligned.
+ * Asynchronous on cuda_stream (a cudaStream_t as void*, NULL = legacy default).
+ */
+wrls_status wrls_reconstruct(int width, int height, int spp, const float* samples, const wrls_recon_params* p,
+                             float* radiance, float* variance, void* cuda_stream);
+
+/*
+ * Per-pixel backward motion from the world position of the first real collision along each
+ * pixel's ray (Sec. 5.3: velocities from the view matrix and per-pixel world coordinates;
+ * Sec. 6 "Optical flow estimation": the collision closest to the viewer). The position is
+ * projected with the previous frame's view-projection matrix:
+ *   clip = M [X, Y, Z, 1]^T, q = ((clip_x / clip_w + 1) W / 2 - 0.5, (1 - clip_y / clip_w) H / 2 - 0.5),
+ *   v_j = q - j  (pixel centres at integer coordinates, row 0 at the top).
+ *   world           device, 3 x H x W (X, Y, Z planes) of frame t; a non-finite position
+ *                   means the ray had no collision.
+ *   prev_view_proj  HOST array of 16 floats, row-major M of frame t-1 (OpenGL-style clip
+ *                   space); all finite.
+ *   miss_policy     0: no collision -> v = 0; 1: -> NaN (the denoiser restarts the pixel).
+ *                   A position behind the previous camera (clip_w <= 0) always gives NaN.
+ *   motion          device, 2 x H x W output (v_x plane, v_y plane), the layout
+ *                   wrls_denoise_frame takes.
+ * Asynchronous on cuda_stream.
+ */
+wrls_status wrls_velocity_from_world(int width, int height, const float* world, const float* prev_view_proj,
+                                     int miss_policy, float* motion, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,11 +21,11 @@
  *   - sigma = 0.5 px and radius = 1.5 px by default (with offsets in [-0.5, 0.5] the 3x3
  *     window holds every sample within 1.5 px); the support test |d| <= radius is taken in
  *     binary32 on d = (float)(x_p - x_j) + ox, as the GPU takes it;
- *   - a sample with a non-finite colour is skipped; a pixel whose window holds no weight
- *     gets a non-finite estimate (the denoiser then treats it as a missing sample);
- *   - variance (optional output): the unbiased sample variance of pixel j's own finite
+ *   - a sample with a non-finite colour or offset is skipped; a pixel whose window holds no
+ *     weight gets a non-finite estimate (the denoiser then treats it as a missing sample);
+ *   - variance (optional output): the unbiased sample variance of pixel j's own valid
  *     samples, averaged over the three channels and divided by their count (the variance
- *     of the pixel mean); NaN with fewer than two finite samples;
+ *     of the pixel mean); NaN with fewer than two valid samples;
  *   - projection: clip = M [X, Y, Z, 1]^T with M the 4x4 row-major view-projection matrix of
  *     frame t-1; pixel coordinates ((clip_x / clip_w + 1) W / 2 - 0.5,
  *     (1 - clip_y / clip_w) H / 2 - 0.5) (pixel centres at integers, row 0 at the top);
@@ -55,6 +55,7 @@ int wrls_oracle_reconstruct(int W, int H, int spp, const float* samples, double 
                         const float* base = samples + (long)s * 5 * np;
                         double f[3] = {base[p], base[np + p], base[2 * np + p]};
                         if (!isfinite(f[0]) || !isfinite(f[1]) || !isfinite(f[2])) continue;
+                        if (!isfinite(base[3 * np + p]) || !isfinite(base[4 * np + p])) continue;
                         float dx = (float)(px - x) + base[3 * np + p];
                         float dy = (float)(py - y) + base[4 * np + p];
                         if (fabsf(dx) > (float)radius || fabsf(dy) > (float)radius) continue;
@@ -73,6 +74,7 @@ int wrls_oracle_reconstruct(int W, int H, int spp, const float* samples, double 
                     const float* base = samples + (long)s * 5 * np;
                     double f[3] = {base[j], base[np + j], base[2 * np + j]};
                     if (!isfinite(f[0]) || !isfinite(f[1]) || !isfinite(f[2])) continue;
+                    if (!isfinite(base[3 * np + j]) || !isfinite(base[4 * np + j])) continue;
                     for (int c = 0; c < 3; ++c) mean[c] += f[c];
                     ++n;
                 }
@@ -86,6 +88,7 @@ int wrls_oracle_reconstruct(int W, int H, int spp, const float* samples, double 
                     const float* base = samples + (long)s * 5 * np;
                     double f[3] = {base[j], base[np + j], base[2 * np + j]};
                     if (!isfinite(f[0]) || !isfinite(f[1]) || !isfinite(f[2])) continue;
+                    if (!isfinite(base[3 * np + j]) || !isfinite(base[4 * np + j])) continue;
                     for (int c = 0; c < 3; ++c) ss += (f[c] - mean[c]) * (f[c] - mean[c]);
                 }
                 var[j] = ss / (3.0 * (n - 1)) / n;

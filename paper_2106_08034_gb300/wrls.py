@@ -40,6 +40,7 @@ EXPORTED = [
     "wrls_stream_set_debug",
     "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
     "wrls_batch_tick_static", "wrls_denoise_sequence", "wrls_stream_set_overlap",
+    "wrls_recon_params_default", "wrls_reconstruct", "wrls_velocity_from_world",
 ]
 
 
@@ -60,6 +61,10 @@ class wrls_params(ctypes.Structure):
         ("state_precision", ctypes.c_int32), ("n_features", ctypes.c_int32),
         ("n_gbuf", ctypes.c_int32), ("reproj_filter", ctypes.c_int32),
     ]
+
+
+class wrls_recon_params(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("sigma", ctypes.c_float), ("radius", ctypes.c_float)]
 
 
 class wrls_frame_io(ctypes.Structure):
@@ -107,6 +112,9 @@ def lib():
         "wrls_batch_tick_static": (i, [ctypes.POINTER(wrls_frame_io), i, vp]),
         "wrls_denoise_sequence": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
         "wrls_stream_set_overlap": (i, [vp, i]),
+        "wrls_recon_params_default": (None, [ctypes.POINTER(wrls_recon_params)]),
+        "wrls_reconstruct": (i, [i, i, i, vp, ctypes.POINTER(wrls_recon_params), vp, vp, vp]),
+        "wrls_velocity_from_world": (i, [i, i, vp, ctypes.POINTER(ctypes.c_float), i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -183,6 +191,33 @@ def wrls_denoise_sequence(stream: int, frames: Sequence[tuple]) -> None:
 
 def wrls_stream_set_overlap(stream: int, blend_ctas_per_sm: int) -> None:
     _check(lib().wrls_stream_set_overlap(stream, int(blend_ctas_per_sm)))
+
+
+def wrls_recon_params_default(**overrides) -> wrls_recon_params:
+    p = wrls_recon_params()
+    lib().wrls_recon_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def wrls_reconstruct(samples, radiance, variance=None, params: Optional[wrls_recon_params] = None,
+                     cuda_stream=None) -> None:
+    """samples: device tensor (spp, 5, H, W) f32 (r, g, b, ox, oy); radiance (3, H, W) and
+    optional variance (H, W) outputs."""
+    spp, _, h, w = samples.shape
+    p = params if params is not None else wrls_recon_params_default()
+    _check(lib().wrls_reconstruct(int(w), int(h), int(spp), _ptr(samples), ctypes.byref(p), _ptr(radiance),
+                                  _ptr(variance), _stream_handle(cuda_stream)))
+
+
+def wrls_velocity_from_world(world, prev_view_proj, motion, miss_policy: int = 0, cuda_stream=None) -> None:
+    """world: device tensor (3, H, W) f32; prev_view_proj: 4x4 row-major (host, any array
+    type); motion (2, H, W) output."""
+    _, h, w = world.shape
+    m = (ctypes.c_float * 16)(*[float(v) for v in list(__import__("numpy").asarray(prev_view_proj).reshape(16))])
+    _check(lib().wrls_velocity_from_world(int(w), int(h), _ptr(world), m, int(miss_policy), _ptr(motion),
+                                          _stream_handle(cuda_stream)))
 
 
 def wrls_stream_reset(stream: int) -> None:

@@ -91,3 +91,18 @@ def test_extended_state_bytes(lib):
                        (dict(n_gbuf=2, n_features=2, feature_mode=1), 18)]:
         b = W.wrls_state_bytes(640, 360, W.wrls_params_default(**kw))
         assert abs(b / base - planes / 25) < 1e-3, (kw, b, base)
+
+
+def test_input_step_arguments_are_checked_on_the_host(lib):
+    import ctypes
+    p = W.wrls_recon_params_default()
+    assert abs(p.sigma - 0.5) < 1e-7 and abs(p.radius - 1.5) < 1e-7
+    bad = W.wrls_recon_params_default(radius=1.6)
+    assert lib.wrls_reconstruct(8, 8, 1, 256, ctypes.byref(bad), 4096, None, None) == W.WRLS_ERR_INVALID_ARG
+    assert lib.wrls_reconstruct(8, 8, 0, 256, ctypes.byref(p), 4096, None, None) == W.WRLS_ERR_INVALID_ARG
+    p.struct_size = 3
+    assert lib.wrls_reconstruct(8, 8, 1, 256, ctypes.byref(p), 4096, None, None) == W.WRLS_ERR_INVALID_ARG
+    m = (ctypes.c_float * 16)(*([1.0] * 16))
+    assert lib.wrls_velocity_from_world(8, 8, 256, m, 2, 4096, None) == W.WRLS_ERR_INVALID_ARG
+    m[3] = float("inf")
+    assert lib.wrls_velocity_from_world(8, 8, 256, m, 0, 4096, None) == W.WRLS_ERR_INVALID_ARG

@@ -168,3 +168,16 @@ def test_reconstruction_single_offset_sample_closed_form():
     w2 = g(ox + 1) * g(oy)
     ref2 = w2 * F / (w2 + (1 + 2 * g(1)) ** 2 - g(1) * g(0))
     assert abs(out[0, py, px - 1] - ref2) < 1e-14
+
+
+def test_reconstruction_skips_samples_with_nonfinite_offsets():
+    """A sample whose offset is not finite is missing like one with a non-finite colour:
+    the estimate equals the one where that sample's colour is NaN instead."""
+    rng = np.random.default_rng(6)
+    smp = _samples(rng, 3, 6, 7)
+    a, b = smp.copy(), smp.copy()
+    a[1, 3, 2, 4] = np.nan
+    b[1, 0, 2, 4] = np.nan
+    oa, va = O.reconstruct(a)
+    ob, vb = O.reconstruct(b)
+    assert np.array_equal(oa, ob) and np.array_equal(va, vb) and np.all(np.isfinite(oa))
