@@ -6,8 +6,9 @@ It shares no code with the CUDA library and never imports it.
 
 ``build()`` compiles ``wrls_oracle.c`` (the paper's predictor p = [1, z], d = 4) and
 ``wrls_oracle_ext.c`` (any d <= 8: G-buffer predictor entries, sample-variance weight,
-nearest-pixel reprojection) and ``wrls_oracle_upstream.c`` (pixel reconstruction filter,
-velocity from first-collision world positions) with gcc (``-O2 -ffp-contract=off -fopenmp``) into
+nearest-pixel reprojection), ``wrls_oracle_upstream.c`` (pixel reconstruction filter,
+velocity from first-collision world positions) and ``wrls_oracle_vpt.c`` (delta-tracking
+volumetric path tracer) with gcc (``-O2 -ffp-contract=off -fopenmp``) into
 ``oracle/_build/libwrls_oracle.so``; ``OracleStream`` and ``OracleExtStream`` run frames
 through them.
 The constants in ``OracleParams`` defaults are the paper's where it gives one
@@ -28,7 +29,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wrls_oracle.c")
 _SRC_EXT = os.path.join(_HERE, "wrls_oracle_ext.c")
 _SRC_UP = os.path.join(_HERE, "wrls_oracle_upstream.c")
-SOURCES = (_SRC, _SRC_EXT, _SRC_UP)
+_SRC_VPT = os.path.join(_HERE, "wrls_oracle_vpt.c")
+SOURCES = (_SRC, _SRC_EXT, _SRC_UP, _SRC_VPT)
 _LIB = os.path.join(_HERE, "_build", "libwrls_oracle.so")
 _lib = None
 
@@ -95,6 +97,29 @@ class OracleExtParams(OracleParams):
         return (4 if self.feature_mode == 0 else 1) + self.n_gbuf
 
 
+class _VptScene(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint32 * 2), ("eye", ctypes.c_float * 3), ("inv_view_proj", ctypes.c_float * 16),
+                ("n_blobs", ctypes.c_int), ("blobs", ctypes.c_float * 80), ("mu_max", ctypes.c_float),
+                ("tf_lo", ctypes.c_float), ("tf_hi", ctypes.c_float), ("albedo", ctypes.c_float),
+                ("color_lo", ctypes.c_float * 3), ("color_hi", ctypes.c_float * 3),
+                ("light_dir", ctypes.c_float * 3), ("light_rgb", ctypes.c_float * 3),
+                ("env_rgb", ctypes.c_float * 3), ("max_bounces", ctypes.c_int)]
+
+
+def _vpt_scene(d: dict) -> _VptScene:
+    sc = _VptScene()
+    sc.seed[0], sc.seed[1] = int(d["seed"]) & 0xFFFFFFFF, int(d["seed_hi"]) & 0xFFFFFFFF
+    for name, n in (("eye", 3), ("color_lo", 3), ("color_hi", 3), ("light_dir", 3), ("light_rgb", 3),
+                    ("env_rgb", 3)):
+        arr = np.asarray(d[name], np.float32).reshape(n)
+        getattr(sc, name)[:] = [float(v) for v in arr]
+    sc.inv_view_proj[:] = [float(v) for v in np.asarray(d["inv_view_proj"], np.float32).reshape(16)]
+    sc.blobs[:] = [float(v) for v in np.asarray(d["blobs"], np.float32).reshape(80)]
+    sc.n_blobs, sc.max_bounces = int(d["n_blobs"]), int(d["max_bounces"])
+    sc.mu_max, sc.tf_lo, sc.tf_hi, sc.albedo = float(d["mu_max"]), float(d["tf_lo"]), float(d["tf_hi"]), float(d["albedo"])
+    return sc
+
+
 def lib():
     """Load the oracle library (``WRLS_ORACLE_LIB`` selects another build of the same
     source, which the mutation tests use to load deliberately broken copies)."""
@@ -125,6 +150,12 @@ def lib():
         _lib.wrls_oracle_reconstruct.restype = ctypes.c_int
         _lib.wrls_oracle_velocity.argtypes = [ctypes.c_int, ctypes.c_int, fp, dp, ctypes.c_int, dp]
         _lib.wrls_oracle_velocity.restype = ctypes.c_int
+        _lib.wrls_oracle_render_vpt.argtypes = [ctypes.POINTER(_VptScene), ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_uint32, fp, fp, fp]
+        _lib.wrls_oracle_render_vpt.restype = ctypes.c_int
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        _lib.wrls_oracle_philox.argtypes = [u32p, u32p, u32p]
+        _lib.wrls_oracle_philox.restype = None
         _lib.wrls_oracle_set_threads.argtypes = [ctypes.c_int]
         _lib.wrls_oracle_get_threads.restype = ctypes.c_int
     return _lib
@@ -283,3 +314,26 @@ def velocity(world: np.ndarray, prev_view_proj: np.ndarray, miss_policy: int = 0
     if rc != 0:
         raise ValueError("wrls_oracle_velocity rejected its arguments")
     return mot
+
+
+def render_vpt(scene: dict, width: int, height: int, spp: int, frame: int = 0, features: bool = True):
+    """Delta-tracking path tracer. Returns (samples (spp,5,H,W), world (3,H,W), features (7,H,W)
+    or None), all f32."""
+    sc = _vpt_scene(scene)
+    smp = np.empty((spp, 5, height, width), np.float32)
+    world = np.empty((3, height, width), np.float32)
+    feat = np.empty((7, height, width), np.float32) if features else None
+    rc = lib().wrls_oracle_render_vpt(ctypes.byref(sc), int(width), int(height), int(spp), int(frame) & 0xFFFFFFFF,
+                                      _fptr(smp), _fptr(world), None if feat is None else _fptr(feat))
+    if rc != 0:
+        raise ValueError("wrls_oracle_render_vpt rejected its arguments")
+    return smp, world, feat
+
+
+def philox(counter, key):
+    """Philox4x32-10 block of the oracle: 4 uint32 counter words, 2 key words -> 4 words."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in counter])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().wrls_oracle_philox(c, k, o)
+    return [int(v) for v in o]

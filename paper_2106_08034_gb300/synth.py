@@ -348,3 +348,39 @@ def first_collision_world(width: int, height: int, view_proj: np.ndarray, seed: 
     blob = np.sin(xs / width * 9.0 + ph[2]) * np.sin(ys / height * 7.0 + ph[3])
     X[:, blob > np.quantile(blob, 1 - miss_frac)] = np.nan
     return X.astype(np.float32)
+
+
+# ---- procedural volume scene for the path tracer (parameters only) ----
+
+def vpt_scene(width: int, height: int, t: int = 0, seed: int = 0, n_blobs: int = 12, mu_max: float = 6.0,
+              albedo: float = 0.9, max_bounces: int = 4, tf_edit_frame: Optional[int] = None,
+              light_move_frame: Optional[int] = None, deg_per_frame: float = 0.5) -> dict:
+    """Parameters of frame t of a seeded procedural volume scene: Gaussian density blobs in
+    [-1, 1]^3, an opacity ramp and a colour ramp (the transfer function), a directional light
+    and an environment, and the orbit camera of `orbit_camera` (eye and inverse
+    view-projection). A transfer-function edit swaps the colour ramp and lowers the opacity
+    ramp from `tf_edit_frame` on; the light turns by 60 degrees from `light_move_frame` on."""
+    rng = np.random.default_rng(seed)
+    blobs = np.zeros((16, 5), np.float32)
+    for i in range(n_blobs):
+        blobs[i, :3] = rng.uniform(-0.55, 0.55, 3)
+        blobs[i, 3] = rng.uniform(0.18, 0.42)
+        blobs[i, 4] = rng.uniform(0.5, 1.2)
+    vp = orbit_camera(t, width, height, deg_per_frame)
+    a = math.radians(30.0 + deg_per_frame * t)
+    eye = np.array([4.0 * math.sin(a), 1.5, 4.0 * math.cos(a)], np.float32)
+    edited = tf_edit_frame is not None and t >= tf_edit_frame
+    moved = light_move_frame is not None and t >= light_move_frame
+    la = math.radians(-40.0 + (60.0 if moved else 0.0))
+    light = np.array([math.cos(la) * 0.6, 0.8, math.sin(la) * 0.6], np.float64)
+    light /= np.linalg.norm(light)
+    return {
+        "seed": (seed * 2654435761 + 12345) & 0xFFFFFFFF, "seed_hi": 0x5EED0000 + seed,
+        "eye": eye, "inv_view_proj": np.linalg.inv(vp).astype(np.float32),
+        "n_blobs": n_blobs, "blobs": blobs, "mu_max": float(mu_max),
+        "tf_lo": 0.05 if not edited else 0.02, "tf_hi": 0.6 if not edited else 0.4, "albedo": float(albedo),
+        "color_lo": np.array([0.9, 0.5, 0.3] if not edited else [0.3, 0.6, 0.9], np.float32),
+        "color_hi": np.array([1.0, 0.95, 0.85] if not edited else [0.85, 1.0, 0.9], np.float32),
+        "light_dir": light.astype(np.float32), "light_rgb": np.array([12.0, 11.0, 10.0], np.float32),
+        "env_rgb": np.array([0.25, 0.3, 0.4], np.float32), "max_bounces": int(max_bounces),
+    }

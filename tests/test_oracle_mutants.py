@@ -67,11 +67,25 @@ MUTANTS_UP = {
     "velocity_matrix_transposed": ("clip[r] += M[r * 4 + c] * X[c];", "clip[r] += M[c * 4 + r] * X[c];"),
 }
 SRC_UP = os.path.join(ROOT, "oracle", "wrls_oracle_upstream.c")
-_SOURCES = {SRC: MUTANTS, SRC_EXT: MUTANTS_EXT, SRC_UP: MUTANTS_UP}
+
+# Mistakes planted in the path tracer oracle; caught by test_oracle_vpt_pins.py.
+MUTANTS_VPT = {
+    "vpt_majorant_halved": ("        if (++g->steps > VPT_MAX_STEPS) return;\n        t += -log(1.0 - rng_u(g)) / sc->mu_max;",
+                            "        if (++g->steps > VPT_MAX_STEPS) return;\n        t += -log(1.0 - rng_u(g)) / (0.5 * sc->mu_max);"),
+    "vpt_phase_function_dropped": ("beta[c] * sc->light_rgb[c] / (4.0 * VPT_PI);", "beta[c] * sc->light_rgb[c];"),
+    "vpt_albedo_not_applied": ("beta[c] *= sc->albedo * (", "beta[c] *= (0.0 * sc->albedo + 1.0) * ("),
+    "vpt_shadow_ray_not_tracked": ("if (visible(sc, g, y, ld))", "if (1)"),
+    "vpt_acceptance_inverted": ("if (!(rng_u(g) < mu / sc->mu_max)) continue;", "if (rng_u(g) < mu / sc->mu_max) continue;"),
+    "vpt_background_dropped": ("for (int c = 0; c < 3; ++c) L[c] += beta[c] * sc->env_rgb[c];",
+                               "for (int c = 0; c < 3; ++c) L[c] += 0.0 * beta[c] * sc->env_rgb[c];"),
+}
+SRC_VPT = os.path.join(ROOT, "oracle", "wrls_oracle_vpt.c")
+_SOURCES = {SRC: MUTANTS, SRC_EXT: MUTANTS_EXT, SRC_UP: MUTANTS_UP, SRC_VPT: MUTANTS_VPT}
 
 _CASES = [(n, SRC, "test_oracle_pins.py") for n in sorted(MUTANTS)] + \
          [(n, SRC_EXT, "test_oracle_ext_pins.py") for n in sorted(MUTANTS_EXT)] + \
-         [(n, SRC_UP, "test_oracle_upstream_pins.py") for n in sorted(MUTANTS_UP)]
+         [(n, SRC_UP, "test_oracle_upstream_pins.py") for n in sorted(MUTANTS_UP)] + \
+         [(n, SRC_VPT, "test_oracle_vpt_pins.py") for n in sorted(MUTANTS_VPT)]
 
 
 @pytest.mark.parametrize("name,src_path,pins", _CASES, ids=[c[0] for c in _CASES])
