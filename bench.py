@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-gbuf", action="store_true", help="skip the d = 8 G-buffer predictor leg")
     ap.add_argument("--no-inputs", action="store_true", help="skip the reconstruction / velocity leg")
+    ap.add_argument("--no-vpt", action="store_true", help="skip the path tracer -> denoiser pipeline leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--batched-passes", type=int, default=3)
     ap.add_argument("--pipeline", type=int, default=-1,
@@ -408,6 +409,45 @@ def inputs_leg(torch, W, synth, dev, peak, reps=24):
     return res
 
 
+def vpt_pipeline_leg(torch, W, synth, dev, frames=12):
+    """The whole pipeline on the GPU at 1920x1080: path tracing of a procedural volume
+    (2 samples/px, delta tracking, up to 4 real collisions) -> reconstruction filter ->
+    velocity from first-collision positions -> denoiser, with the camera orbiting 0.5
+    deg/frame. Per-stage times from CUDA events over `frames` frames after 2 untimed."""
+    Wd, Hd, spp = 1920, 1080, 2
+    cs = torch.cuda.Stream(device=dev)
+    smp = torch.empty(spp, 5, Hd, Wd, device=dev)
+    world = torch.empty(3, Hd, Wd, device=dev)
+    rad = torch.empty(3, Hd, Wd, device=dev)
+    mot = torch.empty(2, Hd, Wd, device=dev)
+    out = torch.empty(3, Hd, Wd, device=dev)
+    s = W.Stream(Wd, Hd, W.wrls_params_default(), cuda_stream=cs)
+    scenes = [W.vpt_scene_struct(synth.vpt_scene(Wd, Hd, t, seed=8)) for t in range(frames + 2)]
+    mats = [synth.orbit_camera(t - 1, Wd, Hd) for t in range(frames + 2)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(frames + 2)]
+    for t in range(frames + 2):
+        e = ev[t]
+        e[0].record(cs)
+        W.wrls_render_vpt(scenes[t], smp, world, frame=t, cuda_stream=cs)
+        e[1].record(cs)
+        W.wrls_reconstruct(smp, rad, cuda_stream=cs)
+        e[2].record(cs)
+        W.wrls_velocity_from_world(world, mats[t], mot, cuda_stream=cs)
+        e[3].record(cs)
+        W.wrls_denoise_frame(s.handle, rad, None, None, mot, out)
+        e[4].record(cs)
+    cs.synchronize()
+    names = ("render", "reconstruct", "velocity", "denoise")
+    ms = {n: sum(ev[t][k].elapsed_time(ev[t][k + 1]) for t in range(2, frames + 2)) / frames
+          for k, n in enumerate(names)}
+    total = sum(ms.values())
+    W.wrls_stream_check(s.handle)
+    s.close()
+    return {"workload": "1920x1080 procedural volume, 2 spp, <= 4 real collisions, orbiting camera",
+            "ms_per_frame": {k: round(v, 4) for k, v in ms.items()}, "total_ms": round(total, 4),
+            "fps": round(1e3 / total, 1), "render_msamples_s": round(Wd * Hd * spp / (ms["render"] / 1e3) / 1e6, 1)}
+
+
 def run_wrls(args):
     import torch
     import torch.distributed as dist
@@ -595,6 +635,9 @@ def run_wrls(args):
     inputs = None
     if not args.no_inputs:
         inputs = inputs_leg(torch, W, synth, dev, peak)
+    vpt = None
+    if not args.no_vpt:
+        vpt = vpt_pipeline_leg(torch, W, synth, dev)
     serving = None
     if not args.no_serve:
         from paper_2106_08034_gb300 import serve
@@ -622,7 +665,7 @@ def run_wrls(args):
                        "l2": "inputs larger than L2: state ping-pong 2 x 207 MB per frame",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched_bf16": batched, "gbuf_predictor_d8": gbuf, "input_steps": inputs, "serving": serving,
+            "batched_bf16": batched, "gbuf_predictor_d8": gbuf, "input_steps": inputs, "vpt_pipeline": vpt, "serving": serving,
             "gpu_launches": (2 if best_pipeline in (0, 3) else 1) * T * args.steps, "clocks": ck,
         }
         print(json.dumps(line), flush=True)

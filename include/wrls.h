@@ -383,6 +383,52 @@ wrls_status wrls_reconstruct(int width, int height, int spp, const float* sample
 wrls_status wrls_velocity_from_world(int width, int height, const float* world, const float* prev_view_proj,
                                      int miss_policy, float* motion, void* cuda_stream);
 
+/*
+ * ---- Volumetric path tracer producing the denoiser's inputs ----
+ *
+ * Progressive path tracing of a procedural heterogeneous volume (Sec. 3, Sec. 6): delta
+ * tracking with the majorant mu_max (Eq. 4), the collision estimator of Eq. 3 (throughput
+ * times the albedo colour at each real collision), next-event estimation to a directional
+ * light with delta-tracked visibility and the isotropic phase function 1 / (4 pi), and the
+ * environment radiance for paths that leave the volume (Eq. 1). Volume: the box [-1, 1]^3,
+ * density rho(x) = min(1, sum_i a_i exp(-|x - c_i|^2 / (2 r_i^2))); transfer function:
+ * mu_t = mu_max clamp((rho - tf_lo) / (tf_hi - tf_lo), 0, 1), albedo colour
+ * albedo (color_lo + rho (color_hi - color_lo)). A path ends after max_bounces real
+ * collisions or 2^20 tentative collisions. Random numbers: Philox4x32-10 with counter
+ * (pixel index, sample index, frame, block) and key seed.
+ */
+typedef struct wrls_vpt_scene {
+    uint32_t struct_size;     /* must equal sizeof(wrls_vpt_scene) */
+    uint32_t seed[2];         /* Philox key */
+    float eye[3];             /* camera position */
+    float inv_view_proj[16];  /* row-major inverse view-projection: rays go from eye through
+                                 inv_view_proj [ndc_x, ndc_y, 1, 1] (dehomogenised) */
+    int32_t n_blobs;          /* 0..16 */
+    float blobs[16][5];       /* cx, cy, cz, radius (> 0), amplitude */
+    float mu_max;             /* > 0 */
+    float tf_lo, tf_hi;       /* opacity ramp, tf_hi > tf_lo */
+    float albedo;             /* single-scattering albedo >= 0 */
+    float color_lo[3], color_hi[3];
+    float light_dir[3];       /* unit vector towards the directional light */
+    float light_rgb[3];       /* its radiance */
+    float env_rgb[3];         /* environment radiance */
+    int32_t max_bounces;      /* >= 1 */
+} wrls_vpt_scene;
+
+/*
+ * Render one frame with spp samples per pixel (1..1024), all outputs device, planar:
+ *   samples   spp x 5 x H x W: r, g, b and the sub-pixel offsets ox, oy of each sample (the
+ *             layout wrls_reconstruct takes); ndc = ((x + 0.5 + ox) / W * 2 - 1,
+ *             1 - (y + 0.5 + oy) / H * 2), offsets from the first two random numbers - 0.5.
+ *   world     3 x H x W: the first real collision closest to the eye among the pixel's
+ *             samples (the input of wrls_velocity_from_world); NaN where none.
+ *   features  7 x H x W or NULL: depth (distance from the eye), normal (-grad rho / |grad rho|)
+ *             and albedo colour at that collision; 0 where none (noisy G-buffers, Fig. 4).
+ * Outputs must not overlap. Asynchronous on cuda_stream.
+ */
+wrls_status wrls_render_vpt(const wrls_vpt_scene* scene, int width, int height, int spp, uint32_t frame,
+                            float* samples, float* world, float* features, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,7 +40,7 @@ EXPORTED = [
     "wrls_stream_set_debug",
     "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
     "wrls_batch_tick_static", "wrls_denoise_sequence", "wrls_stream_set_overlap",
-    "wrls_recon_params_default", "wrls_reconstruct", "wrls_velocity_from_world",
+    "wrls_recon_params_default", "wrls_reconstruct", "wrls_velocity_from_world", "wrls_render_vpt",
 ]
 
 
@@ -65,6 +65,29 @@ class wrls_params(ctypes.Structure):
 
 class wrls_recon_params(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("sigma", ctypes.c_float), ("radius", ctypes.c_float)]
+
+
+class wrls_vpt_scene(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("seed", ctypes.c_uint32 * 2), ("eye", ctypes.c_float * 3),
+                ("inv_view_proj", ctypes.c_float * 16), ("n_blobs", ctypes.c_int32), ("blobs", ctypes.c_float * 80),
+                ("mu_max", ctypes.c_float), ("tf_lo", ctypes.c_float), ("tf_hi", ctypes.c_float),
+                ("albedo", ctypes.c_float), ("color_lo", ctypes.c_float * 3), ("color_hi", ctypes.c_float * 3),
+                ("light_dir", ctypes.c_float * 3), ("light_rgb", ctypes.c_float * 3), ("env_rgb", ctypes.c_float * 3),
+                ("max_bounces", ctypes.c_int32)]
+
+
+def vpt_scene_struct(d: dict) -> "wrls_vpt_scene":
+    """The C struct of a scene given as a dict of its fields (synth.vpt_scene)."""
+    import numpy as np
+    sc = wrls_vpt_scene()
+    sc.struct_size = ctypes.sizeof(wrls_vpt_scene)
+    sc.seed[0], sc.seed[1] = int(d["seed"]) & 0xFFFFFFFF, int(d["seed_hi"]) & 0xFFFFFFFF
+    for name, n in (("eye", 3), ("color_lo", 3), ("color_hi", 3), ("light_dir", 3), ("light_rgb", 3),
+                    ("env_rgb", 3), ("inv_view_proj", 16), ("blobs", 80)):
+        getattr(sc, name)[:] = [float(v) for v in np.asarray(d[name], np.float32).reshape(n)]
+    sc.n_blobs, sc.max_bounces = int(d["n_blobs"]), int(d["max_bounces"])
+    sc.mu_max, sc.tf_lo, sc.tf_hi, sc.albedo = float(d["mu_max"]), float(d["tf_lo"]), float(d["tf_hi"]), float(d["albedo"])
+    return sc
 
 
 class wrls_frame_io(ctypes.Structure):
@@ -115,6 +138,7 @@ def lib():
         "wrls_recon_params_default": (None, [ctypes.POINTER(wrls_recon_params)]),
         "wrls_reconstruct": (i, [i, i, i, vp, ctypes.POINTER(wrls_recon_params), vp, vp, vp]),
         "wrls_velocity_from_world": (i, [i, i, vp, ctypes.POINTER(ctypes.c_float), i, vp, vp]),
+        "wrls_render_vpt": (i, [ctypes.POINTER(wrls_vpt_scene), i, i, i, ctypes.c_uint32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -218,6 +242,15 @@ def wrls_velocity_from_world(world, prev_view_proj, motion, miss_policy: int = 0
     m = (ctypes.c_float * 16)(*[float(v) for v in list(__import__("numpy").asarray(prev_view_proj).reshape(16))])
     _check(lib().wrls_velocity_from_world(int(w), int(h), _ptr(world), m, int(miss_policy), _ptr(motion),
                                           _stream_handle(cuda_stream)))
+
+
+def wrls_render_vpt(scene, samples, world, features=None, frame: int = 0, cuda_stream=None) -> None:
+    """scene: dict (synth.vpt_scene) or wrls_vpt_scene; samples (spp, 5, H, W), world (3, H, W),
+    optional features (7, H, W) device tensors."""
+    sc = scene if isinstance(scene, wrls_vpt_scene) else vpt_scene_struct(scene)
+    spp, _, h, w = samples.shape
+    _check(lib().wrls_render_vpt(ctypes.byref(sc), int(w), int(h), int(spp), int(frame) & 0xFFFFFFFF, _ptr(samples),
+                                 _ptr(world), _ptr(features), _stream_handle(cuda_stream)))
 
 
 def wrls_stream_reset(stream: int) -> None:
