@@ -156,8 +156,11 @@ wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const
  * frames at once (offline denoising of a recorded sequence, throughput runs). Results are
  * those of n calls of wrls_denoise_frame. The frames' updates run in order on the stream's
  * CUDA stream; the blend of frame t runs on a second CUDA stream that the library creates
- * on the first call, so it overlaps the update of frame t+1 (both read the state of frame t;
- * the update of frame t+2, which overwrites it, waits for that blend through an event).
+ * on the first call, so it overlaps the update of frame t+1 (both read the state of frame t).
+ * The first call also adds a third state copy (one more wrls_state_bytes / 2 of device
+ * memory; synchronises the stream once), so that the update of frame t+2 need not wait for
+ * the blend of frame t; the update of frame t+3, which overwrites that copy, waits for it
+ * through an event (t+2 with two copies, if the allocation failed).
  * The memory-bound update and the arithmetic-bound blend then share the GPU. Before
  * returning, the stream's CUDA stream is made to wait for the last blend, so all n outputs
  * are complete once it is synchronised. frames[i].stream must be s or NULL; each frame

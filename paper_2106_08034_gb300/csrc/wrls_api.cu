@@ -258,11 +258,11 @@ static wrls_status timing_slot(wrls_stream* s, cudaEvent_t** ev) {
   return WRLS_OK;
 }
 
-// Update of the next frame (state copy cur -> cur ^ 1) on the stream's CUDA stream.
+// Update of the next frame (state copy cur -> next_copy) on the stream's CUDA stream.
 static wrls_status enqueue_update(wrls_stream* s, const float* radiance, const float* variance,
                                   const float* features, const float* motion, const char* who) {
   const StateDesc& prev = s->state[s->cur];
-  const StateDesc& next = s->state[s->cur ^ 1];
+  const StateDesc& next = s->state[next_copy(s)];
   cudaError_t e;
   if (s->ext)
     e = launch_ext_update(s->ep, s->dim, prev, next, s->need_reset, radiance, motion,
@@ -279,10 +279,10 @@ static wrls_status enqueue_update(wrls_stream* s, const float* radiance, const f
   return WRLS_OK;
 }
 
-// Blend of the state copy the last update wrote (cur ^ 1) into out, on CUDA stream cs.
+// Blend of the state copy the last update wrote (next_copy) into out, on CUDA stream cs.
 static wrls_status enqueue_blend(wrls_stream* s, const KParams& kp, const float* features, float* out,
                                  cudaStream_t cs, const char* who) {
-  const StateDesc& next = s->state[s->cur ^ 1];
+  const StateDesc& next = s->state[next_copy(s)];
   cudaError_t e;
   if (s->ext) {
     ExtParams ep = s->ep;
@@ -298,8 +298,34 @@ static wrls_status enqueue_blend(wrls_stream* s, const KParams& kp, const float*
   return WRLS_OK;
 }
 
+// A third state copy for wrls_denoise_sequence (same geometry as the other two); false if
+// the allocation or the tensor-map encoding fails, and the stream keeps two copies.
+static bool add_third_copy(wrls_stream* s) {
+  int pitch;
+  size_t ps, scale_off;
+  const int nplanes = s->state[0].nplanes;
+  const size_t copy = state_copy_layout(s->W, s->H, s->prm.state_precision, &pitch, &ps, &scale_off, nplanes);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, copy) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  StateDesc d = s->state[0];
+  d.base = mem;
+  d.scale = s->prm.state_precision ? (float*)((char*)mem + scale_off) : nullptr;
+  const char* why = "";
+  if (!s->ext && !encode_stage_maps(d, &why)) {
+    cudaFree(mem);
+    return false;
+  }
+  s->state[2] = d;
+  s->mem3 = mem;
+  s->ncopies = 3;
+  return true;
+}
+
 static void advance(wrls_stream* s) {
-  s->cur ^= 1;
+  s->cur = next_copy(s);
   s->need_reset = false;
   s->has_frame = true;
   s->frames++;
@@ -430,7 +456,7 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
   if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
   if (!s->ext && (s->pipeline == 1 || s->pipeline == 2)) {
     const StateDesc& prev = s->state[s->cur];
-    const StateDesc& next = s->state[s->cur ^ 1];
+    const StateDesc& next = s->state[next_copy(s)];
     WRLS_CHECK_CUDA(launch_fused(s->pipeline, s->kp, prev, next, s->need_reset, radiance, motion, out, s->err, s->work,
                                  s->flags, (int)((s->frames + 1) & 0x7fffffff), s->cs),
                     "wrls_denoise_frame: fused kernel launch");
@@ -494,13 +520,16 @@ wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, i
   if (!s->side) {
     WRLS_CHECK_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking), "wrls_denoise_sequence: stream");
     cudaError_t e = cudaEventCreateWithFlags(&s->ev_u, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_b[0], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_b[1], cudaEventDisableTiming);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&s->ev_b[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("wrls_denoise_sequence: event creation failed: %s", cudaGetErrorString(e));
       return WRLS_ERR_CUDA;
     }
+    // A third copy lets the update of frame t+2 run while the blend of frame t still reads
+    // its copy; without it (allocation failed) that update waits for that blend.
+    WRLS_CHECK_CUDA(cudaStreamSynchronize(s->cs), "wrls_denoise_sequence: synchronize");
+    add_third_copy(s);
   }
   KParams kpo = s->kp;
   kpo.blend_ctas_cap = s->overlap_ctas;
@@ -515,8 +544,9 @@ wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, i
   int last = -1;  // last frame whose blend was enqueued on the side stream
   for (int i = 0; i < n && st == WRLS_OK; ++i) {
     const wrls_frame_io& f = frames[i];
-    // The update of frame i overwrites the state copy that the blend of frame i-2 reads.
-    if (i >= 2 && !ck(cudaStreamWaitEvent(s->cs, s->ev_b[i & 1], 0), "wait")) break;
+    // The update of frame i overwrites the state copy that the blend of frame i - ncopies reads.
+    const int nc = s->ncopies;
+    if (i >= nc && !ck(cudaStreamWaitEvent(s->cs, s->ev_b[(i - nc) % 3], 0), "wait")) break;
     cudaEvent_t* ev = nullptr;
     if ((st = timing_slot(s, &ev)) != WRLS_OK) break;
     if (ev && !ck(cudaEventRecord(ev[0], s->cs), "event record")) break;
@@ -532,13 +562,13 @@ wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, i
       if (!ck(cudaEventRecord(ev[3], s->side), "event record")) break;
       s->t_pending++;
     }
-    if (!ck(cudaEventRecord(s->ev_b[i & 1], s->side), "event record")) break;
+    if (!ck(cudaEventRecord(s->ev_b[i % 3], s->side), "event record")) break;
     advance(s);
   }
   // join: later work on the stream's CUDA stream sees every output (also after an error)
   if (last >= 0) {
-    cudaError_t e = cudaEventRecord(s->ev_b[last & 1], s->side);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_b[last & 1], 0);
+    cudaError_t e = cudaEventRecord(s->ev_b[last % 3], s->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_b[last % 3], 0);
     ck(e, "join");
   }
   return st;
@@ -615,10 +645,11 @@ void wrls_stream_destroy(wrls_stream* s) {
   if (s->side) cudaStreamSynchronize(s->side);
   free_timing(s);
   if (s->ev_u) cudaEventDestroy(s->ev_u);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
     if (s->ev_b[i]) cudaEventDestroy(s->ev_b[i]);
   if (s->side) cudaStreamDestroy(s->side);
   cudaFree(s->mem);
+  if (s->mem3) cudaFree(s->mem3);
   if (s->staging) cudaFree(s->staging);
   cudaGetLastError();
   if (prev_dev != s->device) cudaSetDevice(prev_dev);

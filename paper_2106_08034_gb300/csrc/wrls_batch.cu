@@ -411,7 +411,7 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
   for (int i = 0; i < n; ++i) {
     wrls_stream* s = frames[i].stream;
     const StateDesc& pv = s->state[s->cur];
-    const StateDesc& nx = s->state[s->cur ^ 1];
+    const StateDesc& nx = s->state[next_copy(s)];
     FrameWork& w = fw[i];
     w.maps = pv.maps;
     w.stage_ok = pv.stage_ok ? 1 : 0;
@@ -474,7 +474,7 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
   if (e != cudaSuccess) { set_error("wrls_batch_tick: graph launch: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
   for (int i = 0; i < n; ++i) {
     wrls_stream* s = frames[i].stream;
-    s->cur ^= 1;
+    s->cur = next_copy(s);
     s->need_reset = false;
     s->has_frame = true;
     s->frames++;
@@ -626,7 +626,7 @@ extern "C" wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n
   for (int i = 0; i < n; ++i) {
     wrls_stream* s = frames[i].stream;
     const StateDesc& pv = s->state[s->cur];
-    const StateDesc& nx = s->state[s->cur ^ 1];
+    const StateDesc& nx = s->state[next_copy(s)];
     FrameWork& w = fw[i];
     w.maps = pv.maps;
     w.stage_ok = pv.stage_ok ? 1 : 0;
@@ -672,7 +672,7 @@ extern "C" wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n
   }
   for (int i = 0; i < n; ++i) {
     wrls_stream* s = frames[i].stream;
-    s->cur ^= 1;
+    s->cur = next_copy(s);
     s->need_reset = false;
     s->has_frame = true;
     s->frames++;

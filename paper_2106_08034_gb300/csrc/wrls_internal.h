@@ -107,14 +107,16 @@ struct wrls_stream {
   bool ext = false;             // extended predictor / weights (wrls_ext.cu kernels)
   int dim = 4;                  // predictor dimension of the extended kernels
   wrls::ExtParams ep{};
-  wrls::StateDesc state[2];
+  wrls::StateDesc state[3];     // copies in rotation: state[cur] holds frame t-1
+  int ncopies = 2;              // 2; 3 once wrls_denoise_sequence has added a copy
+  void* mem3 = nullptr;         // the third copy (wrls_denoise_sequence)
   void* mem = nullptr;          // both state copies, then the device error word
   int* err = nullptr;           // device error word (WRLS_ERR_TIMEOUT from a bounded wait)
   int* work = nullptr;          // fused kernel: item and exit counters (zero between launches)
   int* flags = nullptr;         // fused kernel: per-update-tile done flags (frame epochs)
   int pipeline = 0;             // 0, 3 = update kernel + blend kernel (3: prefetching update); 1, 2 = fused
   size_t mem_bytes = 0;
-  int cur = 0;                  // copy holding frame t-1
+  int cur = 0;                  // copy holding frame t-1 (the next frame writes next_copy())
   bool need_reset = true;
   bool has_frame = false;
   cudaStream_t cs = nullptr;
@@ -125,7 +127,8 @@ struct wrls_stream {
   // wrls_denoise_sequence: blends on a second CUDA stream, ordered by events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_u = nullptr;          // update of frame t done (side stream waits)
-  cudaEvent_t ev_b[2] = {nullptr, nullptr};  // blend of frame t done (update t+2 waits), by t & 1
+  cudaEvent_t ev_b[3] = {nullptr, nullptr, nullptr};  // blend of frame t done, by t % 3: the update of
+                                                      // frame t + ncopies, which overwrites its copy, waits
   int overlap_ctas = 1;                // CTAs per SM of a persistent blend that overlaps an update
   // kernel tracing
   static constexpr int kTimingCap = 8192;
@@ -134,3 +137,6 @@ struct wrls_stream {
   double t_update_ms = 0.0, t_blend_ms = 0.0;
   uint64_t t_frames = 0;
 };
+
+// The state copy the next frame writes: the one after `cur` in the rotation.
+inline int next_copy(const wrls_stream* s) { return s->cur + 1 < s->ncopies ? s->cur + 1 : 0; }
