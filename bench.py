@@ -567,34 +567,52 @@ def run_wrls(args):
     frames_total = args.steps * T * world
     value = job_mpix_per_s(args.steps * T, px, world, t_max)
 
-    # e2e: the same metric through the host-buffer entry point, copies in the timed region
+    # e2e: the same metric through the host-buffer entry points, copies in the timed region:
+    # the whole step through wrls_denoise_sequence_host (input copies, kernels and output
+    # copies of consecutive frames overlap), and frame by frame through wrls_denoise_frame_host
     e2e = None
     if not args.no_e2e:
         ring = 8
         h_rad = [rad[t].cpu().pin_memory() for t in range(ring)]
         h_mot = [mot[t].cpu().pin_memory() for t in range(ring)]
         h_out = [torch.empty(3, Hd, Wd).pin_memory() for _ in range(ring)]
-        s2 = W.Stream(Wd, Hd, p, cuda_stream=cs)
         e2e_steps = max(1, min(args.steps, 3))
+        host_io = [(h_rad[t % ring], None, None, h_mot[t % ring], h_out[t % ring]) for t in range(T)]
 
-        def step_host():
+        def time_host(fn, s2):
+            fn(s2)
+            cs.synchronize()
+            if world > 1:
+                dist.barrier()
+            e0.record(cs)
+            for _ in range(e2e_steps):
+                fn(s2)
+            e1.record(cs)
+            e1.synchronize()
+            return max_over_ranks(e0.elapsed_time(e1), dev)
+
+        def seq_host(s2):
+            W.wrls_denoise_sequence_host(s2.handle, host_io)
+
+        def frame_host(s2):
             for t in range(T):
                 k = t % ring
                 W.wrls_denoise_frame_host(s2.handle, h_rad[k], None, None, h_mot[k], h_out[k])
-        step_host()
-        cs.synchronize()
-        if world > 1:
-            dist.barrier()
-        e0.record(cs)
-        for _ in range(e2e_steps):
-            step_host()
-        e1.record(cs)
-        e1.synchronize()
-        ms2 = max_over_ranks(e0.elapsed_time(e1), dev)
-        e2e = {"value": round(job_mpix_per_s(e2e_steps * T, px, world, ms2), 2), "unit": "Mpix/s",
-               "h2d_bytes_per_step": T * px * 20, "d2h_bytes_per_step": T * px * 12,
-               "steps": e2e_steps}
+        s2 = W.Stream(Wd, Hd, p, cuda_stream=cs)
+        W.wrls_stream_set_pipeline(s2.handle, best_pipeline)
+        W.wrls_stream_set_blend_config(s2.handle, blend_cfg)
+        W.wrls_stream_set_overlap(s2.handle, int(best[3:].split("/")[1]) if best.startswith("seq") else 2)
+        ms_seq = time_host(seq_host, s2)
         s2.close()
+        s3 = W.Stream(Wd, Hd, p, cuda_stream=cs)
+        W.wrls_stream_set_pipeline(s3.handle, best_pipeline)
+        W.wrls_stream_set_blend_config(s3.handle, blend_cfg)
+        ms_frame = time_host(frame_host, s3)
+        s3.close()
+        e2e = {"value": round(job_mpix_per_s(e2e_steps * T, px, world, ms_seq), 2), "unit": "Mpix/s",
+               "h2d_bytes_per_step": T * px * 20, "d2h_bytes_per_step": T * px * 12,
+               "steps": e2e_steps, "entry": "wrls_denoise_sequence_host (pinned host buffers)",
+               "per_frame_host_entry": round(job_mpix_per_s(e2e_steps * T, px, world, ms_frame), 2)}
 
     peak, peak_kind = measured_peaks()
     upd_per = upd_ms / max(nfr, 1)

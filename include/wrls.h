@@ -171,6 +171,22 @@ wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const
  */
 wrls_status wrls_denoise_sequence(wrls_stream* s, const struct wrls_frame_io* frames, int n);
 
+/*
+ * wrls_denoise_sequence with HOST buffers (pinned memory gives asynchronous copies): for
+ * each frame the inputs (radiance, motion; variance and G-buffer planes when the parameters
+ * use them) are copied to one of three device slots on a copy stream, the frame is denoised
+ * as by wrls_denoise_sequence, and the output is copied back on a second copy stream, so
+ * that the input copy of frame t+1, the kernels of frame t and the output copy of frame t-1
+ * can run at once. Events keep a slot from being refilled before the kernels that read it
+ * (and its output from being overwritten before it was copied back). The first call
+ * allocates the three slots (kept until destroy) and the copy streams. Before returning,
+ * the stream's CUDA stream is made to wait for the last output copy and the last blend, so
+ * every host output is complete once it is synchronised; the host buffers must stay valid
+ * until then. frames[i].stream must be s or NULL. Kernel timing is not recorded for these
+ * frames. Asynchronous.
+ */
+wrls_status wrls_denoise_sequence_host(wrls_stream* s, const struct wrls_frame_io* frames, int n);
+
 /* CTAs per SM of the persistent blend kernels (blend configurations 4-9) when they overlap
  * an update in wrls_denoise_sequence: fewer leave the update room on every SM. 0 = as many
  * as fit; default 1. */

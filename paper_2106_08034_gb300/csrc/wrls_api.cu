@@ -482,6 +482,8 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
   return WRLS_OK;
 }
 
+static wrls_status sequence_setup(wrls_stream* s, const char* who);
+
 wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, int n) {
   if (!s || !frames || n < 1) {
     set_error("wrls_denoise_sequence: NULL stream or frames, or n < 1");
@@ -517,19 +519,12 @@ wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, i
     }
     return WRLS_OK;
   }
-  if (!s->side) {
-    WRLS_CHECK_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking), "wrls_denoise_sequence: stream");
-    cudaError_t e = cudaEventCreateWithFlags(&s->ev_u, cudaEventDisableTiming);
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&s->ev_b[k], cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      set_error("wrls_denoise_sequence: event creation failed: %s", cudaGetErrorString(e));
-      return WRLS_ERR_CUDA;
-    }
-    // A third copy lets the update of frame t+2 run while the blend of frame t still reads
-    // its copy; without it (allocation failed) that update waits for that blend.
-    WRLS_CHECK_CUDA(cudaStreamSynchronize(s->cs), "wrls_denoise_sequence: synchronize");
-    add_third_copy(s);
+  // first use: side stream, events, and a third state copy, which lets the update of frame
+  // t+2 run while the blend of frame t still reads its copy (without it, when the
+  // allocation fails, that update waits for that blend)
+  {
+    wrls_status st0 = sequence_setup(s, "wrls_denoise_sequence");
+    if (st0 != WRLS_OK) return st0;
   }
   KParams kpo = s->kp;
   kpo.blend_ctas_cap = s->overlap_ctas;
@@ -568,6 +563,131 @@ wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, i
   // join: later work on the stream's CUDA stream sees every output (also after an error)
   if (last >= 0) {
     cudaError_t e = cudaEventRecord(s->ev_b[last % 3], s->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_b[last % 3], 0);
+    ck(e, "join");
+  }
+  return st;
+}
+
+// Side stream, its events and the third state copy of the sequence entries (first use).
+static wrls_status sequence_setup(wrls_stream* s, const char* who) {
+  if (s->side) return WRLS_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_u, cudaEventDisableTiming);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&s->ev_b[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("%s: stream/event creation failed: %s", who, cudaGetErrorString(e));
+    return WRLS_ERR_CUDA;
+  }
+  add_third_copy(s);
+  return WRLS_OK;
+}
+
+wrls_status wrls_denoise_sequence_host(wrls_stream* s, const wrls_frame_io* frames, int n) {
+  if (!s || !frames || n < 1) {
+    set_error("wrls_denoise_sequence_host: NULL stream or frames, or n < 1");
+    return WRLS_ERR_INVALID_ARG;
+  }
+  const bool need_var = s->ext && s->prm.weight_mode == 2, need_g = s->ext && s->prm.n_gbuf > 0;
+  for (int i = 0; i < n; ++i) {
+    const wrls_frame_io& f = frames[i];
+    if ((f.stream && f.stream != s) || !f.radiance || !f.motion || !f.out || (need_var && !f.variance) ||
+        (need_g && !f.features)) {
+      set_error("wrls_denoise_sequence_host: frame %d names another stream or lacks a required buffer", i);
+      return WRLS_ERR_INVALID_ARG;
+    }
+  }
+  if (!s->ext && (s->pipeline == 1 || s->pipeline == 2)) {  // fused pipelines: one frame at a time
+    for (int i = 0; i < n; ++i) {
+      const wrls_frame_io& f = frames[i];
+      wrls_status st = wrls_denoise_frame_host(s, f.radiance, f.variance, f.features, f.motion, f.out);
+      if (st != WRLS_OK) return st;
+    }
+    return WRLS_OK;
+  }
+  wrls_status st = sequence_setup(s, "wrls_denoise_sequence_host");
+  if (st != WRLS_OK) return st;
+  const size_t np = (size_t)s->W * s->H;
+  const size_t slot_floats = (8 + (s->ext ? 1 + (size_t)s->prm.n_gbuf : 0)) * np;
+  if (!s->ring) {
+    cudaError_t e = cudaMalloc(&s->ring, wrls_stream::kHostSlots * slot_floats * sizeof(float));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
+    for (int k = 0; k < wrls_stream::kHostSlots && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&s->ev_in[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_used[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_done[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("wrls_denoise_sequence_host: set-up failed: %s", cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? WRLS_ERR_OOM : WRLS_ERR_CUDA;
+    }
+    s->ring_slot = slot_floats;
+    // the copy streams start behind everything already queued on the stream's CUDA stream
+    WRLS_CHECK_CUDA(cudaStreamSynchronize(s->cs), "wrls_denoise_sequence_host: synchronize");
+  }
+  KParams kpo = s->kp;
+  kpo.blend_ctas_cap = s->overlap_ctas;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == WRLS_OK) {
+      set_error("wrls_denoise_sequence_host: %s: %s", what, cudaGetErrorString(e));
+      st = WRLS_ERR_CUDA;
+    }
+    return st == WRLS_OK;
+  };
+  // earlier work on the stream's CUDA stream comes first
+  ck(cudaEventRecord(s->ev_u, s->cs), "event record");
+  ck(cudaStreamWaitEvent(s->h2d, s->ev_u, 0), "wait");
+  const int NS = wrls_stream::kHostSlots;
+  int last = -1;
+  for (int i = 0; i < n && st == WRLS_OK; ++i) {
+    const wrls_frame_io& f = frames[i];
+    const int k = i % NS;
+    float* base = s->ring + (size_t)k * s->ring_slot;
+    float *d_rad = base, *d_mot = base + 3 * np, *d_out = base + 5 * np;
+    float* d_var = need_var ? base + 8 * np : nullptr;
+    float* d_g = need_g ? base + 9 * np : nullptr;
+    // inputs: after the kernels of frame i - NS are done with this slot
+    if (i >= NS && !ck(cudaStreamWaitEvent(s->h2d, s->ev_used[k], 0), "wait")) break;
+    if (!ck(cudaMemcpyAsync(d_rad, f.radiance, 3 * np * 4, cudaMemcpyHostToDevice, s->h2d), "radiance copy")) break;
+    if (!ck(cudaMemcpyAsync(d_mot, f.motion, 2 * np * 4, cudaMemcpyHostToDevice, s->h2d), "motion copy")) break;
+    if (d_var && !ck(cudaMemcpyAsync(d_var, f.variance, np * 4, cudaMemcpyHostToDevice, s->h2d), "variance copy"))
+      break;
+    if (d_g && !ck(cudaMemcpyAsync(d_g, f.features, (size_t)s->prm.n_gbuf * np * 4, cudaMemcpyHostToDevice, s->h2d),
+                   "feature copy"))
+      break;
+    if (!ck(cudaEventRecord(s->ev_in[k], s->h2d), "event record")) break;
+    // update on the stream's CUDA stream (after its inputs, and after the blend that last
+    // read the state copy it overwrites)
+    const int nc = s->ncopies;
+    if (i >= nc && !ck(cudaStreamWaitEvent(s->cs, s->ev_b[(i - nc) % 3], 0), "wait")) break;
+    if (!ck(cudaStreamWaitEvent(s->cs, s->ev_in[k], 0), "wait")) break;
+    if ((st = enqueue_update(s, d_rad, d_var, d_g, d_mot, "wrls_denoise_sequence_host")) != WRLS_OK) break;
+    if (!ck(cudaEventRecord(s->ev_u, s->cs), "event record")) break;
+    // blend on the side stream (after the update, and after the output copy of frame i - NS)
+    if (!ck(cudaStreamWaitEvent(s->side, s->ev_u, 0), "wait")) break;
+    if (i >= NS && !ck(cudaStreamWaitEvent(s->side, s->ev_out[k], 0), "wait")) break;
+    if ((st = enqueue_blend(s, kpo, d_g, d_out, s->side, "wrls_denoise_sequence_host")) != WRLS_OK) break;
+    last = i;
+    if (!ck(cudaEventRecord(s->ev_b[i % 3], s->side), "event record")) break;
+    // the slot's inputs are free once the update (and, with G-buffer entries, the blend) ran
+    if (!ck(cudaEventRecord(s->ev_used[k], need_g ? s->side : s->cs), "event record")) break;
+    if (!ck(cudaEventRecord(s->ev_done[k], s->side), "event record")) break;
+    if (!ck(cudaStreamWaitEvent(s->d2h, s->ev_done[k], 0), "wait")) break;
+    if (!ck(cudaMemcpyAsync(f.out, d_out, 3 * np * 4, cudaMemcpyDeviceToHost, s->d2h), "output copy")) break;
+    if (!ck(cudaEventRecord(s->ev_out[k], s->d2h), "event record")) break;
+    advance(s);
+  }
+  // join: the stream's CUDA stream waits for the last output copy (the copy stream is in
+  // order, so for all of them) and for the last blend
+  if (last >= 0) {
+    cudaError_t e = cudaEventRecord(s->ev_out[last % NS], s->d2h);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_out[last % NS], 0);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_b[last % 3], s->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, s->ev_b[last % 3], 0);
     ck(e, "join");
   }
@@ -648,6 +768,17 @@ void wrls_stream_destroy(wrls_stream* s) {
   for (int i = 0; i < 3; ++i)
     if (s->ev_b[i]) cudaEventDestroy(s->ev_b[i]);
   if (s->side) cudaStreamDestroy(s->side);
+  if (s->h2d) cudaStreamSynchronize(s->h2d);
+  if (s->d2h) cudaStreamSynchronize(s->d2h);
+  for (int k = 0; k < wrls_stream::kHostSlots; ++k) {
+    if (s->ev_in[k]) cudaEventDestroy(s->ev_in[k]);
+    if (s->ev_used[k]) cudaEventDestroy(s->ev_used[k]);
+    if (s->ev_done[k]) cudaEventDestroy(s->ev_done[k]);
+    if (s->ev_out[k]) cudaEventDestroy(s->ev_out[k]);
+  }
+  if (s->h2d) cudaStreamDestroy(s->h2d);
+  if (s->d2h) cudaStreamDestroy(s->d2h);
+  if (s->ring) cudaFree(s->ring);
   cudaFree(s->mem);
   if (s->mem3) cudaFree(s->mem3);
   if (s->staging) cudaFree(s->staging);

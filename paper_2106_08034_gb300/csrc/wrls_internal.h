@@ -123,6 +123,15 @@ struct wrls_stream {
   int device = 0;
   uint64_t frames = 0;
   float* staging = nullptr;     // device I/O buffers of wrls_denoise_frame_host
+  // wrls_denoise_sequence_host: a ring of device I/O slots and copy streams
+  static constexpr int kHostSlots = 3;
+  float* ring = nullptr;        // kHostSlots slots of (radiance, motion, output, variance, G-buffers)
+  size_t ring_slot = 0;         // floats per slot
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_in[kHostSlots] = {};    // slot's inputs copied
+  cudaEvent_t ev_used[kHostSlots] = {};  // slot's inputs no longer read by kernels
+  cudaEvent_t ev_done[kHostSlots] = {};  // slot's output written
+  cudaEvent_t ev_out[kHostSlots] = {};   // slot's output copied to the host
   int blend_cfg = 0;            // blend tile configuration
   // wrls_denoise_sequence: blends on a second CUDA stream, ordered by events
   cudaStream_t side = nullptr;

@@ -39,7 +39,7 @@ EXPORTED = [
     "wrls_stream_autotune", "wrls_stream_set_blend_config", "wrls_stream_set_pipeline",
     "wrls_stream_set_debug",
     "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
-    "wrls_batch_tick_static", "wrls_denoise_sequence", "wrls_stream_set_overlap",
+    "wrls_batch_tick_static", "wrls_denoise_sequence", "wrls_denoise_sequence_host", "wrls_stream_set_overlap",
     "wrls_recon_params_default", "wrls_reconstruct", "wrls_velocity_from_world", "wrls_render_vpt",
 ]
 
@@ -134,6 +134,7 @@ def lib():
         "wrls_batch_destroy": (None, [vp]),
         "wrls_batch_tick_static": (i, [ctypes.POINTER(wrls_frame_io), i, vp]),
         "wrls_denoise_sequence": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
+        "wrls_denoise_sequence_host": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
         "wrls_stream_set_overlap": (i, [vp, i]),
         "wrls_recon_params_default": (None, [ctypes.POINTER(wrls_recon_params)]),
         "wrls_reconstruct": (i, [i, i, i, vp, ctypes.POINTER(wrls_recon_params), vp, vp, vp]),
@@ -211,6 +212,14 @@ def wrls_denoise_sequence(stream: int, frames: Sequence[tuple]) -> None:
     for k, (rad, var, feat, mot, out) in enumerate(frames):
         arr[k] = wrls_frame_io(stream, _ptr(rad), _ptr(var), _ptr(feat), _ptr(mot), _ptr(out))
     _check(lib().wrls_denoise_sequence(stream, arr, len(frames)))
+
+
+def wrls_denoise_sequence_host(stream: int, frames: Sequence[tuple]) -> None:
+    """frames: sequence of (radiance, variance, features, motion, out) HOST tensors (pinned)."""
+    arr = (wrls_frame_io * max(1, len(frames)))()
+    for k, (rad, var, feat, mot, out) in enumerate(frames):
+        arr[k] = wrls_frame_io(stream, _ptr(rad), _ptr(var), _ptr(feat), _ptr(mot), _ptr(out))
+    _check(lib().wrls_denoise_sequence_host(stream, arr, len(frames)))
 
 
 def wrls_stream_set_overlap(stream: int, blend_ctas_per_sm: int) -> None:

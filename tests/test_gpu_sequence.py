@@ -161,3 +161,32 @@ def test_sequence_and_per_frame_calls_interleave(prec):
     assert torch.equal(st_a, st_b)
     s.close()
     s2.close()
+
+
+@pytest.mark.parametrize("kw,chunks", [(dict(), (5, 9)), (dict(state_precision=1), (14,)),
+                                       (dict(n_features=synth.N_FEATURES, n_gbuf=2, weight_mode=2), (4, 10))])
+def test_host_sequence_equals_per_frame_host_calls(kw, chunks):
+    """wrls_denoise_sequence_host (input copies, kernels and output copies of consecutive
+    frames overlapping on three streams, three device slots reused) gives bit for bit the
+    outputs of per-frame host calls, including across calls and slot reuse."""
+    spec = synth.SceneSpec(160, 96, 14, seed=66, motion="orbit", firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    p = W.wrls_params_default(**kw)
+    pin = [{k: f[k].pin_memory() for k in ("radiance", "motion", "variance", "features")} for f in fr]
+    ref = [torch.empty(3, spec.height, spec.width).pin_memory() for _ in fr]
+    s = W.Stream(spec.width, spec.height, p)
+    for t, f in enumerate(pin):
+        W.wrls_denoise_frame_host(s.handle, f["radiance"], f["variance"], f["features"], f["motion"], ref[t])
+    W.wrls_stream_check(s.handle)
+    s.close()
+    got = [torch.full((3, spec.height, spec.width), float("nan")).pin_memory() for _ in fr]
+    s = W.Stream(spec.width, spec.height, p)
+    a = 0
+    for c in chunks:
+        W.wrls_denoise_sequence_host(s.handle, [(pin[t]["radiance"], pin[t]["variance"], pin[t]["features"],
+                                                 pin[t]["motion"], got[t]) for t in range(a, a + c)])
+        a += c
+    W.wrls_stream_check(s.handle)   # synchronises the stream's CUDA stream, joined with the copies
+    s.close()
+    for t in range(spec.frames):
+        assert torch.equal(got[t], ref[t]), t
