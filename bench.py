@@ -245,6 +245,31 @@ def batched_leg(args, torch, W, synth, dev):
     W.wrls_batch_destroy(batch)
     for s in streams:
         s.close()
+    # the plain per-frame path on the same workload (FP32 state, and BF16 state for the cost
+    # of batching): every stream's frame through wrls_denoise_frame, stream after stream
+    def per_frame_ms(prec):
+        ps = [W.Stream(sp.width, sp.height, W.wrls_params_default(state_precision=prec), cuda_stream=cs)
+              for sp in specs]
+
+        def frame_tick(t):
+            for i in range(len(specs)):
+                W.wrls_denoise_frame(ps[i].handle, data[i][0][t % ring], None, None, data[i][1][t % ring], outs[i])
+        for t in range(8):
+            frame_tick(t)
+        cs.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(cs)
+        for t in range(n_ticks):
+            frame_tick(t)
+        b.record(cs)
+        b.synchronize()
+        for s in ps:
+            W.wrls_stream_check(s.handle)
+            s.close()
+        return a.elapsed_time(b)
+    ms32 = per_frame_ms(W.WRLS_STATE_F32)
+    ms16 = per_frame_ms(W.WRLS_STATE_BF16)
     bytes_bf16 = 140
     return {
         "workload": ("mix16_60f: 16 streams (4x512^2, 4x1280x720, 4x1920x1080, 2x2560x1440, "
@@ -255,7 +280,15 @@ def batched_leg(args, torch, W, synth, dev):
                     "max": round(per[-1], 4)},
         "frame_latency_note": "all 16 frames of a tick are released at its launch: frame latency = tick time",
         "hbm_path_frac": round(bytes_bf16 * n_ticks * px / (total_ms / 1e3) / 1e9 / measured_peaks()[0], 4),
-        "blend_config": cfg, "launches_per_tick": 2,
+        "blend_config_largest_stream": cfg, "launches_per_tick": 2 * len(specs),
+        "tick_form": "one CUDA graph of each stream's update and blend kernels on 4 parallel branches",
+        "plain_f32_per_frame_same_workload": {
+            "value": round(n_ticks * px / (ms32 / 1e3) / 1e6, 1), "unit": "Mpix/s",
+            "ms_per_tick": round(ms32 / n_ticks, 4),
+            "note": "the 16 frames of each tick through wrls_denoise_frame (FP32 state, default blend "
+                    "configuration), stream after stream"},
+        "plain_bf16_per_frame_same_workload": {"value": round(n_ticks * px / (ms16 / 1e3) / 1e6, 1),
+                                               "unit": "Mpix/s", "ms_per_tick": round(ms16 / n_ticks, 4)},
     }
 
 

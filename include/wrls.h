@@ -284,12 +284,16 @@ wrls_status wrls_stream_kernel_times(wrls_stream* s, double* update_ms, double* 
 const char* wrls_last_error(void);
 
 /*
- * ---- Batched tick: all ready frames of many streams in one persistent launch ----
+ * ---- Batched tick: all ready frames of many streams in one graph launch ----
  *
- * One tick processes one frame of each of n streams (of any sizes) with a single
- * persistent kernel launch that pulls (stream, tile) work items from a device work list;
- * the launch is captured once in a CUDA graph per batch shape and replayed. Results are
- * identical to calling wrls_denoise_frame on each stream alone.
+ * One tick processes one frame of each of n streams (of any sizes) with a single CUDA
+ * graph launch. For streams on the two-kernel pipelines (0, 3) the graph holds each
+ * stream's own update and blend kernels (with the stream's tuned blend tile), the streams
+ * spread over four parallel branches so that the blend of one stream overlaps the update of
+ * another; it is captured each tick and applied to the instantiated graph with
+ * cudaGraphExecUpdate. With a fused pipeline (1, 2) one persistent kernel pulls (stream,
+ * tile) work items from a device work list, replayed from a graph captured once per batch
+ * shape. Results are identical to calling wrls_denoise_frame on each stream alone.
  */
 typedef struct wrls_frame_io {
     wrls_stream* stream;
@@ -310,8 +314,9 @@ wrls_status wrls_batch_set_cuda_stream(wrls_batch* b, void* cuda_stream);
 
 /* Run one tick over n frames (1 <= n <= max_streams; each stream at most once, all
  * streams of the same state precision and blend mode, none on the extended path). The
- * blend tile configuration is the
- * one tuned for the largest stream of the tick. Asynchronous. */
+ * pipeline of the largest stream decides the form of the tick: on the two-kernel form every
+ * stream uses its own update pipeline and blend tile configuration, on the fused form every
+ * stream uses the fused variant of the largest stream. Asynchronous. */
 wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n);
 
 /* Synchronise and free. NULL is a no-op. */

@@ -1,13 +1,20 @@
-// Batched tick: one frame of each of n streams (of any sizes) denoised by a persistent
-// kernel pair that pulls (stream, tile) work items from a device work table.
+// Batched tick: one frame of each of n streams (of any sizes) in one CUDA graph launch.
 //
-// Per tick the host writes a table (header + one FrameWork per frame, with each frame's
-// first tile index) into one of two pinned host buffers and replays a CUDA graph captured
-// once per (buffer, state precision): copy table -> device, zero the two work counters,
-// persistent update kernel, persistent blend kernel. A CTA takes the next tile with an
-// atomicAdd on its counter until the counter passes the total; no CTA ever waits on
-// another. The tile bodies are those of the single-frame kernels, so every stream's
-// output and state are bitwise identical to denoising it alone.
+// Two-kernel pipelines (the default): the graph holds each stream's own update and blend
+// kernels (those of wrls_denoise_frame, with their parameters in the constant bank and the
+// stream's tuned blend tile), the streams' chains spread over kLanes parallel branches, so
+// that one stream's arithmetic-bound blend runs while another stream's memory-bound update
+// runs. The graph is captured every tick (input pointers and restart flags change) and
+// applied to the instantiated graph with cudaGraphExecUpdate.
+//
+// Fused pipelines and wrls_batch_tick_static: the host writes a table (header + one
+// FrameWork per frame, with each frame's first tile index) and persistent kernels pull
+// (stream, tile) work items from it: a CTA takes the next tile with an atomicAdd on a work
+// counter until the counter passes the total; no CTA ever waits on another. The fused tick
+// replays a graph captured once per (pinned table buffer, precision, blend mode, variant).
+//
+// The tile bodies are those of the single-frame kernels, so every stream's output and
+// state are bitwise identical to denoising it alone.
 #include <stdio.h>
 #include <string.h>
 
@@ -179,59 +186,6 @@ static int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
-template <class SV, int TH, int R, int MODE>
-static cudaError_t capture_tick_cfg(cudaStream_t cap, const void* h_table, void* d_table, size_t bytes,
-                                    int* d_counters, cudaGraphExec_t* exec) {
-  constexpr int sbytes = BlendGeom<TH>::kSmemBytes;
-  constexpr int ubytes = update_smem_bytes<SV>();
-  constexpr int nt = kTW * TH / R;
-  cudaError_t e = cudaFuncSetAttribute(k_batch_blend<SV, TH, R, MODE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sbytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_batch_update<SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, ubytes);
-  if (e != cudaSuccess) return e;
-  int ou = 0, ob = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_batch_update<SV>, kTileThreads, ubytes);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_batch_blend<SV, TH, R, MODE>, nt, sbytes);
-  if (e != cudaSuccess) return e;
-  const int sms = sm_count();
-  const int gu = sms * (ou > 0 ? ou : 1), gb = sms * (ob > 0 ? ob : 1);
-  const BatchHeader* hdr = (const BatchHeader*)d_table;
-  const FrameWork* fw = (const FrameWork*)((char*)d_table + sizeof(BatchHeader));
-  cudaGraph_t g = nullptr;
-  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return e;
-  cudaMemcpyAsync(d_table, h_table, bytes, cudaMemcpyHostToDevice, cap);
-  cudaMemsetAsync(d_counters, 0, 4 * sizeof(int), cap);
-  k_batch_update<SV><<<gu, kTileThreads, ubytes, cap>>>(hdr, fw, d_counters);
-  k_batch_blend<SV, TH, R, MODE><<<gb, nt, sbytes, cap>>>(hdr, fw, d_counters);
-  e = cudaStreamEndCapture(cap, &g);
-  if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(exec, g, 0);
-  cudaGraphDestroy(g);
-  return e;
-}
-
-template <class SV, int MODE>
-static cudaError_t capture_tick_mode(int cfg, cudaStream_t cap, const void* h, void* d, size_t bytes,
-                                     int* c, cudaGraphExec_t* exec) {
-  switch (cfg) {
-    case 0: return capture_tick_cfg<SV, 16, 4, MODE>(cap, h, d, bytes, c, exec);
-    case 1: return capture_tick_cfg<SV, 8, 4, MODE>(cap, h, d, bytes, c, exec);
-    case 2: return capture_tick_cfg<SV, 16, 2, MODE>(cap, h, d, bytes, c, exec);
-    case 3: return capture_tick_cfg<SV, 32, 4, MODE>(cap, h, d, bytes, c, exec);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <class SV>
-static cudaError_t capture_tick(int mode, int cfg, cudaStream_t cap, const void* h, void* d,
-                                size_t bytes, int* c, cudaGraphExec_t* exec) {
-  return mode == 0 ? capture_tick_mode<SV, 0>(cfg, cap, h, d, bytes, c, exec)
-                   : capture_tick_mode<SV, 1>(cfg, cap, h, d, bytes, c, exec);
-}
-
 template <class SV, int MODE, int R, int MIN_CTAS>
 static cudaError_t capture_fused_v(cudaStream_t cap, const void* h_table, void* d_table, size_t bytes,
                                    int* d_counters, cudaGraphExec_t* exec) {
@@ -284,14 +238,17 @@ struct wrls_batch {
   int max_streams = 0;
   cudaStream_t cs = nullptr;
   cudaStream_t cap = nullptr;
+  static constexpr int kLanes = 4;          // parallel branches of the per-stream tick graph
+  cudaStream_t lane[kLanes] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kLanes] = {};
+  cudaGraphExec_t exec_chains = nullptr;    // the per-stream tick graph
   size_t table_bytes = 0;
   void* d_table = nullptr;
   int* d_counters = nullptr;
   void* h_table[2] = {nullptr, nullptr};
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  // graph per (pinned slot, precision, blend mode, blend tile configuration) for the
-  // two-kernel tick, and per (pinned slot, precision, blend mode, variant) for the fused tick
-  cudaGraphExec_t exec[2][3][2][kBlendSyncConfigs] = {};
+  // graph per (pinned slot, precision, blend mode, variant) for the fused tick
   cudaGraphExec_t exec_fused[2][3][2][2] = {};
   int fused_ctas = 0;  // resident CTAs of the fused kernel (sets the blends' lag)
   int slot = 0;
@@ -302,10 +259,6 @@ static void batch_free(wrls_batch* b) {
   for (int s = 0; s < 2; ++s) {
     for (int p = 0; p < 3; ++p)
       for (int m = 0; m < 2; ++m)
-        for (int c = 0; c < kBlendSyncConfigs; ++c)
-          if (b->exec[s][p][m][c]) cudaGraphExecDestroy(b->exec[s][p][m][c]);
-    for (int p = 0; p < 3; ++p)
-      for (int m = 0; m < 2; ++m)
         for (int v = 0; v < 2; ++v)
           if (b->exec_fused[s][p][m][v]) cudaGraphExecDestroy(b->exec_fused[s][p][m][v]);
     if (b->ev[s]) cudaEventDestroy(b->ev[s]);
@@ -314,8 +267,70 @@ static void batch_free(wrls_batch* b) {
   if (b->d_table) cudaFree(b->d_table);
   if (b->d_counters) cudaFree(b->d_counters);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int k = 0; k < wrls_batch::kLanes; ++k) {
+    if (b->lane[k]) cudaStreamDestroy(b->lane[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->exec_chains) cudaGraphExecDestroy(b->exec_chains);
   cudaGetLastError();
   delete b;
+}
+
+// Two-kernel tick: a CUDA graph of each stream's own update and blend kernels, the streams'
+// chains spread over kLanes parallel branches. Captured every tick and applied to the
+// instantiated graph with cudaGraphExecUpdate (a new instantiation when the shape changed).
+static wrls_status tick_chains(wrls_batch* b, const wrls_frame_io* frames, int n) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("wrls_batch_tick: begin capture: %s", cudaGetErrorString(e));
+    return WRLS_ERR_CUDA;
+  }
+  e = cudaEventRecord(b->ev_fork, b->cap);
+  const int lanes = n < wrls_batch::kLanes ? n : wrls_batch::kLanes;
+  for (int k = 0; k < lanes && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->lane[k], b->ev_fork, 0);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    wrls_stream* s = frames[i].stream;
+    cudaStream_t ln = b->lane[i % lanes];
+    const StateDesc& prev = s->state[s->cur];
+    const StateDesc& next = s->state[next_copy(s)];
+    e = s->pipeline == 3
+            ? launch_update_pipelined(s->kp, prev, next, s->need_reset, frames[i].radiance, frames[i].motion, s->err, ln)
+            : launch_update(s->kp, prev, next, s->need_reset, frames[i].radiance, frames[i].motion, s->err, ln);
+    if (e == cudaSuccess) e = launch_blend(s->kp, s->blend_cfg, next, frames[i].out, s->err, ln);
+  }
+  for (int k = 0; k < lanes && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->ev_join[k], b->lane[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev_join[k], 0);
+  }
+  const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+  if (e == cudaSuccess) e = ee;
+  if (e == cudaSuccess && b->exec_chains) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(b->exec_chains, g, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(b->exec_chains);
+      b->exec_chains = nullptr;
+    }
+  }
+  if (e == cudaSuccess && !b->exec_chains) e = cudaGraphInstantiate(&b->exec_chains, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec_chains, b->cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("wrls_batch_tick: %s", cudaGetErrorString(e));
+    return WRLS_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    wrls_stream* s = frames[i].stream;
+    s->cur = next_copy(s);
+    s->need_reset = false;
+    s->has_frame = true;
+    s->frames++;
+  }
+  return WRLS_OK;
 }
 
 extern "C" {
@@ -340,6 +355,11 @@ wrls_status wrls_batch_create(int max_streams, wrls_batch** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[s], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int k = 0; k < wrls_batch::kLanes && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->lane[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     set_error("wrls_batch_create: %s", cudaGetErrorString(e));
     wrls_status st = e == cudaErrorMemoryAllocation ? WRLS_ERR_OOM : WRLS_ERR_CUDA;
@@ -389,25 +409,37 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
         return WRLS_ERR_INVALID_ARG;
       }
   }
+  {
+    // the pipeline of the largest stream decides the tick's form
+    int pl = 1;
+    size_t most = 0;
+    for (int i = 0; i < n; ++i) {
+      const size_t px = (size_t)frames[i].stream->W * frames[i].stream->H;
+      if (px > most) {
+        most = px;
+        pl = frames[i].stream->pipeline == 3 ? 0 : frames[i].stream->pipeline;
+      }
+    }
+    if (pl == 0) return tick_chains(b, frames, n);
+  }
   const int slot = b->slot;
   cudaError_t e = cudaEventSynchronize(b->ev[slot]);  // the slot's previous copy has run
   if (e != cudaSuccess) { set_error("wrls_batch_tick: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
   BatchHeader* hdr = (BatchHeader*)b->h_table[slot];
   FrameWork* fw = (FrameWork*)((char*)b->h_table[slot] + sizeof(BatchHeader));
-  int cfg = 0, pipeline = 1;
+  // fused tick: the fused variant of the largest stream
+  int pipeline = 1;
   {
     size_t most = 0;
     for (int i = 0; i < n; ++i) {
       const size_t px = (size_t)frames[i].stream->W * frames[i].stream->H;
       if (px > most) {
         most = px;
-        cfg = blend_sync_config(frames[i].stream->blend_cfg);
-        pipeline = frames[i].stream->pipeline == 3 ? 0 : frames[i].stream->pipeline;
+        pipeline = frames[i].stream->pipeline;
       }
     }
   }
-  const int th_b = blend_rows(cfg);
-  int tiles_u = 0, tiles_b = 0, items_f = 0;
+  int items_f = 0;
   for (int i = 0; i < n; ++i) {
     wrls_stream* s = frames[i].stream;
     const StateDesc& pv = s->state[s->cur];
@@ -430,37 +462,22 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
     w.H = s->H;
     w.reset = s->need_reset ? 1 : 0;
     w.tiles_x = (s->W + kTW - 1) / kTW;
-    w.begin_update = tiles_u;
-    w.begin_blend = tiles_b;
     w.begin_fused = items_f;
     w.flags = s->flags;
     w.epoch = (int)((s->frames + 1) & 0x7fffffff);
-    tiles_u += w.tiles_x * ((s->H + kTH - 1) / kTH);
-    tiles_b += w.tiles_x * ((s->H + th_b - 1) / th_b);
     w.lag = fused_lag(s->W, s->H, b->fused_ctas);
     items_f += fused_items(s->W, s->H, w.lag);
   }
   hdr->n = n;
-  hdr->total_update = tiles_u;
-  hdr->total_blend = tiles_b;
   hdr->total_fused = items_f;
-  cudaGraphExec_t& ex = pipeline != 0 ? b->exec_fused[slot][prec][mode][pipeline == 2 ? 1 : 0]
-                                      : b->exec[slot][prec][mode][cfg];
+  cudaGraphExec_t& ex = b->exec_fused[slot][prec][mode][pipeline == 2 ? 1 : 0];
   if (!ex) {
     const size_t bytes = b->table_bytes;
     void* h = b->h_table[slot];
-    if (pipeline != 0) {
-      switch (prec) {
-        case 0: e = capture_fused<StateF32>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-        case 1: e = capture_fused<StateBF16>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-        default: e = capture_fused<StateF16>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-      }
-    } else {
-      switch (prec) {
-        case 0: e = capture_tick<StateF32>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-        case 1: e = capture_tick<StateBF16>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-        default: e = capture_tick<StateF16>(mode, cfg, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-      }
+    switch (prec) {
+      case 0: e = capture_fused<StateF32>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+      case 1: e = capture_fused<StateBF16>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
+      default: e = capture_fused<StateF16>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
     }
     if (e != cudaSuccess) {
       cudaGetLastError();
