@@ -224,8 +224,9 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
  * denoised frame; `out` (device, 3 x H x W) is overwritten and ends up holding the current
  * frame's output. times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per
  * launch (-1 for a configuration the state format does not offer) and *chosen (optional)
- * the selected configuration. Synchronises the stream. The batched tick uses the
- * one-CTA-per-tile configuration of the same tile shape. Streams on the extended path have
+ * the selected configuration. Synchronises the stream. wrls_batch_tick uses each stream's
+ * configuration; wrls_batch_tick_static uses the one-CTA-per-tile configuration of the same
+ * tile shape. Streams on the extended path have
  * one blend configuration: every time is reported as -1 and 0 is chosen, without a launch.
  */
 #define WRLS_BLEND_CONFIGS 10
@@ -242,7 +243,8 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
  * 128 threads blend with more register reuse and fewer CTAs per SM). Its inter-CTA waits are
  * bounded (WRLS_ERR_TIMEOUT via wrls_stream_check). 3: as 0, with a persistent update kernel
  * that prefetches each tile's motion, radiance and state window (TMA) while the tile before it
- * is being updated. The batched tick runs pipeline 3 as 0. All give bitwise identical results.
+ * is being updated. wrls_batch_tick_static runs pipeline 3 as 0. All give bitwise identical
+ * results.
  * With the fused kernel the kernel timing reports the whole frame as the update time.
  */
 wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused);

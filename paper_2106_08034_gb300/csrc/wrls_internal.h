@@ -74,7 +74,7 @@ inline bool blend_config_ok(int cfg, int precision, bool tma_ok, bool tma2_ok) {
   if (cfg < kBlendSyncConfigs) return true;
   return precision == 0 && (cfg < 8 ? tma_ok : tma2_ok);
 }
-// The synchronous configuration with the same tile shape (used by the batched tick).
+// The synchronous configuration with the same tile shape (used by wrls_batch_tick_static).
 inline int blend_sync_config(int cfg) {
   static const int map[kBlendConfigs] = {0, 1, 2, 3, 2, 2, 1, 0, 2, 1};
   return (cfg >= 0 && cfg < kBlendConfigs) ? map[cfg] : 0;
