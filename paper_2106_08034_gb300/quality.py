@@ -69,3 +69,47 @@ def noise_sweep(spec: synth.SceneSpec, mus=(-7.0, -5.5, -4.0, -2.5), device="cud
     varying samples per pixel (Sec. 7.4, Fig. 16-17)."""
     import dataclasses
     return {mu: score_sequence(dataclasses.replace(spec, noise_mu=mu), None, device) for mu in mus}
+
+
+VPT_MODES = {
+    "wRLS-F-5x5": {},
+    "RLS-F-5x5": {"weight_mode": 1},
+    "RLS-G-5x5": {"weight_mode": 1, "feature_mode": 1, "n_gbuf": 4, "n_features": 4},
+    "wRLS-F+G-5x5": {"n_gbuf": 4, "n_features": 4},
+    "varW-F-5x5": {"weight_mode": 2},
+    "wRLS-F-temporal": {"radius": 0},
+}
+
+
+def vpt_ablation(width: int = 320, height: int = 180, frames: int = 24, spp: int = 2, ref_spp: int = 64,
+                 seed: int = 12, skip: int = 4, device="cuda") -> Dict[str, Dict[str, float]]:
+    """The ablations on path-traced input: every frame of an orbiting camera around the
+    procedural volume is rendered at `spp` samples per pixel (wrls_render_vpt), filtered
+    (wrls_reconstruct, with the variance output), given velocities from its first-collision
+    positions (wrls_velocity_from_world) and denoised; the reference is the same frame at
+    `ref_spp` with other random numbers. G-buffer modes regress on the renderer's noisy
+    albedo (3 planes) and depth of the closest first collision (Fig. 4). Scores as
+    score_sequence, against the reference."""
+    ins = []
+    for t in range(frames):
+        sc = synth.vpt_scene(width, height, t, seed=seed)
+        smp = torch.empty(spp, 5, height, width, device=device)
+        world = torch.empty(3, height, width, device=device)
+        feat = torch.empty(7, height, width, device=device)
+        W.wrls_render_vpt(sc, smp, world, feat, frame=t)
+        rad = torch.empty(3, height, width, device=device)
+        var = torch.empty(height, width, device=device)
+        W.wrls_reconstruct(smp, rad, var)
+        mot = torch.empty(2, height, width, device=device)
+        W.wrls_velocity_from_world(world, synth.orbit_camera(t - 1, width, height), mot)
+        ref_sc = dict(sc, seed_hi=sc["seed_hi"] + 0x10000)
+        rsmp = torch.empty(ref_spp, 5, height, width, device=device)
+        rworld = torch.empty(3, height, width, device=device)
+        W.wrls_render_vpt(ref_sc, rsmp, rworld, frame=t)
+        ref = torch.empty(3, height, width, device=device)
+        W.wrls_reconstruct(rsmp, ref)
+        g = torch.stack([feat[4], feat[5], feat[6], feat[0]]).contiguous()   # albedo, depth
+        ins.append({"radiance": rad, "variance": var, "motion": mot, "features": g, "truth": ref})
+    torch.cuda.synchronize()
+    spec = synth.SceneSpec(width, height, frames, seed=seed)
+    return {name: score_sequence(spec, ov, device, skip=skip, frames=ins) for name, ov in VPT_MODES.items()}

@@ -45,3 +45,20 @@ def test_error_falls_with_input_noise():
     errs = [sweep[mu]["relmse"] for mu in sorted(sweep)]
     print(sweep)
     assert all(a < b for a, b in zip(errs, errs[1:]))
+
+
+def test_ablations_on_path_traced_input():
+    """The paper's claims on path-traced frames (wrls_render_vpt, 2 spp, reconstruction filter,
+    velocities from first collisions), scored against 64-spp renders of the same frames: the
+    temporal feature beats a regression on the renderer's noisy G-buffers (Sec. 5.3, Fig. 4,
+    8), the Eq. 13 weight beats the sample-variance weight at few samples (Sec. 5.3), the 5x5
+    blend lowers the temporal-only error, and the output error is far below the input's."""
+    rep = quality.vpt_ablation(width=256, height=144, frames=20)
+    print(rep)
+    full = rep["wRLS-F-5x5"]
+    assert full["relmse"] < 0.5 * full["relmse_input"]
+    assert full["relmse"] < 0.85 * rep["RLS-G-5x5"]["relmse"]
+    assert full["flicker"] < rep["RLS-G-5x5"]["flicker"]
+    assert full["relmse"] < rep["varW-F-5x5"]["relmse"]
+    assert full["relmse"] < rep["wRLS-F-temporal"]["relmse"]
+    assert full["relmse"] < rep["wRLS-F+G-5x5"]["relmse"]
