@@ -197,6 +197,56 @@ def cpu_oracle_rate(spec, seconds: float, frames_ring: int = 4):
     return n * spec.width * spec.height / dt / 1e6, n, dt, O.get_threads()
 
 
+def cpu_single_thread_rate(seconds: float = 4.0):
+    """The FP64 oracle on one host thread: Mpix/s on the 128x128 static sequence (8 frames,
+    repeated until `seconds` of work)."""
+    import oracle as O
+    from paper_2106_08034_gb300 import synth
+    spec = synth.static_128x128_8f()
+    sc = synth.Scene(spec)
+    frames = [(f["radiance"].numpy(), f["motion"].numpy()) for f in (sc.frame(t) for t in range(spec.frames))]
+    before = O.get_threads()
+    O.set_threads(1)
+    try:
+        n, t0 = 0, time.perf_counter()
+        while True:
+            st = O.OracleStream(spec.width, spec.height)
+            for f in frames:
+                st.frame(*f)
+                n += 1
+            dt = time.perf_counter() - t0
+            if dt >= seconds:
+                break
+    finally:
+        O.set_threads(before)
+    return n * spec.width * spec.height / dt / 1e6, n, dt
+
+
+def small_stream_latency(torch, W, synth, dev, reps=200):
+    """Per-frame device latency of the 128x128 static sequence (the smallest configuration,
+    launch-bound): CUDA events around each wrls_denoise_frame call, after warm-up."""
+    spec = synth.static_128x128_8f()
+    sc = synth.Scene(spec)
+    fr = [sc.frame(t, device=dev) for t in range(spec.frames)]
+    cs = torch.cuda.Stream(device=dev)
+    s = W.Stream(spec.width, spec.height, W.wrls_params_default(), cuda_stream=cs)
+    out = torch.empty(3, spec.height, spec.width, device=dev)
+    for f in fr:
+        W.wrls_denoise_frame(s.handle, f["radiance"], None, None, f["motion"], out)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for i in range(reps):
+        f = fr[i % len(fr)]
+        ev[i][0].record(cs)
+        W.wrls_denoise_frame(s.handle, f["radiance"], None, None, f["motion"], out)
+        ev[i][1].record(cs)
+    ev[-1][1].synchronize()
+    lat = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)
+    W.wrls_stream_check(s.handle)
+    s.close()
+    return {"workload": "static_128x128_8f (128x128, static camera), per-frame calls",
+            "us_per_frame": {"p50": round(lat[len(lat) // 2], 2), "p99": round(lat[int(0.99 * (len(lat) - 1))], 2)}}
+
+
 def batched_leg(args, torch, W, synth, dev):
     """16 concurrent streams of mixed sizes (mix16_60f), BF16 state, one graph-captured
     persistent tick per frame index. Inputs: a ring of 8 generated frames per stream
@@ -698,11 +748,15 @@ def run_wrls(args):
                                "admission by device memory and by a pixel-rate budget of 0.75 x the calibrated "
                                "batched throughput")
 
+    small = small_stream_latency(torch, W, synth, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, dt, cores = cpu_oracle_rate(spec, args.cpu_seconds)
+        rate1, n1, dt1 = cpu_single_thread_rate()
         cpu = {"value": round(rate, 4), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
-               "sample": "%d frames of the 1920x1080 pan workload (%.1f s), FP64 C oracle" % (n, dt)}
+               "sample": "%d frames of the 1920x1080 pan workload (%.1f s), FP64 C oracle" % (n, dt),
+               "single_thread": {"value": round(rate1, 4), "unit": "Mpix/s", "cores": 1,
+                                 "sample": "%d frames of the 128x128 static sequence (%.1f s)" % (n1, dt1)}}
 
     if rank == 0:
         line = {
@@ -716,7 +770,7 @@ def run_wrls(args):
                        "l2": "inputs larger than L2: state ping-pong 2 x 207 MB per frame",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched_bf16": batched, "gbuf_predictor_d8": gbuf, "input_steps": inputs, "vpt_pipeline": vpt, "serving": serving,
+            "batched_bf16": batched, "gbuf_predictor_d8": gbuf, "input_steps": inputs, "vpt_pipeline": vpt, "small_stream": small, "serving": serving,
             "gpu_launches": (2 if best_pipeline in (0, 3) else 1) * T * args.steps, "clocks": ck,
         }
         print(json.dumps(line), flush=True)
