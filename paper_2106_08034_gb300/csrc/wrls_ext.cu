@@ -14,8 +14,9 @@
 // triangle of P row by row (d(d+1)/2 planes), z (3 planes). With d = 4 and the temporal
 // feature this is the paper layout of the fast kernels.
 //
-// These kernels are one thread per pixel with plain cached loads (32 x 8 tiles); the blend
-// stages the 36 x 12 window of beta, z and the per-pixel range factor in shared memory.
+// The update is one thread per pixel with plain cached loads (32 x 8 tiles); the blend
+// stages the 36 x 12 window of beta, z and the per-pixel range factor in shared memory and
+// gives each thread two vertically adjacent outputs of the 32 x 8 tile.
 #include "wrls_internal.h"
 
 namespace wrls {
@@ -227,18 +228,34 @@ constexpr float kExtFarZ = 1e18f;  // feature of an out-of-image neighbour: its 
 // 5x5 blend: out_i = sum_k b_ik (p_i beta_k) / sum_k b_ik (blend_mode 1: p_k beta_k), with
 // b_ik = 2^(spatial_ik - |z_i - z_k|^2 max(r_i, r_k)), r = log2(e) / (h_s^2 (|z| + eps)^2):
 // the Eq. 13 distance of the two features, min(|z_i|, |z_k|) taken through max(r_i, r_k).
+// A CTA of 32 x 4 threads blends a 32 x 8 tile; each thread produces two vertically adjacent
+// outputs, so that every neighbour read from shared memory serves both (6 x 5 reads for two
+// outputs instead of 2 x 25).
+constexpr int kExtBlendRows = 2;
+
 template <int D, bool F>
-__global__ void __launch_bounds__(kExtTW * kExtTH)
+__device__ __forceinline__ void ext_predictor_g(const float* __restrict__ gbuf, size_t npix, size_t j, float p[D]) {
+  using L = ExtDim<D, F>;
+#pragma unroll
+  for (int i = 0; i < L::kG; ++i) {
+    const float g = __ldg(gbuf + (size_t)i * npix + j);
+    p[L::kG0 + i] = isfinite(g) ? g : 0.0f;
+  }
+}
+
+template <int D, bool F>
+__global__ void __launch_bounds__(kExtTW * kExtTH / kExtBlendRows)
     k_blend_ext(const ExtParams ep, const int W, const int H, const float* __restrict__ cur, const int pitch,
                 const size_t ps, const float* __restrict__ gbuf, float* __restrict__ out) {
   using L = ExtDim<D, F>;
   constexpr int NPL = 3 * D + 4;  // beta planes, z (3), range factor
+  constexpr int NT = kExtTW * kExtTH / kExtBlendRows;
   static_assert(NPL * kExtSP * 4 <= 48 * 1024, "blend window exceeds static shared memory");
   __shared__ float sm[NPL * kExtSP];
   const KParams& kp = ep.kp;
   const int bx0 = blockIdx.x * kExtTW, by0 = blockIdx.y * kExtTH;
   const int tid = threadIdx.y * kExtTW + threadIdx.x;
-  for (int e = tid; e < kExtSP; e += kExtTW * kExtTH) {
+  for (int e = tid; e < kExtSP; e += NT) {
     const int gx = bx0 - 2 + e % kExtSW, gy = by0 - 2 + e / kExtSW;
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
       const float* src = cur + (size_t)gy * pitch + gx;
@@ -261,71 +278,94 @@ __global__ void __launch_bounds__(kExtTW * kExtTH)
     }
   }
   __syncthreads();
-  const int x = bx0 + threadIdx.x, y = by0 + threadIdx.y;
-  if (x >= W || y >= H) return;
-  const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
-  const int ei = (threadIdx.y + 2) * kExtSW + threadIdx.x + 2;
-  const float zi0 = sm[(3 * D + 0) * kExtSP + ei], zi1 = sm[(3 * D + 1) * kExtSP + ei],
-              zi2 = sm[(3 * D + 2) * kExtSP + ei];
-  const float ri = sm[(3 * D + 3) * kExtSP + ei];
-  float pi[D];
-  pi[0] = 1.0f;
-  if (F) {
-    pi[1] = zi0;
-    pi[2] = zi1;
-    pi[3] = zi2;
-  }
+  const int x = bx0 + threadIdx.x;
+  const int ty0 = threadIdx.y * kExtBlendRows;  // first of the thread's two rows in the tile
+  const size_t npix = (size_t)W * H;
+  // the two outputs' features, range factors and predictors
+  float zi[kExtBlendRows][3], ri[kExtBlendRows], pi[kExtBlendRows][D];
 #pragma unroll
-  for (int i = 0; i < L::kG; ++i) {
-    const float g = __ldg(gbuf + (size_t)i * npix + j);
-    pi[L::kG0 + i] = isfinite(g) ? g : 0.0f;
-  }
-  float num0 = 0.0f, num1 = 0.0f, num2 = 0.0f, den = 0.0f;
+  for (int r = 0; r < kExtBlendRows; ++r) {
+    const int ei = (ty0 + r + 2) * kExtSW + threadIdx.x + 2;
+    zi[r][0] = sm[(3 * D + 0) * kExtSP + ei];
+    zi[r][1] = sm[(3 * D + 1) * kExtSP + ei];
+    zi[r][2] = sm[(3 * D + 2) * kExtSP + ei];
+    ri[r] = sm[(3 * D + 3) * kExtSP + ei];
+    pi[r][0] = 1.0f;
+    if (F) {
+      pi[r][1] = zi[r][0];
+      pi[r][2] = zi[r][1];
+      pi[r][3] = zi[r][2];
+    }
+    const int y = by0 + ty0 + r;
 #pragma unroll
-  for (int dy = 0; dy < 5; ++dy)
+    for (int i = 0; i < L::kG; ++i) pi[r][L::kG0 + i] = 0.0f;
+    if (x < W && y < H) ext_predictor_g<D, F>(gbuf, npix, (size_t)y * W + x, pi[r]);
+  }
+  float num[kExtBlendRows][3] = {}, den[kExtBlendRows] = {};
+#pragma unroll
+  for (int wy = 0; wy < 4 + kExtBlendRows; ++wy)  // window rows ty0 .. ty0 + 5 (relative)
 #pragma unroll
     for (int dx = 0; dx < 5; ++dx) {
-      const int e = ei + (dy - 2) * kExtSW + (dx - 2);
+      const int e = (ty0 + wy) * kExtSW + threadIdx.x + dx;
       const float zk0 = sm[(3 * D + 0) * kExtSP + e], zk1 = sm[(3 * D + 1) * kExtSP + e],
                   zk2 = sm[(3 * D + 2) * kExtSP + e];
       const float rk = sm[(3 * D + 3) * kExtSP + e];
-      const float a0 = zi0 - zk0, a1 = zi1 - zk1, a2 = zi2 - zk2;
-      const float b = ex2_approx(kp.spatial[dy * 5 + dx] - (a0 * a0 + a1 * a1 + a2 * a2) * fmaxf(ri, rk));
-      float pu[D];
-      if (kp.blend_mode == 0) {
+      float bk[3 * D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) pu[a] = pi[a];
-      } else {
-        const int xx = x + dx - 2, yy = y + dy - 2;
+      for (int a = 0; a < 3 * D; ++a) bk[a] = sm[a * kExtSP + e];
+      float own[3] = {0.0f, 0.0f, 0.0f};  // blend_mode 1: neighbour k's own prediction
+      if (kp.blend_mode != 0) {
+        const int xx = x + dx - 2, yy = by0 + ty0 + wy - 2;
         const bool in = xx >= 0 && xx < W && yy >= 0 && yy < H;
-        pu[0] = 1.0f;
+        float pk[D];
+        pk[0] = 1.0f;
         if (F) {
-          pu[1] = in ? zk0 : 0.0f;
-          pu[2] = in ? zk1 : 0.0f;
-          pu[3] = in ? zk2 : 0.0f;
+          pk[1] = in ? zk0 : 0.0f;
+          pk[2] = in ? zk1 : 0.0f;
+          pk[3] = in ? zk2 : 0.0f;
         }
 #pragma unroll
-        for (int i = 0; i < L::kG; ++i) {
-          const float g = in ? __ldg(gbuf + (size_t)i * npix + (size_t)yy * W + xx) : 0.0f;
-          pu[L::kG0 + i] = isfinite(g) ? g : 0.0f;
+        for (int i = 0; i < L::kG; ++i) pk[L::kG0 + i] = 0.0f;
+        if (in) ext_predictor_g<D, F>(gbuf, npix, (size_t)yy * W + xx, pk);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          own[0] = fmaf(pk[a], bk[0 * D + a], own[0]);
+          own[1] = fmaf(pk[a], bk[1 * D + a], own[1]);
+          own[2] = fmaf(pk[a], bk[2 * D + a], own[2]);
         }
       }
-      float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        p0 = fmaf(pu[a], sm[(0 * D + a) * kExtSP + e], p0);
-        p1 = fmaf(pu[a], sm[(1 * D + a) * kExtSP + e], p1);
-        p2 = fmaf(pu[a], sm[(2 * D + a) * kExtSP + e], p2);
+      for (int r = 0; r < kExtBlendRows; ++r) {
+        const int dy = wy - r;  // this neighbour's row offset (0..4) for output r
+        if (dy < 0 || dy > 4) continue;  // resolved at compile time
+        const float a0 = zi[r][0] - zk0, a1 = zi[r][1] - zk1, a2 = zi[r][2] - zk2;
+        const float b = ex2_approx(kp.spatial[dy * 5 + dx] - (a0 * a0 + a1 * a1 + a2 * a2) * fmaxf(ri[r], rk));
+        float p0 = own[0], p1 = own[1], p2 = own[2];
+        if (kp.blend_mode == 0) {
+          p0 = p1 = p2 = 0.0f;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            p0 = fmaf(pi[r][a], bk[0 * D + a], p0);
+            p1 = fmaf(pi[r][a], bk[1 * D + a], p1);
+            p2 = fmaf(pi[r][a], bk[2 * D + a], p2);
+          }
+        }
+        num[r][0] = fmaf(b, p0, num[r][0]);
+        num[r][1] = fmaf(b, p1, num[r][1]);
+        num[r][2] = fmaf(b, p2, num[r][2]);
+        den[r] += b;
       }
-      num0 = fmaf(b, p0, num0);
-      num1 = fmaf(b, p1, num1);
-      num2 = fmaf(b, p2, num2);
-      den += b;
     }
-  const float inv = 1.0f / den;
-  out[j] = num0 * inv;
-  out[npix + j] = num1 * inv;
-  out[2 * npix + j] = num2 * inv;
+#pragma unroll
+  for (int r = 0; r < kExtBlendRows; ++r) {
+    const int y = by0 + ty0 + r;
+    if (x >= W || y >= H) continue;
+    const size_t j = (size_t)y * W + x;
+    const float inv = 1.0f / den[r];
+    out[j] = num[r][0] * inv;
+    out[npix + j] = num[r][1] * inv;
+    out[2 * npix + j] = num[r][2] * inv;
+  }
 }
 
 __global__ void k_read_state_ext(const int W, const int H, const float* __restrict__ cur, const int pitch,
@@ -346,7 +386,7 @@ static cudaError_t launch_ext_t(const ExtParams& ep, const StateDesc& prev, cons
                                              (float*)next.base, prev.pitch, prev.plane_stride, rad, mot, var, gbuf);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !out) return e;
-  k_blend_ext<D, F><<<grid, block, 0, cs>>>(ep, next.W, next.H, (const float*)next.base, next.pitch,
+  k_blend_ext<D, F><<<grid, dim3(kExtTW, kExtTH / kExtBlendRows), 0, cs>>>(ep, next.W, next.H, (const float*)next.base, next.pitch,
                                             next.plane_stride, gbuf, out);
   return cudaGetLastError();
 }
@@ -355,7 +395,7 @@ template <int D, bool F>
 static cudaError_t launch_ext_blend_t(const ExtParams& ep, const StateDesc& cur, const float* gbuf, float* out,
                                       cudaStream_t cs) {
   const dim3 grid((cur.W + kExtTW - 1) / kExtTW, (cur.H + kExtTH - 1) / kExtTH), block(kExtTW, kExtTH);
-  k_blend_ext<D, F><<<grid, block, 0, cs>>>(ep, cur.W, cur.H, (const float*)cur.base, cur.pitch,
+  k_blend_ext<D, F><<<grid, dim3(kExtTW, kExtTH / kExtBlendRows), 0, cs>>>(ep, cur.W, cur.H, (const float*)cur.base, cur.pitch,
                                             cur.plane_stride, gbuf, out);
   return cudaGetLastError();
 }
