@@ -325,6 +325,15 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n);
 void wrls_batch_destroy(wrls_batch* b);
 
 /*
+ * One batched tick without an executor object: frame io[i] of stream streams[i] (io[i].stream
+ * may be NULL or must equal streams[i]), 1 <= n <= 256, with the rules of wrls_batch_tick.
+ * The library keeps one executor per device, created on the first call on that device
+ * (allocation as in wrls_batch_create) and kept until the process exits; calls are
+ * serialised by a lock. The tick runs on streams[0]'s CUDA stream. Asynchronous.
+ */
+wrls_status wrls_denoise_batch(wrls_stream* const* streams, const struct wrls_frame_io* io, int n);
+
+/*
  * wrls_batch_tick_static: the batched tick for callers that cannot allocate device memory.
  * The paper has no counterpart; this is an integration entry point.
  *

@@ -26,6 +26,9 @@
 
 namespace wrls {
 
+constexpr int kDenoiseBatchMax = 256;  // frames per wrls_denoise_batch call
+constexpr int kMaxDevices = 64;         // devices with a wrls_denoise_batch executor
+
 struct alignas(128) FrameWork {
   StageMaps maps;    // TMA tensor maps of the previous state copy
   KParams kp;
@@ -498,6 +501,46 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
   }
   b->slot ^= 1;
   return WRLS_OK;
+}
+
+wrls_status wrls_denoise_batch(wrls_stream* const* streams, const wrls_frame_io* io, int n) {
+  if (!streams || !io || n < 1 || n > kDenoiseBatchMax) {
+    set_error("wrls_denoise_batch: NULL argument or n = %d outside [1, %d]", n, kDenoiseBatchMax);
+    return WRLS_ERR_INVALID_ARG;
+  }
+  wrls_frame_io* fr = new (std::nothrow) wrls_frame_io[n];
+  if (!fr) {
+    set_error("wrls_denoise_batch: host allocation failed");
+    return WRLS_ERR_OOM;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!streams[i] || (io[i].stream && io[i].stream != streams[i])) {
+      delete[] fr;
+      set_error("wrls_denoise_batch: frame %d: NULL stream, or io.stream differs from streams[%d]", i, i);
+      return WRLS_ERR_INVALID_ARG;
+    }
+    fr[i] = io[i];
+    fr[i].stream = streams[i];
+  }
+  // one executor per device, created on first use and kept until the process exits
+  static std::mutex mu;
+  static wrls_batch* executors[kMaxDevices] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  wrls_status st = WRLS_OK;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDevices) {
+      set_error("wrls_denoise_batch: device %d beyond the executor table", dev);
+      st = WRLS_ERR_INVALID_ARG;
+    } else {
+      if (!executors[dev]) st = wrls_batch_create(kDenoiseBatchMax, &executors[dev]);
+      if (st == WRLS_OK) st = wrls_batch_set_cuda_stream(executors[dev], (void*)streams[0]->cs);
+      if (st == WRLS_OK) st = wrls_batch_tick(executors[dev], fr, n);
+    }
+  }
+  delete[] fr;
+  return st;
 }
 
 void wrls_batch_destroy(wrls_batch* b) {

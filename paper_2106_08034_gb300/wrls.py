@@ -41,6 +41,7 @@ EXPORTED = [
     "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
     "wrls_batch_tick_static", "wrls_denoise_sequence", "wrls_denoise_sequence_host", "wrls_stream_set_overlap",
     "wrls_recon_params_default", "wrls_reconstruct", "wrls_velocity_from_world", "wrls_render_vpt",
+    "wrls_denoise_batch",
 ]
 
 
@@ -133,6 +134,7 @@ def lib():
         "wrls_batch_tick": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
         "wrls_batch_destroy": (None, [vp]),
         "wrls_batch_tick_static": (i, [ctypes.POINTER(wrls_frame_io), i, vp]),
+        "wrls_denoise_batch": (i, [ctypes.POINTER(vp), ctypes.POINTER(wrls_frame_io), i]),
         "wrls_denoise_sequence": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
         "wrls_denoise_sequence_host": (i, [vp, ctypes.POINTER(wrls_frame_io), i]),
         "wrls_stream_set_overlap": (i, [vp, i]),
@@ -356,6 +358,18 @@ def wrls_batch_tick_static(frames: Sequence[tuple], cuda_stream=None) -> None:
     for k, (s, rad, var, feat, mot, out) in enumerate(frames):
         arr[k] = wrls_frame_io(s, _ptr(rad), _ptr(var), _ptr(feat), _ptr(mot), _ptr(out))
     _check(lib().wrls_batch_tick_static(arr, len(frames), _stream_handle(cuda_stream)))
+
+
+def wrls_denoise_batch(frames: Sequence[tuple]) -> None:
+    """One batched tick on the library's executor. frames: (stream, radiance, variance,
+    features, motion, out)."""
+    n = len(frames)
+    hs = (ctypes.c_void_p * max(1, n))()
+    arr = (wrls_frame_io * max(1, n))()
+    for k, (s, rad, var, feat, mot, out) in enumerate(frames):
+        hs[k] = s
+        arr[k] = wrls_frame_io(s, _ptr(rad), _ptr(var), _ptr(feat), _ptr(mot), _ptr(out))
+    _check(lib().wrls_denoise_batch(hs, arr, n))
 
 
 def wrls_batch_destroy(batch: Optional[int]) -> None:

@@ -106,3 +106,12 @@ def test_input_step_arguments_are_checked_on_the_host(lib):
     assert lib.wrls_velocity_from_world(8, 8, 256, m, 2, 4096, None) == W.WRLS_ERR_INVALID_ARG
     m[3] = float("inf")
     assert lib.wrls_velocity_from_world(8, 8, 256, m, 0, 4096, None) == W.WRLS_ERR_INVALID_ARG
+
+
+def test_denoise_batch_arguments_are_checked_on_the_host(lib):
+    assert lib.wrls_denoise_batch(None, None, 1) == W.WRLS_ERR_INVALID_ARG
+    import ctypes
+    hs = (ctypes.c_void_p * 1)(None)
+    arr = (W.wrls_frame_io * 1)()
+    assert lib.wrls_denoise_batch(hs, arr, 0) == W.WRLS_ERR_INVALID_ARG
+    assert lib.wrls_denoise_batch(hs, arr, 1) == W.WRLS_ERR_INVALID_ARG   # NULL stream

@@ -57,3 +57,29 @@ def test_each_session_in_the_mix_equals_alone(precision):
         alone.close()
     srv.close()
     assert srv.latencies and all(l > 0 for l in srv.latencies)
+
+
+def test_denoise_batch_entry_equals_per_frame_calls():
+    """wrls_denoise_batch (the library's own executor) gives bit for bit the outputs of
+    wrls_denoise_frame on each stream, over several ticks of mixed sizes."""
+    import torch
+    from paper_2106_08034_gb300 import synth
+    from paper_2106_08034_gb300 import wrls as W
+    sizes = [(96, 64), (160, 90), (72, 40)]
+    frames = [[synth.Scene(synth.SceneSpec(w, h, 4, seed=90 + i, motion="orbit", firefly_frac=0.05)).frame(t, device="cuda")
+               for t in range(4)] for i, (w, h) in enumerate(sizes)]
+    p = W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
+    a = [W.Stream(w, h, p) for w, h in sizes]
+    b = [W.Stream(w, h, p) for w, h in sizes]
+    oa = [torch.empty(3, h, w, device="cuda") for w, h in sizes]
+    ob = [torch.empty(3, h, w, device="cuda") for w, h in sizes]
+    for t in range(4):
+        W.wrls_denoise_batch([(a[i].handle, frames[i][t]["radiance"], None, None, frames[i][t]["motion"], oa[i])
+                              for i in range(len(sizes))])
+        for i in range(len(sizes)):
+            b[i].denoise(frames[i][t]["radiance"], frames[i][t]["motion"], ob[i])
+        torch.cuda.synchronize()
+        for i in range(len(sizes)):
+            assert torch.equal(oa[i], ob[i]), (t, i)
+    for s in a + b:
+        s.close()

@@ -438,3 +438,22 @@ def test_paper_qualitative_claims():
     assert wrls < 0.5 * rls
     assert wrls < temporal
     assert wrls < 0.2 * inp
+
+
+def test_channel_permutation_equivariance():
+    """R2 (one P shared by the three channel models): permuting the colour channels of every
+    input permutes the output channels, because the weight depends on colour norms only and
+    the shared P of p = [1, z] is only reordered. A channel index mix-up or a P that is not
+    shared consistently breaks this."""
+    W, H, T = 10, 8, 12
+    spec = synth.SceneSpec(W, H, T, seed=31, motion="orbit", firefly_frac=0.1)
+    fr = _frames(spec)
+    perm = [2, 0, 1]
+    a = O.OracleStream(W, H)
+    b = O.OracleStream(W, H)
+    for f in fr:
+        rad, mot = f["radiance"].numpy(), f["motion"].numpy()
+        oa, wa, _ = a.frame(rad, mot)
+        ob, wb, _ = b.frame(np.ascontiguousarray(rad[perm]), mot)
+        assert np.allclose(wb, wa, rtol=1e-12, atol=1e-14)
+        assert np.allclose(ob, oa[perm], rtol=1e-9, atol=1e-12)
