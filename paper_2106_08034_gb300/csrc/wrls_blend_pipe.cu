@@ -38,16 +38,18 @@ __device__ __forceinline__ void blend_compute_soa(const float* __restrict__ w, c
   const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
   const int x = bx0 + tx, y0 = by0 + ty * R;
   const bool feat = kp.feature_mode == 0;
-  float zi[R][3], ri[R], den[R];
-  float acc[R][MODE == 0 ? 12 : 3];
+  float zi[R][3], pf[R][3], ri[R], den[R], acc[R][3];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int idx = (ty * R + i + R0) * SW + tx + 4;
     zi[i][0] = w[12 * P + idx]; zi[i][1] = w[13 * P + idx]; zi[i][2] = w[14 * P + idx];
     ri[i] = w[15 * P + idx];
-    den[i] = 0.0f;
 #pragma unroll
-    for (int p = 0; p < (MODE == 0 ? 12 : 3); ++p) acc[i][p] = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+      pf[i][c] = feat ? zi[i][c] : 0.0f;
+      acc[i][c] = 0.0f;
+    }
+    den[i] = 0.0f;
   }
 #pragma unroll
   for (int kr = 0; kr < R + 2 * R0; ++kr) {
@@ -61,9 +63,9 @@ __device__ __forceinline__ void blend_compute_soa(const float* __restrict__ w, c
       float pk0 = 0.0f, pk1 = 0.0f, pk2 = 0.0f;
       if (MODE == 1) {
         const float a1 = feat ? zk0 : 0.0f, a2 = feat ? zk1 : 0.0f, a3 = feat ? zk2 : 0.0f;
-        pk0 = bk[0] + bk[1] * a1 + bk[2] * a2 + bk[3] * a3;
-        pk1 = bk[4] + bk[5] * a1 + bk[6] * a2 + bk[7] * a3;
-        pk2 = bk[8] + bk[9] * a1 + bk[10] * a2 + bk[11] * a3;
+        pk0 = cross_pred(bk[0], bk[1], bk[2], bk[3], a1, a2, a3);
+        pk1 = cross_pred(bk[4], bk[5], bk[6], bk[7], a1, a2, a3);
+        pk2 = cross_pred(bk[8], bk[9], bk[10], bk[11], a1, a2, a3);
       }
 #pragma unroll
       for (int i = 0; i < R; ++i) {
@@ -71,14 +73,16 @@ __device__ __forceinline__ void blend_compute_soa(const float* __restrict__ w, c
         if (dy < -R0 || dy > R0) continue;  // compile-time
         const float e0 = zi[i][0] - zk0, e1 = zi[i][1] - zk1, e2 = zi[i][2] - zk2;
         const float rk = fmaxf(ri[i], rkk);
-        const float b = ex2_approx(kp.spatial[(dy + R0) * RW + (dx + R0)] - (e0 * e0 + e1 * e1 + e2 * e2) * rk);
+        const float b = ex2_approx(blend_exponent(kp.spatial[(dy + R0) * RW + (dx + R0)], e0, e1, e2, rk));
         den[i] += b;
         if (MODE == 0) {
-#pragma unroll
-          for (int p = 0; p < 12; ++p) acc[i][p] += b * bk[p];
-        } else {
-          acc[i][0] += b * pk0; acc[i][1] += b * pk1; acc[i][2] += b * pk2;
+          pk0 = cross_pred(bk[0], bk[1], bk[2], bk[3], pf[i][0], pf[i][1], pf[i][2]);
+          pk1 = cross_pred(bk[4], bk[5], bk[6], bk[7], pf[i][0], pf[i][1], pf[i][2]);
+          pk2 = cross_pred(bk[8], bk[9], bk[10], bk[11], pf[i][0], pf[i][1], pf[i][2]);
         }
+        acc[i][0] = fmaf(b, pk0, acc[i][0]);
+        acc[i][1] = fmaf(b, pk1, acc[i][1]);
+        acc[i][2] = fmaf(b, pk2, acc[i][2]);
       }
     }
   }
@@ -88,20 +92,11 @@ __device__ __forceinline__ void blend_compute_soa(const float* __restrict__ w, c
   for (int i = 0; i < R; ++i) {
     const int y = y0 + i;
     if (y >= H) break;
-    float o0, o1, o2;
-    if (MODE == 0) {
-      const float p1 = feat ? zi[i][0] : 0.0f, p2 = feat ? zi[i][1] : 0.0f, p3 = feat ? zi[i][2] : 0.0f;
-      o0 = acc[i][0] + acc[i][1] * p1 + acc[i][2] * p2 + acc[i][3] * p3;
-      o1 = acc[i][4] + acc[i][5] * p1 + acc[i][6] * p2 + acc[i][7] * p3;
-      o2 = acc[i][8] + acc[i][9] * p1 + acc[i][10] * p2 + acc[i][11] * p3;
-    } else {
-      o0 = acc[i][0]; o1 = acc[i][1]; o2 = acc[i][2];
-    }
     const float inv = 1.0f / den[i];
     const size_t j = (size_t)y * W + x;
-    out[j] = o0 * inv;
-    out[npix + j] = o1 * inv;
-    out[2 * npix + j] = o2 * inv;
+    out[j] = acc[i][0] * inv;
+    out[npix + j] = acc[i][1] * inv;
+    out[2 * npix + j] = acc[i][2] * inv;
   }
 }
 
@@ -233,7 +228,7 @@ cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& 
 // ---- two-wide variant: each thread blends 2 adjacent columns x R rows -----------------------
 //
 // Tiles are 64 x TH; the window is kBlendBoxW2 = 72 columns (64 + 2 x 4) x (TH + 4) rows of the
-// 12 beta and 3 z planes (one TMA box each) plus an rk plane. A thread's two output columns
+// 12 beta and 3 z planes (one TMA box each) plus a plane of -rk. A thread's two output columns
 // 2tx and 2tx+1 have neighbour columns 2tx-2 .. 2tx+3: three aligned column pairs, each
 // fetched with one 64-bit shared load per plane, so each neighbour value is loaded once for up
 // to two output columns and R rows. Same arithmetic and neighbour order per output as
@@ -261,8 +256,7 @@ __device__ __forceinline__ void blend_compute_soa2(const float* __restrict__ w, 
   const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
   const int x = bx0 + 2 * tx, y0 = by0 + ty * R;
   const bool feat = kp.feature_mode == 0;
-  float zi[NO][3], ri[NO], den[NO];
-  float acc[NO][MODE == 0 ? 12 : 3];
+  float zi[NO][3], pf[NO][3], ri[NO], den[NO], acc[NO][3];
 #pragma unroll
   for (int o = 0; o < 2; ++o)
 #pragma unroll
@@ -270,10 +264,13 @@ __device__ __forceinline__ void blend_compute_soa2(const float* __restrict__ w, 
       const int idx = (ty * R + i + R0) * SW + 2 * tx + 4 + o;
       const int q = o * R + i;
       zi[q][0] = w[12 * P + idx]; zi[q][1] = w[13 * P + idx]; zi[q][2] = w[14 * P + idx];
-      ri[q] = w[15 * P + idx];
-      den[q] = 0.0f;
+      ri[q] = w[15 * P + idx];  // -rk
 #pragma unroll
-      for (int p = 0; p < (MODE == 0 ? 12 : 3); ++p) acc[q][p] = 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        pf[q][c] = feat ? zi[q][c] : 0.0f;
+        acc[q][c] = 0.0f;
+      }
+      den[q] = 0.0f;
     }
 #pragma unroll
   for (int kr = 0; kr < R + 2 * R0; ++kr) {
@@ -299,9 +296,9 @@ __device__ __forceinline__ void blend_compute_soa2(const float* __restrict__ w, 
         float pk0 = 0.0f, pk1 = 0.0f, pk2 = 0.0f;
         if (MODE == 1) {
           const float a1 = feat ? zk0 : 0.0f, a2 = feat ? zk1 : 0.0f, a3 = feat ? zk2 : 0.0f;
-          pk0 = bk[0] + bk[1] * a1 + bk[2] * a2 + bk[3] * a3;
-          pk1 = bk[4] + bk[5] * a1 + bk[6] * a2 + bk[7] * a3;
-          pk2 = bk[8] + bk[9] * a1 + bk[10] * a2 + bk[11] * a3;
+          pk0 = cross_pred(bk[0], bk[1], bk[2], bk[3], a1, a2, a3);
+          pk1 = cross_pred(bk[4], bk[5], bk[6], bk[7], a1, a2, a3);
+          pk2 = cross_pred(bk[8], bk[9], bk[10], bk[11], a1, a2, a3);
         }
 #pragma unroll
         for (int o = 0; o < 2; ++o) {
@@ -313,16 +310,17 @@ __device__ __forceinline__ void blend_compute_soa2(const float* __restrict__ w, 
             if (dy < -R0 || dy > R0) continue;  // compile-time
             const int q = o * R + i;
             const float e0 = zi[q][0] - zk0, e1 = zi[q][1] - zk1, e2 = zi[q][2] - zk2;
-            const float rk = fmaxf(ri[q], rkk);
-            const float b =
-                ex2_approx(kp.spatial[(dy + R0) * RW + (dx + R0)] - (e0 * e0 + e1 * e1 + e2 * e2) * rk);
+            const float rk = -fminf(ri[q], rkk);  // both hold -rk: max of the positive values
+            const float b = ex2_approx(blend_exponent(kp.spatial[(dy + R0) * RW + (dx + R0)], e0, e1, e2, rk));
             den[q] += b;
             if (MODE == 0) {
-#pragma unroll
-              for (int p = 0; p < 12; ++p) acc[q][p] += b * bk[p];
-            } else {
-              acc[q][0] += b * pk0; acc[q][1] += b * pk1; acc[q][2] += b * pk2;
+              pk0 = cross_pred(bk[0], bk[1], bk[2], bk[3], pf[q][0], pf[q][1], pf[q][2]);
+              pk1 = cross_pred(bk[4], bk[5], bk[6], bk[7], pf[q][0], pf[q][1], pf[q][2]);
+              pk2 = cross_pred(bk[8], bk[9], bk[10], bk[11], pf[q][0], pf[q][1], pf[q][2]);
             }
+            acc[q][0] = fmaf(b, pk0, acc[q][0]);
+            acc[q][1] = fmaf(b, pk1, acc[q][1]);
+            acc[q][2] = fmaf(b, pk2, acc[q][2]);
           }
         }
       }
@@ -337,26 +335,127 @@ __device__ __forceinline__ void blend_compute_soa2(const float* __restrict__ w, 
       const int y = y0 + i;
       if (y >= H) break;
       const int q = o * R + i;
-      float o0, o1, o2;
-      if (MODE == 0) {
-        const float p1 = feat ? zi[q][0] : 0.0f, p2 = feat ? zi[q][1] : 0.0f, p3 = feat ? zi[q][2] : 0.0f;
-        o0 = acc[q][0] + acc[q][1] * p1 + acc[q][2] * p2 + acc[q][3] * p3;
-        o1 = acc[q][4] + acc[q][5] * p1 + acc[q][6] * p2 + acc[q][7] * p3;
-        o2 = acc[q][8] + acc[q][9] * p1 + acc[q][10] * p2 + acc[q][11] * p3;
-      } else {
-        o0 = acc[q][0]; o1 = acc[q][1]; o2 = acc[q][2];
-      }
       const float inv = 1.0f / den[q];
       const size_t j = (size_t)y * W + x + o;
-      out[j] = o0 * inv;
-      out[npix + j] = o1 * inv;
-      out[2 * npix + j] = o2 * inv;
+      out[j] = acc[q][0] * inv;
+      out[npix + j] = acc[q][1] * inv;
+      out[2 * npix + j] = acc[q][2] * inv;
     }
   }
 }
 
+// MODE 0 with packed binary32 pairs. The thread's two columns 2tx and 2tx+1 at the same
+// neighbour offset (dx, dy) read neighbour columns c and c+1, which for even dx are the two
+// halves of one aligned 64-bit load: the feature differences, the range exponent, the weight
+// sum, the cross predictions and the accumulations of both outputs then take one packed
+// instruction per pair of values (sub/mul/fma .f32x2). Odd dx (the halves of two different
+// loads) stays scalar. Per output the neighbours are still visited row by row, dx ascending,
+// with the operations of blend_exponent and cross_pred, so the results are bitwise those of
+// the scalar blends.
+template <int TH, int R>
+__device__ __forceinline__ void blend_compute_soa2_packed(const float* __restrict__ w, const KParams& kp,
+                                                          const int W, const int H, float* __restrict__ out,
+                                                          const int bx0, const int by0) {
+  constexpr int R0 = kMaxRadius;
+  static_assert(R0 == 2, "the pairing below assumes a 5 x 5 window");
+  constexpr int RW = 2 * R0 + 1;
+  constexpr int SW = kBlendBoxW2;
+  constexpr int P = TmaBlend2Geom<TH>::PLANE;
+  const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
+  const int x = bx0 + 2 * tx, y0 = by0 + ty * R;
+  const bool feat = kp.feature_mode == 0;
+  // .x: output column 2tx, .y: output column 2tx + 1
+  float2 zi[R][3], pf[R][3], nri[R], den[R], acc[R][3];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int idx = (ty * R + i + R0) * SW + 2 * tx + 4;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      zi[i][c] = *reinterpret_cast<const float2*>(w + (12 + c) * P + idx);
+      pf[i][c] = feat ? zi[i][c] : make_float2(0.0f, 0.0f);
+      acc[i][c] = make_float2(0.0f, 0.0f);
+    }
+    nri[i] = *reinterpret_cast<const float2*>(w + 15 * P + idx);
+    den[i] = make_float2(0.0f, 0.0f);
+  }
+#pragma unroll
+  for (int kr = 0; kr < R + 2 * R0; ++kr) {
+#pragma unroll
+    for (int pair = 0; pair < 3; ++pair) {
+      // neighbour columns 2tx-2+2pair (.x) and 2tx-1+2pair (.y)
+      const int idx = (ty * R + kr) * SW + 2 * tx + 2 + 2 * pair;
+      float2 bk[12];
+#pragma unroll
+      for (int p = 0; p < 12; ++p) bk[p] = *reinterpret_cast<const float2*>(w + p * P + idx);
+      const float2 z0 = *reinterpret_cast<const float2*>(w + 12 * P + idx);
+      const float2 z1 = *reinterpret_cast<const float2*>(w + 13 * P + idx);
+      const float2 z2 = *reinterpret_cast<const float2*>(w + 14 * P + idx);
+      const float2 nr = *reinterpret_cast<const float2*>(w + 15 * P + idx);
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int dy = kr - R0 - i;
+        if (dy < -R0 || dy > R0) continue;  // compile-time
+        // (a) column 2tx+1 against neighbour .x: dx = 2 pair - 3
+        if (pair >= 1) {
+          const int dx = 2 * pair - 3;
+          const float e0 = zi[i][0].y - z0.x, e1 = zi[i][1].y - z1.x, e2 = zi[i][2].y - z2.x;
+          const float rk = -fminf(nri[i].y, nr.x);
+          const float b = ex2_approx(blend_exponent(kp.spatial[(dy + R0) * RW + (dx + R0)], e0, e1, e2, rk));
+          den[i].y += b;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            acc[i][c].y = fmaf(b, cross_pred(bk[4 * c].x, bk[4 * c + 1].x, bk[4 * c + 2].x, bk[4 * c + 3].x,
+                                             pf[i][0].y, pf[i][1].y, pf[i][2].y), acc[i][c].y);
+        }
+        // (b) both columns at dx = 2 pair - 2: column 2tx against .x, column 2tx+1 against .y
+        {
+          const int dx = 2 * pair - 2;
+          const float sp = kp.spatial[(dy + R0) * RW + (dx + R0)];
+          const float2 e0 = f2sub(zi[i][0], z0), e1 = f2sub(zi[i][1], z1), e2 = f2sub(zi[i][2], z2);
+          const float2 nrk = make_float2(fminf(nri[i].x, nr.x), fminf(nri[i].y, nr.y));
+          const float2 t = blend_exponent2(make_float2(sp, sp), e0, e1, e2, nrk);
+          const float2 b = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+          den[i] = f2add(den[i], b);
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            acc[i][c] = f2fma(b, cross_pred2(bk[4 * c], bk[4 * c + 1], bk[4 * c + 2], bk[4 * c + 3],
+                                             pf[i][0], pf[i][1], pf[i][2]), acc[i][c]);
+        }
+        // (c) column 2tx against neighbour .y: dx = 2 pair - 1
+        if (pair <= 1) {
+          const int dx = 2 * pair - 1;
+          const float e0 = zi[i][0].x - z0.y, e1 = zi[i][1].x - z1.y, e2 = zi[i][2].x - z2.y;
+          const float rk = -fminf(nri[i].x, nr.y);
+          const float b = ex2_approx(blend_exponent(kp.spatial[(dy + R0) * RW + (dx + R0)], e0, e1, e2, rk));
+          den[i].x += b;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            acc[i][c].x = fmaf(b, cross_pred(bk[4 * c].y, bk[4 * c + 1].y, bk[4 * c + 2].y, bk[4 * c + 3].y,
+                                             pf[i][0].x, pf[i][1].x, pf[i][2].x), acc[i][c].x);
+        }
+      }
+    }
+  }
+  const size_t npix = (size_t)W * H;
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    if (x + o >= W) break;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int y = y0 + i;
+      if (y >= H) break;
+      const float inv = 1.0f / (o ? den[i].y : den[i].x);
+      const size_t j = (size_t)y * W + x + o;
+      out[j] = (o ? acc[i][0].y : acc[i][0].x) * inv;
+      out[npix + j] = (o ? acc[i][1].y : acc[i][1].x) * inv;
+      out[2 * npix + j] = (o ? acc[i][2].y : acc[i][2].x) * inv;
+    }
+  }
+}
+
+// At most 128 registers a thread, so that two 256-thread CTAs (the shared-memory limit) fit an SM.
 template <int TH, int R, int MODE>
-__global__ void __launch_bounds__(kTW * TH / R)
+__global__ void __launch_bounds__(kTW * TH / R, 65536 / 128 / (kTW * TH / R))
     k_blend_tma2(const KParams kp, const int W, const int H, const __grid_constant__ BlendMaps maps,
                  float* __restrict__ out, int* err) {
   using G = TmaBlend2Geom<TH>;
@@ -395,18 +494,19 @@ __global__ void __launch_bounds__(kTW * TH / R)
       if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
         const float z0 = sm[12 * P + i], z1 = sm[13 * P + i], z2 = sm[14 * P + i];
         const float r = 1.0f / (sqrtf(z0 * z0 + z1 * z1 + z2 * z2) + kp.eps);
-        sm[15 * P + i] = r * r * kp.range_k;
+        sm[15 * P + i] = -(r * r * kp.range_k);
       } else {
 #pragma unroll
         for (int p = 0; p < 12; ++p) sm[p * P + i] = 0.0f;
         sm[12 * P + i] = kFarZ;
         sm[13 * P + i] = kFarZ;
         sm[14 * P + i] = kFarZ;
-        sm[15 * P + i] = 0.0f;
+        sm[15 * P + i] = -0.0f;
       }
     }
     __syncthreads();
-    blend_compute_soa2<TH, R, MODE>(sm, kp, W, H, out, bx0, by0);
+    if constexpr (MODE == 0) blend_compute_soa2_packed<TH, R>(sm, kp, W, H, out, bx0, by0);
+    else blend_compute_soa2<TH, R, MODE>(sm, kp, W, H, out, bx0, by0);
     if (next >= n_tiles) break;
     __syncthreads();  // the window is refilled for the next tile
     if (threadIdx.x == 0) {

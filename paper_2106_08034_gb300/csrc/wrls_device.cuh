@@ -52,6 +52,46 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Base-2 exponent of the blend weight of a (pixel i, neighbour k) pair: spatial - |e|^2 rk with
+// e = z_i - z_k and rk = K / (min(|z_i|, |z_k|) + eps)^2. The rounding order is fixed here
+// (e0^2, then + e1^2, + e2^2 by fused multiply-adds, then one fused multiply-add with -rk) so
+// that every blend kernel, scalar or packed (blend_exponent2), gives the same bits.
+__device__ __forceinline__ float blend_exponent(float sp, float e0, float e1, float e2, float rk) {
+  return fmaf(fmaf(e2, e2, fmaf(e1, e1, e0 * e0)), -rk, sp);
+}
+
+// ---- packed binary32 pairs (sm_100 family: one instruction for two lanes' worth) ----------
+// Each component is rounded as the scalar operation would be (round to nearest even, no
+// flush), so a packed loop gives bitwise the results of its scalar form.
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Cross prediction of one colour channel of pixel i by neighbour k's model (Sec. 5.3):
+// p_i . beta_k,c = b0 + a1 b1 + a2 b2 + a3 b3 with p_i = [1, a1, a2, a3], accumulated in this
+// order by fused multiply-adds in every blend kernel.
+__device__ __forceinline__ float cross_pred(float b0, float b1, float b2, float b3, float a1, float a2, float a3) {
+  return fmaf(a3, b3, fmaf(a2, b2, fmaf(a1, b1, b0)));
+}
+__device__ __forceinline__ float2 cross_pred2(float2 b0, float2 b1, float2 b2, float2 b3, float2 a1, float2 a2,
+                                              float2 a3) {
+  return f2fma(a3, b3, f2fma(a2, b2, f2fma(a1, b1, b0)));
+}
+
+// blend_exponent for two pairs at once; nrk holds -rk.
+__device__ __forceinline__ float2 blend_exponent2(float2 sp, float2 e0, float2 e1, float2 e2, float2 nrk) {
+  return f2fma(f2fma(e2, e2, f2fma(e1, e1, f2mul(e0, e0))), nrk, sp);
+}
+
 // ---- TMA / mbarrier helpers (inline PTX) ------------------------------------------------
 
 // Staged window of the previous state for one 32 x 8 update tile: kStageH rows x kStageW

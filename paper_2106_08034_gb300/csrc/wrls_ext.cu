@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kExtTW * kExtTH / kExtBlendRows)
         const int dy = wy - r;  // this neighbour's row offset (0..4) for output r
         if (dy < 0 || dy > 4) continue;  // resolved at compile time
         const float a0 = zi[r][0] - zk0, a1 = zi[r][1] - zk1, a2 = zi[r][2] - zk2;
-        const float b = ex2_approx(kp.spatial[dy * 5 + dx] - (a0 * a0 + a1 * a1 + a2 * a2) * fmaxf(ri[r], rk));
+        const float b = ex2_approx(blend_exponent(kp.spatial[dy * 5 + dx], a0, a1, a2, fmaxf(ri[r], rk)));
         float p0 = own[0], p1 = own[1], p2 = own[2];
         if (kp.blend_mode == 0) {
           p0 = p1 = p2 = 0.0f;

@@ -219,8 +219,8 @@ __device__ __forceinline__ void blend_fill(float4* __restrict__ sb, float4* __re
 }
 
 // Blend the outputs of the tile whose window is in shared memory. MODE 0: out_i = sum_k b_ik
-// (p_i . beta_k) / sum_k b_ik (neighbours' models predict pixel i); MODE 1: sum_k b_ik (p_k .
-// beta_k) / sum_k b_ik. b_ik = exp(-|dxy|^2 / (2 sigma_s^2)) exp(-d_z(i,k)^2 / h_s^2) with d_z the
+// (p_i . beta_k) / sum_k b_ik (neighbours' models predict pixel i; cross_pred per pair, three
+// accumulators per output); MODE 1: sum_k b_ik (p_k . beta_k) / sum_k b_ik. b_ik = exp(-|dxy|^2 / (2 sigma_s^2)) exp(-d_z(i,k)^2 / h_s^2) with d_z the
 // Eq. 13 distance of the features; 1 / (min(|z_i|, |z_k|) + eps) = max(r_i, r_k), computed in
 // base 2 as exp2(spatial - |z_i - z_k|^2 max(rk_i, rk_k)).
 template <int TH, int R, int MODE>
@@ -233,15 +233,17 @@ __device__ __forceinline__ void blend_compute(const float4* __restrict__ sb,
   const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
   const int x = bx0 + tx, y0 = by0 + ty * R;
   const bool feat = kp.feature_mode == 0;
-  float zi[R][3], ri[R], den[R];
-  float acc[R][MODE == 0 ? 12 : 3];
+  float zi[R][3], pf[R][3], ri[R], den[R], acc[R][3];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const float4 q = szr[(ty * R + i + R0) * kBlendSW + tx + R0];
     zi[i][0] = q.x; zi[i][1] = q.y; zi[i][2] = q.z; ri[i] = q.w;
-    den[i] = 0.0f;
 #pragma unroll
-    for (int p = 0; p < (MODE == 0 ? 12 : 3); ++p) acc[i][p] = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+      pf[i][c] = feat ? zi[i][c] : 0.0f;  // feature entries of p_i
+      acc[i][c] = 0.0f;
+    }
+    den[i] = 0.0f;
   }
 #pragma unroll
   for (int kr = 0; kr < R + 2 * R0; ++kr) {
@@ -253,9 +255,9 @@ __device__ __forceinline__ void blend_compute(const float4* __restrict__ sb,
       float pk0 = 0.0f, pk1 = 0.0f, pk2 = 0.0f;
       if (MODE == 1) {
         const float a1 = feat ? q3.x : 0.0f, a2 = feat ? q3.y : 0.0f, a3 = feat ? q3.z : 0.0f;
-        pk0 = q0.x + q0.y * a1 + q0.z * a2 + q0.w * a3;
-        pk1 = q1.x + q1.y * a1 + q1.z * a2 + q1.w * a3;
-        pk2 = q2.x + q2.y * a1 + q2.z * a2 + q2.w * a3;
+        pk0 = cross_pred(q0.x, q0.y, q0.z, q0.w, a1, a2, a3);
+        pk1 = cross_pred(q1.x, q1.y, q1.z, q1.w, a1, a2, a3);
+        pk2 = cross_pred(q2.x, q2.y, q2.z, q2.w, a1, a2, a3);
       }
 #pragma unroll
       for (int i = 0; i < R; ++i) {
@@ -263,15 +265,16 @@ __device__ __forceinline__ void blend_compute(const float4* __restrict__ sb,
         if (dy < -R0 || dy > R0) continue;  // compile-time
         const float e0 = zi[i][0] - q3.x, e1 = zi[i][1] - q3.y, e2 = zi[i][2] - q3.z;
         const float rk = fmaxf(ri[i], q3.w);  // K / (min(|z_i|, |z_k|) + eps)^2
-        const float b = ex2_approx(kp.spatial[(dy + R0) * RW + (dx + R0)] - (e0 * e0 + e1 * e1 + e2 * e2) * rk);
+        const float b = ex2_approx(blend_exponent(kp.spatial[(dy + R0) * RW + (dx + R0)], e0, e1, e2, rk));
         den[i] += b;
         if (MODE == 0) {
-          acc[i][0] += b * q0.x; acc[i][1] += b * q0.y; acc[i][2] += b * q0.z; acc[i][3] += b * q0.w;
-          acc[i][4] += b * q1.x; acc[i][5] += b * q1.y; acc[i][6] += b * q1.z; acc[i][7] += b * q1.w;
-          acc[i][8] += b * q2.x; acc[i][9] += b * q2.y; acc[i][10] += b * q2.z; acc[i][11] += b * q2.w;
-        } else {
-          acc[i][0] += b * pk0; acc[i][1] += b * pk1; acc[i][2] += b * pk2;
+          pk0 = cross_pred(q0.x, q0.y, q0.z, q0.w, pf[i][0], pf[i][1], pf[i][2]);
+          pk1 = cross_pred(q1.x, q1.y, q1.z, q1.w, pf[i][0], pf[i][1], pf[i][2]);
+          pk2 = cross_pred(q2.x, q2.y, q2.z, q2.w, pf[i][0], pf[i][1], pf[i][2]);
         }
+        acc[i][0] = fmaf(b, pk0, acc[i][0]);
+        acc[i][1] = fmaf(b, pk1, acc[i][1]);
+        acc[i][2] = fmaf(b, pk2, acc[i][2]);
       }
     }
   }
@@ -281,21 +284,11 @@ __device__ __forceinline__ void blend_compute(const float4* __restrict__ sb,
   for (int i = 0; i < R; ++i) {
     const int y = y0 + i;
     if (y >= H) break;
-    float o0, o1, o2;
-    if (MODE == 0) {
-      // sum_k b_k (p_i . beta_k) = p_i . sum_k b_k beta_k, p_i = [1, z_i]
-      const float p1 = feat ? zi[i][0] : 0.0f, p2 = feat ? zi[i][1] : 0.0f, p3 = feat ? zi[i][2] : 0.0f;
-      o0 = acc[i][0] + acc[i][1] * p1 + acc[i][2] * p2 + acc[i][3] * p3;
-      o1 = acc[i][4] + acc[i][5] * p1 + acc[i][6] * p2 + acc[i][7] * p3;
-      o2 = acc[i][8] + acc[i][9] * p1 + acc[i][10] * p2 + acc[i][11] * p3;
-    } else {
-      o0 = acc[i][0]; o1 = acc[i][1]; o2 = acc[i][2];
-    }
     const float inv = 1.0f / den[i];
     const size_t j = (size_t)y * W + x;
-    out[j] = o0 * inv;
-    out[npix + j] = o1 * inv;
-    out[2 * npix + j] = o2 * inv;
+    out[j] = acc[i][0] * inv;
+    out[npix + j] = acc[i][1] * inv;
+    out[2 * npix + j] = acc[i][2] * inv;
   }
 }
 
