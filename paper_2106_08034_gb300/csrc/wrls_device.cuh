@@ -191,9 +191,11 @@ struct StateF32 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) z[c] = __ldcg(base + (kZ + c) * plane_stride + idx);
   }
+  // idx < 2^32: each plane's base is uniform over the warp and the pixel offset 32-bit
   __device__ __forceinline__ void store(size_t idx, const float v[kNState]) const {
+    const uint32_t i = (uint32_t)idx;
 #pragma unroll
-    for (int p = 0; p < kNState; ++p) base[p * plane_stride + idx] = v[p];
+    for (int p = 0; p < kNState; ++p) (base + p * plane_stride)[i] = v[p];
   }
   // Staged window: [plane][kStageH][kStageW] binary32; box origin x multiple of 4 (16 B).
   static constexpr int kAlignX = 4;
@@ -260,11 +262,12 @@ struct State16 {
     float s = fmaxf(fmaxf(v[kP + 0], v[kP + 4]), fmaxf(v[kP + 7], v[kP + 9]));
     if (!(s > 0.0f) || !isfinite(s)) s = 1.0f;
     const float inv_s = 1.0f / s;
-    scale[idx] = s;
+    const uint32_t i = (uint32_t)idx;
+    scale[i] = s;
 #pragma unroll
     for (int p = 0; p < kNState; ++p) {
       float f = (p >= kP && p < kZ) ? v[p] * inv_s : v[p];
-      base[p * plane_stride + idx] = from_f(f);
+      (base + p * plane_stride)[i] = from_f(f);
     }
   }
 };
@@ -306,6 +309,34 @@ __device__ __forceinline__ void init_model(const KParams& kp, const float z[3], 
   }
 }
 
+// Bilinear interpolation of every state value from its four taps in a fixed rounding order,
+// st = ((w00 a + w10 b) + w01 c) + w11 d by fused multiply-adds; consecutive planes are taken in
+// packed pairs (same rounding per component). bilerp_top takes the taps (x0, y0), (x1, y0),
+// bilerp_bottom adds (x0, y1), (x1, y1).
+__device__ __forceinline__ void bilerp_top(float w00, float w10, const float a[kNState], const float b[kNState],
+                                           float st[kNState]) {
+  const float2 wa = make_float2(w00, w00), wb = make_float2(w10, w10);
+#pragma unroll
+  for (int p = 0; p + 1 < kNState; p += 2) {
+    const float2 v = f2fma(wb, make_float2(b[p], b[p + 1]), f2mul(wa, make_float2(a[p], a[p + 1])));
+    st[p] = v.x;
+    st[p + 1] = v.y;
+  }
+  if (kNState % 2) st[kNState - 1] = fmaf(w10, b[kNState - 1], w00 * a[kNState - 1]);
+}
+__device__ __forceinline__ void bilerp_bottom(float w01, float w11, const float c[kNState], const float d[kNState],
+                                              float st[kNState]) {
+  const float2 wc = make_float2(w01, w01), wd = make_float2(w11, w11);
+#pragma unroll
+  for (int p = 0; p + 1 < kNState; p += 2) {
+    const float2 v = f2fma(wd, make_float2(d[p], d[p + 1]),
+                           f2fma(wc, make_float2(c[p], c[p + 1]), make_float2(st[p], st[p + 1])));
+    st[p] = v.x;
+    st[p + 1] = v.y;
+  }
+  if (kNState % 2) st[kNState - 1] = fmaf(w11, d[kNState - 1], fmaf(w01, c[kNState - 1], st[kNState - 1]));
+}
+
 // Bilinear fetch of the previous state at q = (qx, qy) (Sec. 5.3: models are reprojected,
 // not colours). q is valid; taps beyond the last row/column are clamped.
 template <class SV>
@@ -319,12 +350,10 @@ __device__ __forceinline__ void gather_bilinear(const SV& prev, int W, int H, fl
   float a[kNState], b[kNState];
   prev.load((size_t)y0 * prev.pitch + x0, a);
   prev.load((size_t)y0 * prev.pitch + x1, b);
-#pragma unroll
-  for (int p = 0; p < kNState; ++p) st[p] = w00 * a[p] + w10 * b[p];
+  bilerp_top(w00, w10, a, b, st);
   prev.load((size_t)y1 * prev.pitch + x0, a);
   prev.load((size_t)y1 * prev.pitch + x1, b);
-#pragma unroll
-  for (int p = 0; p < kNState; ++p) st[p] += w01 * a[p] + w11 * b[p];
+  bilerp_bottom(w01, w11, a, b, st);
 }
 
 // Bilinear fetch from the staged window whose origin is (X0, Y0).
@@ -340,12 +369,10 @@ __device__ __forceinline__ void gather_bilinear_staged(const unsigned char* stag
   float a[kNState], b[kNState];
   SV::load_staged(stage, r0 + x0 - X0, a);
   SV::load_staged(stage, r0 + x1 - X0, b);
-#pragma unroll
-  for (int p = 0; p < kNState; ++p) st[p] = w00 * a[p] + w10 * b[p];
+  bilerp_top(w00, w10, a, b, st);
   SV::load_staged(stage, r1 + x0 - X0, a);
   SV::load_staged(stage, r1 + x1 - X0, b);
-#pragma unroll
-  for (int p = 0; p < kNState; ++p) st[p] += w01 * a[p] + w11 * b[p];
+  bilerp_bottom(w01, w11, a, b, st);
 }
 
 // Eq. 12 feature, Eq. 13 weight and the wRLS update (Eq. 8, 14, 9, 11) of one pixel.
