@@ -34,7 +34,7 @@ BYTES_PATH_F32 = 232     # per pixel and frame for the whole path: + out 12
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_update launch on a
 # 1920x1080 frame, from the ncu capture summarised in profiles/k_update_pan_1080p.md (same
 # kernel build). Writes still held in L2 when the kernel ends are not counted by ncu.
-TRAFFIC_PER_LAUNCH = {"k_update": 248871680 + 168864768}
+TRAFFIC_PER_LAUNCH = {"k_update": 248864768 + 168868352}
 # Extended path with the G-buffer predictor p = [1, z, g_1..g_4] (d = 8): the state is
 # 3d + d(d+1)/2 + 3 = 63 binary32 values (252 B) per pixel.
 BYTES_UPDATE_D8 = 252 + 12 + 8 + 16 + 252   # state read, radiance, motion, 4 G-buffer planes, state write
