@@ -213,6 +213,32 @@ def test_blend_configs_bitwise_identical_and_autotune():
         assert torch.equal(o, outs[0])
 
 
+@pytest.mark.parametrize("kw", [dict(blend_mode=1), dict(feature_mode=1), dict(radius=1), dict(radius=0)])
+def test_blend_configs_bitwise_identical_variants(kw):
+    """Every blend configuration (scalar, persistent, two-wide packed) gives the same bits for
+    the blend variants too (own predictions, no feature, 3 x 3 window, temporal only), on a
+    ragged image, and the two-wide output matches the oracle."""
+    spec = synth.SceneSpec(203, 45, 4, seed=52, motion="orbit", firefly_frac=0.05)
+    p = W.wrls_params_default(**kw)
+    fr = cpu_frames(spec)
+    outs = []
+    for cfg in range(W.BLEND_CONFIGS):
+        s = W.Stream(spec.width, spec.height, p)
+        W.wrls_stream_set_blend_config(s.handle, cfg)
+        o = torch.empty(3, spec.height, spec.width, device="cuda")
+        for f in fr:
+            s.denoise(f["radiance"].cuda(), f["motion"].cuda(), o)
+        W.wrls_stream_check(s.handle)
+        outs.append(o.cpu())
+        s.close()
+    for cfg, o in enumerate(outs[1:], 1):
+        assert torch.equal(o, outs[0]), cfg
+    st = O.OracleStream(spec.width, spec.height, oracle_params_from(p))
+    for f in fr:
+        ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
+    assert rel_err(outs[9].numpy(), ref) <= REL_TOL
+
+
 @pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_blend_configs_match_oracle(cfg):
     spec = synth.SceneSpec(197, 53, 5, seed=51, motion="pan", firefly_frac=0.05)
