@@ -224,9 +224,11 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
  * denoised frame; `out` (device, 3 x H x W) is overwritten and ends up holding the current
  * frame's output. times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per
  * launch (-1 for a configuration the state format does not offer) and *chosen (optional)
- * the selected configuration. Synchronises the stream. wrls_batch_tick uses each stream's
- * configuration; wrls_batch_tick_static uses the one-CTA-per-tile configuration of the same
- * tile shape. Streams on the extended path have
+ * the selected configuration. Synchronises the stream. After wrls_stream_create the
+ * configuration is 9 for binary32 state on images of at least 2^19 pixels (and 72 x 20), else
+ * 2. wrls_batch_tick uses each stream's configuration; wrls_batch_tick_static uses a
+ * one-CTA-per-tile configuration of the same tile rows (2 for configurations 8 and 9).
+ * Streams on the extended path have
  * one blend configuration: every time is reported as -1 and 0 is chosen, without a launch.
  */
 #define WRLS_BLEND_CONFIGS 10

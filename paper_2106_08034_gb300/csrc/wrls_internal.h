@@ -62,7 +62,7 @@ cudaError_t launch_update(const KParams& kp, const StateDesc& prev, const StateD
 // Encode the TMA tensor maps of a state copy (sets stage_ok; false only on a driver error).
 bool encode_stage_maps(StateDesc& d, const char** why);
 // Blend tile configurations (tile rows TH x output rows per thread R):
-// 0: 16x4 (default), 1: 8x4, 2: 16x2, 3: 32x4 -- one CTA per tile, synchronous fill;
+// 0: 16x4, 1: 8x4, 2: 16x2, 3: 32x4 -- one CTA per tile, synchronous fill;
 // 4: 16x2, 5: 16x2, 6: 8x2, 7: 16x4 -- persistent, TMA-filled windows, double-buffered (4, 6)
 // or single (5, 7) (binary32 state, images of at least 40 x 20 pixels);
 // 8: 16 rows x 2 x 2, 9: 8 rows x 2 x 2 -- persistent, TMA-filled, each thread 2 columns x
@@ -74,9 +74,10 @@ inline bool blend_config_ok(int cfg, int precision, bool tma_ok, bool tma2_ok) {
   if (cfg < kBlendSyncConfigs) return true;
   return precision == 0 && (cfg < 8 ? tma_ok : tma2_ok);
 }
-// The synchronous configuration with the same tile shape (used by wrls_batch_tick_static).
+// The synchronous configuration wrls_batch_tick_static runs in place of a persistent one (the
+// same tile rows and outputs per thread; 16 x 2 for the two-wide configurations).
 inline int blend_sync_config(int cfg) {
-  static const int map[kBlendConfigs] = {0, 1, 2, 3, 2, 2, 1, 0, 2, 1};
+  static const int map[kBlendConfigs] = {0, 1, 2, 3, 2, 2, 1, 0, 2, 2};
   return (cfg >= 0 && cfg < kBlendConfigs) ? map[cfg] : 0;
 }
 cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err, cudaStream_t cs);
