@@ -18,8 +18,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "wrls_internal.h"
 #include "wrls_fused.cuh"
@@ -246,6 +248,7 @@ struct wrls_batch {
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kLanes] = {};
   cudaGraphExec_t exec_chains = nullptr;    // the per-stream tick graph
+  std::vector<int> order;                   // frames by pixel count, largest first
   size_t table_bytes = 0;
   void* d_table = nullptr;
   int* d_counters = nullptr;
@@ -294,9 +297,22 @@ static wrls_status tick_chains(wrls_batch* b, const wrls_frame_io* frames, int n
   e = cudaEventRecord(b->ev_fork, b->cap);
   const int lanes = n < wrls_batch::kLanes ? n : wrls_batch::kLanes;
   for (int k = 0; k < lanes && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->lane[k], b->ev_fork, 0);
-  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+  // Largest frame first, each to the branch with the fewest pixels so far, so that the
+  // branches carry similar work and each ends with its smallest kernels.
+  std::vector<int>& order = b->order;
+  order.resize(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto px = [&](int i) { return (long long)frames[i].stream->W * frames[i].stream->H; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return px(a) > px(c); });
+  long long load[wrls_batch::kLanes] = {};
+  for (int j = 0; j < n && e == cudaSuccess; ++j) {
+    const int i = order[j];
+    int k = 0;
+    for (int m = 1; m < lanes; ++m)
+      if (load[m] < load[k]) k = m;
+    load[k] += px(i);
     wrls_stream* s = frames[i].stream;
-    cudaStream_t ln = b->lane[i % lanes];
+    cudaStream_t ln = b->lane[k];
     const StateDesc& prev = s->state[s->cur];
     const StateDesc& next = s->state[next_copy(s)];
     e = s->pipeline == 3
@@ -348,6 +364,13 @@ wrls_status wrls_batch_create(int max_streams, wrls_batch** out) {
   wrls_batch* b = new (std::nothrow) wrls_batch();
   if (!b) { set_error("wrls_batch_create: host allocation failed"); return WRLS_ERR_OOM; }
   b->max_streams = max_streams;
+  try {
+    b->order.reserve(max_streams);  // the ticks resize within this capacity: no allocation
+  } catch (...) {
+    delete b;
+    set_error("wrls_batch_create: host allocation failed");
+    return WRLS_ERR_OOM;
+  }
   cudaGetDevice(&b->device);
   b->fused_ctas = 3 * sm_count();
   b->table_bytes = sizeof(BatchHeader) + (size_t)max_streams * sizeof(FrameWork);
