@@ -220,7 +220,8 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
  * double-buffered (4, 6: the next window arrives while the current one is blended) or single
  * (5, 7: more CTAs per SM) (binary32 state, images of at least 40 x 20 pixels); 8: 16 rows,
  * 9: 8 rows, with each thread blending 2 adjacent columns x 2 rows from a TMA-filled window
- * (64-column tiles; binary32 state, images of at least 72 x 20 pixels). All configurations give bitwise identical outputs. Requires one
+ * (64-column tiles; images of at least 72 x 20 pixels; with a 16-bit state the planes are
+ * copied as 16-bit values, decoded in shared memory, and need a row pitch of at least 80). All configurations give bitwise identical outputs. Requires one
  * denoised frame; `out` (device, 3 x H x W) is overwritten and ends up holding the current
  * frame's output. times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per
  * launch (-1 for a configuration the state format does not offer) and *chosen (optional)

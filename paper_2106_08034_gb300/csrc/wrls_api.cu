@@ -109,6 +109,19 @@ bool encode_stage_maps(StateDesc& d, const char** why) {
       }
       d.blend_tma2_ok = true;
     }
+  } else if (!f32 && d.H >= 20 && d.pitch >= kBlendBoxW2 + 8) {
+    // two-wide blend windows of the 16-bit planes: 80-column boxes from x - 8 (16 bytes)
+    const cuuint32_t w = (cuuint32_t)(kBlendBoxW2 + 8);
+    const cuuint32_t hb16[3] = {w, 20, 12}, hz16[3] = {w, 20, 3}, hb8[3] = {w, 12, 12}, hz8[3] = {w, 12, 3};
+    CUtensorMap* m2[4] = {&d.bmaps.beta16w, &d.bmaps.z16w, &d.bmaps.beta8w, &d.bmaps.z8w};
+    const cuuint32_t* bx2[4] = {hb16, hz16, hb8, hz8};
+    for (int i = 0; i < 4; ++i) {
+      r = enc(m2[i], CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, d.base, dims, strides, bx2[i], es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for a 16-bit two-wide blend window"; return false; }
+    }
+    d.blend_tma2_ok = true;
   }
   return true;
 }

@@ -12,6 +12,8 @@
 // planes directly (structure of arrays: a warp's loads are 32 consecutive floats).
 // Waits are bounded (kWaitLimit clocks); on expiry the CTA records WRLS_ERR_TIMEOUT, waits
 // (bounded) for its copies in flight and returns.
+#include <string.h>
+
 #include "wrls_internal.h"
 #include "wrls_tiles.cuh"
 
@@ -154,9 +156,7 @@ __global__ void __launch_bounds__(kTW * TH / R)
     for (int i = threadIdx.x; i < P; i += NT) {
       const int gx = bx0 - 4 + i % kBlendBoxW, gy = by0 - 2 + i / kBlendBoxW;
       if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-        const float z0 = wcur[12 * P + i], z1 = wcur[13 * P + i], z2 = wcur[14 * P + i];
-        const float r = 1.0f / (sqrtf(z0 * z0 + z1 * z1 + z2 * z2) + kp.eps);
-        wcur[15 * P + i] = r * r * kp.range_k;
+        wcur[15 * P + i] = blend_rk(wcur[12 * P + i], wcur[13 * P + i], wcur[14 * P + i], kp.eps, kp.range_k);
       } else {
 #pragma unroll
         for (int p = 0; p < 12; ++p) wcur[p * P + i] = 0.0f;
@@ -492,9 +492,7 @@ __global__ void __launch_bounds__(kTW * TH / R, 65536 / 128 / (kTW * TH / R))
     for (int i = threadIdx.x; i < P; i += NT) {
       const int gx = bx0 - 4 + i % kBlendBoxW2, gy = by0 - 2 + i / kBlendBoxW2;
       if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-        const float z0 = sm[12 * P + i], z1 = sm[13 * P + i], z2 = sm[14 * P + i];
-        const float r = 1.0f / (sqrtf(z0 * z0 + z1 * z1 + z2 * z2) + kp.eps);
-        sm[15 * P + i] = -(r * r * kp.range_k);
+        sm[15 * P + i] = -blend_rk(sm[12 * P + i], sm[13 * P + i], sm[14 * P + i], kp.eps, kp.range_k);
       } else {
 #pragma unroll
         for (int p = 0; p < 12; ++p) sm[p * P + i] = 0.0f;
@@ -543,9 +541,180 @@ static cudaError_t launch_tma2_cfg(const KParams& kp, const StateDesc& cur, floa
   return cudaGetLastError();
 }
 
+// ---- two-wide variant for the 16-bit state formats ---------------------------------------
+//
+// The 12 beta and 3 z planes arrive as 16-bit values: one TMA box per plane group of 80
+// columns (x origin tile x - 8, a 16-byte boundary) x (TH + 4) rows, landing in the upper part
+// of the binary32 window buffer. A conversion pass then writes the binary32 window of the
+// binary32 kernel (72 columns from tile x - 4, 16 planes with -rk) in three groups of five
+// planes: each thread reads its raw values of a group into registers, a barrier, then writes
+// the decoded group. The raw planes sit at the end of the buffer, placed so that the binary32
+// planes of a group never overlap the raw planes of a later group (static_assert below): one
+// buffer serves both, and the kernel keeps the shared memory, hence the occupancy, of the
+// binary32 kernel. The blend is blend_compute_soa2_packed / blend_compute_soa2 on the decoded
+// values, so the outputs equal those of the other blend configurations for the same state.
+template <int TH>
+struct TmaBlend2hGeom {
+  static constexpr int SH = TH + 2 * kMaxRadius;
+  static constexpr int PLANE = TmaBlend2Geom<TH>::PLANE;  // binary32 plane: SH x 72
+  static constexpr int RAWW = kBlendBoxW2 + 8;              // 16-bit values a raw row (80)
+  static constexpr int RAWPLANE = SH * RAWW;
+  static constexpr int BUF_BYTES = 16 * PLANE * 4;
+  static constexpr int RAW_OFF = (BUF_BYTES - 15 * RAWPLANE * 2) / 128 * 128;
+  static constexpr uint32_t kTx = 15u * RAWPLANE * 2u;
+  static constexpr int kSmemBytes = BUF_BYTES + 128;
+  static constexpr int kPairs = SH * (kBlendBoxW2 / 2);     // column pairs of the binary32 window
+  static_assert(RAW_OFF >= 10 * (4 * PLANE - 2 * RAWPLANE),
+                "binary32 planes of a group would overlap raw planes of a later group");
+  static_assert(RAW_OFF + 15 * RAWPLANE * 2 <= BUF_BYTES, "raw planes exceed the buffer");
+  static_assert((12 * RAWPLANE * 2) % 128 == 0, "z box destination not 128-byte aligned");
+};
+
+template <typename T>
+__device__ __forceinline__ float2 unpack16x2(uint32_t u);
+template <>
+__device__ __forceinline__ float2 unpack16x2<__nv_bfloat16>(uint32_t u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));  // exact
+}
+template <>
+__device__ __forceinline__ float2 unpack16x2<__half>(uint32_t u) {
+  __half2 h;
+  memcpy(&h, &u, sizeof(h));
+  return __half22float2(h);
+}
+
+template <int TH, int R, int MODE, typename T>
+__global__ void __launch_bounds__(kTW * TH / R, 65536 / 128 / (kTW * TH / R))
+    k_blend_tma2h(const KParams kp, const int W, const int H, const __grid_constant__ BlendMaps maps,
+                  float* __restrict__ out, int* err) {
+  using G = TmaBlend2hGeom<TH>;
+  constexpr int NT = kTW * TH / R;
+  constexpr int P = G::PLANE;
+  constexpr int TW2 = 2 * kTW;
+  constexpr int NJ = (G::kPairs + NT - 1) / NT;  // column pairs a thread converts
+  constexpr int HW = kBlendBoxW2 / 2;             // column pairs a row
+  extern __shared__ unsigned char dsmem[];
+  unsigned char* buf = align128(dsmem);
+  float* sm = reinterpret_cast<float*>(buf);
+  const uint32_t* raw = reinterpret_cast<const uint32_t*>(buf + G::RAW_OFF);  // two values a word
+  __shared__ alignas(8) uint64_t bar;
+  const CUtensorMap* mb = TH == 16 ? &maps.beta16w : &maps.beta8w;
+  const CUtensorMap* mz = TH == 16 ? &maps.z16w : &maps.z8w;
+  const int tiles_x = (W + TW2 - 1) / TW2;
+  const int n_tiles = tiles_x * ((H + TH - 1) / TH);
+  int tile = blockIdx.x;
+  if (tile >= n_tiles) return;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t ph = 0u;
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, G::kTx);
+    tma_load_3d(buf + G::RAW_OFF, mb, (tile % tiles_x) * TW2 - 8, (tile / tiles_x) * TH - 2, 0, &bar);
+    tma_load_3d(buf + G::RAW_OFF + 12 * G::RAWPLANE * 2, mz, (tile % tiles_x) * TW2 - 8, (tile / tiles_x) * TH - 2,
+                kZ, &bar);
+  }
+  for (;;) {
+    const int next = tile + gridDim.x;
+    const bool ok = mbar_wait_bounded(&bar, ph);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(err, (int)WRLS_ERR_TIMEOUT);
+      mbar_wait_bounded(&bar, ph);  // the copies may still be in flight
+      return;
+    }
+    ph ^= 1u;
+    const int bx0 = (tile % tiles_x) * TW2, by0 = (tile / tiles_x) * TH;
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      uint32_t v[NJ][5];
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int j = threadIdx.x + jj * NT;
+        if (j < G::kPairs) {
+          const int w = (j / HW) * (G::RAWW / 2) + j % HW + 2;  // raw columns 2cp+4, 2cp+5
+#pragma unroll
+          for (int q = 0; q < 5; ++q) v[jj][q] = raw[(5 * g + q) * (G::RAWPLANE / 2) + w];
+        }
+      }
+      __syncthreads();  // the group's raw values are read before its binary32 planes are written
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int j = threadIdx.x + jj * NT;
+        if (j < G::kPairs) {
+          const int row = j / HW, cp = j % HW;
+          const int gx = bx0 - 4 + 2 * cp, gy = by0 - 2 + row;
+          const bool rin = gy >= 0 && gy < H;
+          const bool in0 = rin && gx >= 0 && gx < W, in1 = rin && gx + 1 >= 0 && gx + 1 < W;
+          float2 f[5];
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const float far = (5 * g + q) < 12 ? 0.0f : kFarZ;
+            f[q] = unpack16x2<T>(v[jj][q]);
+            if (!in0) f[q].x = far;
+            if (!in1) f[q].y = far;
+            *reinterpret_cast<float2*>(sm + (5 * g + q) * P + row * kBlendBoxW2 + 2 * cp) = f[q];
+          }
+          if (g == 2) {
+            const float2 nr = make_float2(in0 ? -blend_rk(f[2].x, f[3].x, f[4].x, kp.eps, kp.range_k) : -0.0f,
+                                          in1 ? -blend_rk(f[2].y, f[3].y, f[4].y, kp.eps, kp.range_k) : -0.0f);
+            *reinterpret_cast<float2*>(sm + 15 * P + row * kBlendBoxW2 + 2 * cp) = nr;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (MODE == 0) blend_compute_soa2_packed<TH, R>(sm, kp, W, H, out, bx0, by0);
+    else blend_compute_soa2<TH, R, MODE>(sm, kp, W, H, out, bx0, by0);
+    if (next >= n_tiles) break;
+    __syncthreads();  // the buffer is refilled for the next tile
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar, G::kTx);
+      tma_load_3d(buf + G::RAW_OFF, mb, (next % tiles_x) * TW2 - 8, (next / tiles_x) * TH - 2, 0, &bar);
+      tma_load_3d(buf + G::RAW_OFF + 12 * G::RAWPLANE * 2, mz, (next % tiles_x) * TW2 - 8,
+                  (next / tiles_x) * TH - 2, kZ, &bar);
+    }
+    tile = next;
+  }
+}
+
+template <int TH, int R, int MODE, typename T>
+static cudaError_t launch_tma2h_cfg(const KParams& kp, const StateDesc& cur, float* out, int* err, cudaStream_t cs) {
+  constexpr int bytes = TmaBlend2hGeom<TH>::kSmemBytes;
+  constexpr int nt = kTW * TH / R;
+  static int per_sm = 0;  // per instantiation
+  if (!per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_blend_tma2h<TH, R, MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_tma2h<TH, R, MODE, T>, nt, bytes);
+    if (e != cudaSuccess) return e;
+    per_sm = occ > 0 ? occ : 1;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tiles = ((cur.W + 2 * kTW - 1) / (2 * kTW)) * ((cur.H + TH - 1) / TH);
+  const int use = (kp.blend_ctas_cap > 0 && kp.blend_ctas_cap < per_sm) ? kp.blend_ctas_cap : per_sm;
+  int grid = sms * use;
+  if (grid > n_tiles) grid = n_tiles;
+  k_blend_tma2h<TH, R, MODE, T><<<grid, nt, bytes, cs>>>(kp, cur.W, cur.H, cur.bmaps, out, err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_two_wide_16(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
+                                      cudaStream_t cs) {
+  if (kp.blend_mode == 0)
+    return cfg == 0 ? launch_tma2h_cfg<16, 2, 0, T>(kp, cur, out, err, cs) : launch_tma2h_cfg<8, 2, 0, T>(kp, cur, out, err, cs);
+  return cfg == 0 ? launch_tma2h_cfg<16, 2, 1, T>(kp, cur, out, err, cs) : launch_tma2h_cfg<8, 2, 1, T>(kp, cur, out, err, cs);
+}
+
 cudaError_t launch_blend_two_wide(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
                                   cudaStream_t cs) {
-  if (cur.precision != 0 || !cur.blend_tma2_ok) return cudaErrorInvalidValue;
+  if (!cur.blend_tma2_ok) return cudaErrorInvalidValue;
+  if (cur.precision == 1) return launch_two_wide_16<__nv_bfloat16>(kp, cfg, cur, out, err, cs);
+  if (cur.precision == 2) return launch_two_wide_16<__half>(kp, cfg, cur, out, err, cs);
+  if (cur.precision != 0) return cudaErrorInvalidValue;
   if (kp.blend_mode == 0)
     return cfg == 0 ? launch_tma2_cfg<16, 2, 0>(kp, cur, out, err, cs) : launch_tma2_cfg<8, 2, 0>(kp, cur, out, err, cs);
   return cfg == 0 ? launch_tma2_cfg<16, 2, 1>(kp, cur, out, err, cs) : launch_tma2_cfg<8, 2, 1>(kp, cur, out, err, cs);

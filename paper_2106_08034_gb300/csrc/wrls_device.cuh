@@ -60,6 +60,13 @@ __device__ __forceinline__ float blend_exponent(float sp, float e0, float e1, fl
   return fmaf(fmaf(e2, e2, fmaf(e1, e1, e0 * e0)), -rk, sp);
 }
 
+// Range factor of a window pixel: rk = K / (|z| + eps)^2 with K = log2(e) / h_s^2, |z|^2 summed
+// by fused multiply-adds (one rounding order for every blend kernel).
+__device__ __forceinline__ float blend_rk(float z0, float z1, float z2, float eps, float range_k) {
+  const float r = 1.0f / (sqrtf(fmaf(z2, z2, fmaf(z1, z1, z0 * z0))) + eps);
+  return r * r * range_k;
+}
+
 // ---- packed binary32 pairs (sm_100 family: one instruction for two lanes' worth) ----------
 // Each component is rounded as the scalar operation would be (round to nearest even, no
 // flush), so a packed loop gives bitwise the results of its scalar form.

@@ -66,13 +66,14 @@ bool encode_stage_maps(StateDesc& d, const char** why);
 // 4: 16x2, 5: 16x2, 6: 8x2, 7: 16x4 -- persistent, TMA-filled windows, double-buffered (4, 6)
 // or single (5, 7) (binary32 state, images of at least 40 x 20 pixels);
 // 8: 16 rows x 2 x 2, 9: 8 rows x 2 x 2 -- persistent, TMA-filled, each thread 2 columns x
-// 2 rows (binary32 state, images of at least 72 x 20 pixels).
+// 2 rows (any state format; images of at least 72 x 20 pixels, 16-bit formats a row pitch of
+// at least 80).
 constexpr int kBlendConfigs = 10;
 constexpr int kBlendSyncConfigs = 4;
 inline bool blend_config_ok(int cfg, int precision, bool tma_ok, bool tma2_ok) {
   if (cfg < 0 || cfg >= kBlendConfigs) return false;
   if (cfg < kBlendSyncConfigs) return true;
-  return precision == 0 && (cfg < 8 ? tma_ok : tma2_ok);
+  return cfg < 8 ? (precision == 0 && tma_ok) : tma2_ok;
 }
 // The synchronous configuration wrls_batch_tick_static runs in place of a persistent one (the
 // same tile rows and outputs per thread; 16 x 2 for the two-wide configurations).

@@ -203,11 +203,10 @@ __device__ __forceinline__ void blend_fill(float4* __restrict__ sb, float4* __re
       float b[12], z[3];
       if constexpr (COHERENT) cur.load_beta_z_l2((size_t)gy * cur.pitch + gx, b, z);
       else cur.load_beta_z((size_t)gy * cur.pitch + gx, b, z);
-      const float r = 1.0f / (sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]) + kp.eps);
       sb[3 * i + 0] = make_float4(b[0], b[1], b[2], b[3]);
       sb[3 * i + 1] = make_float4(b[4], b[5], b[6], b[7]);
       sb[3 * i + 2] = make_float4(b[8], b[9], b[10], b[11]);
-      szr[i] = make_float4(z[0], z[1], z[2], r * r * kp.range_k);
+      szr[i] = make_float4(z[0], z[1], z[2], blend_rk(z[0], z[1], z[2], kp.eps, kp.range_k));
     } else {
       const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       sb[3 * i + 0] = zero;

@@ -239,6 +239,34 @@ def test_blend_configs_bitwise_identical_variants(kw):
     assert rel_err(outs[9].numpy(), ref) <= REL_TOL
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_blend_configs_bitwise_identical_16bit(prec):
+    """With BF16 / FP16 state the one-CTA-per-tile blends (0-3) and the two-wide blends (8, 9),
+    which copy the 16-bit planes by TMA and decode them in shared memory, give the same bits;
+    configurations 4-7 are refused; autotune times 0-3, 8, 9 only."""
+    spec = synth.SceneSpec(203, 45, 4, seed=53, motion="orbit", firefly_frac=0.05)
+    p = W.wrls_params_default(state_precision=prec)
+    fr = cpu_frames(spec)
+    outs = {}
+    for cfg in (0, 1, 2, 3, 8, 9):
+        s = W.Stream(spec.width, spec.height, p)
+        W.wrls_stream_set_blend_config(s.handle, cfg)
+        o = torch.empty(3, spec.height, spec.width, device="cuda")
+        for f in fr:
+            s.denoise(f["radiance"].cuda(), f["motion"].cuda(), o)
+        if cfg == 0:
+            times, chosen = W.wrls_stream_autotune(s.handle, o, reps=2)
+            assert [t > 0 for t in times] == [c in (0, 1, 2, 3, 8, 9) for c in range(W.BLEND_CONFIGS)]
+            assert chosen in (0, 1, 2, 3, 8, 9)
+            with pytest.raises(W.WrlsError):
+                W.wrls_stream_set_blend_config(s.handle, 5)
+        W.wrls_stream_check(s.handle)
+        outs[cfg] = o.cpu()
+        s.close()
+    for cfg in (1, 2, 3, 8, 9):
+        assert torch.equal(outs[cfg], outs[0]), cfg
+
+
 @pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_blend_configs_match_oracle(cfg):
     spec = synth.SceneSpec(197, 53, 5, seed=51, motion="pan", firefly_frac=0.05)
