@@ -207,6 +207,17 @@ void wrls_stream_destroy(wrls_stream* s);
  */
 wrls_status wrls_stream_read_state(wrls_stream* s, float* dst);
 
+/*
+ * Load a per-pixel state (checkpoint / resume, session migration; not in the paper): `src`
+ * (device, caller-owned, same planar layout and plane count as wrls_stream_read_state) becomes
+ * the stream's current state, encoded in its format (the 16-bit formats round beta and z and
+ * store P scaled by its largest diagonal entry, as the update does); the next frame reprojects
+ * from it instead of starting over. Asynchronous on the stream's CUDA stream; `src` may be
+ * reused once that stream has passed this call. A state read from a stream with the same
+ * size and parameters resumes it exactly with the binary32 format.
+ */
+wrls_status wrls_stream_write_state(wrls_stream* s, const float* src);
+
 /* Frames denoised since create. */
 uint64_t wrls_stream_frames(const wrls_stream* s);
 

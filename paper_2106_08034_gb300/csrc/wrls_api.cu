@@ -468,6 +468,7 @@ wrls_status wrls_stream_set_cuda_stream(wrls_stream* s, void* cuda_stream) {
 
 wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const float* variance,
                                const float* features, const float* motion, float* out) {
+  NvtxRange nvtx("wrls_denoise_frame");
   if (!s) { set_error("wrls_denoise_frame: stream is NULL"); return WRLS_ERR_INVALID_ARG; }
   wrls_status st = check_frame(s, radiance, variance, features, motion, out, "wrls_denoise_frame");
   if (st != WRLS_OK) return st;
@@ -506,6 +507,7 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
 static wrls_status sequence_setup(wrls_stream* s, const char* who);
 
 wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, int n) {
+  NvtxRange nvtx("wrls_denoise_sequence");
   if (!s || !frames || n < 1) {
     set_error("wrls_denoise_sequence: NULL stream or frames, or n < 1");
     return WRLS_ERR_INVALID_ARG;
@@ -607,6 +609,7 @@ static wrls_status sequence_setup(wrls_stream* s, const char* who) {
 }
 
 wrls_status wrls_denoise_sequence_host(wrls_stream* s, const wrls_frame_io* frames, int n) {
+  NvtxRange nvtx("wrls_denoise_sequence_host");
   if (!s || !frames || n < 1) {
     set_error("wrls_denoise_sequence_host: NULL stream or frames, or n < 1");
     return WRLS_ERR_INVALID_ARG;
@@ -726,6 +729,7 @@ wrls_status wrls_stream_set_overlap(wrls_stream* s, int blend_ctas_per_sm) {
 
 wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const float* variance,
                                     const float* features, const float* motion, float* out) {
+  NvtxRange nvtx("wrls_denoise_frame_host");
   if (!s || !radiance || !motion || !out) {
     set_error("wrls_denoise_frame_host: stream, radiance, motion and out must be non-NULL");
     return WRLS_ERR_INVALID_ARG;
@@ -809,6 +813,7 @@ void wrls_stream_destroy(wrls_stream* s) {
 }
 
 wrls_status wrls_stream_read_state(wrls_stream* s, float* dst) {
+  NvtxRange nvtx("wrls_stream_read_state");
   if (!s || !dst) { set_error("wrls_stream_read_state: NULL argument"); return WRLS_ERR_INVALID_ARG; }
   if (!aligned4(dst)) { set_error("wrls_stream_read_state: dst must be 4-byte aligned"); return WRLS_ERR_INVALID_ARG; }
   if (!s->has_frame) { set_error("wrls_stream_read_state: no frame denoised yet"); return WRLS_ERR_STATE; }
@@ -817,6 +822,20 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst) {
                     "wrls_stream_read_state: launch");
   else
     WRLS_CHECK_CUDA(launch_read_state(s->state[s->cur], dst, s->cs), "wrls_stream_read_state: launch");
+  return WRLS_OK;
+}
+
+wrls_status wrls_stream_write_state(wrls_stream* s, const float* src) {
+  NvtxRange nvtx("wrls_stream_write_state");
+  if (!s || !src) { set_error("wrls_stream_write_state: NULL argument"); return WRLS_ERR_INVALID_ARG; }
+  if (!aligned4(src)) { set_error("wrls_stream_write_state: src must be 4-byte aligned"); return WRLS_ERR_INVALID_ARG; }
+  if (s->ext)
+    WRLS_CHECK_CUDA(launch_write_state_ext(s->state[s->cur], s->state[s->cur].nplanes, src, s->cs),
+                    "wrls_stream_write_state: launch");
+  else
+    WRLS_CHECK_CUDA(launch_write_state(s->state[s->cur], src, s->cs), "wrls_stream_write_state: launch");
+  s->has_frame = true;
+  s->need_reset = false;
   return WRLS_OK;
 }
 
@@ -843,6 +862,7 @@ wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config) {
 }
 
 wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen) {
+  NvtxRange nvtx("wrls_stream_autotune");
   if (!s || !out || reps < 1) { set_error("wrls_stream_autotune: bad argument"); return WRLS_ERR_INVALID_ARG; }
   if (!s->has_frame) { set_error("wrls_stream_autotune: no frame denoised yet"); return WRLS_ERR_STATE; }
   if (s->ext) {  // one blend configuration on the extended path

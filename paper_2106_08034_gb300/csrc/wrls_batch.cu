@@ -403,6 +403,7 @@ wrls_status wrls_batch_set_cuda_stream(wrls_batch* b, void* cuda_stream) {
 }
 
 wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
+  NvtxRange nvtx("wrls_batch_tick");
   if (!b || !frames) { set_error("wrls_batch_tick: NULL argument"); return WRLS_ERR_INVALID_ARG; }
   if (n < 1 || n > b->max_streams) {
     set_error("wrls_batch_tick: n = %d outside [1, %d]", n, b->max_streams);
@@ -527,6 +528,7 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
 }
 
 wrls_status wrls_denoise_batch(wrls_stream* const* streams, const wrls_frame_io* io, int n) {
+  NvtxRange nvtx("wrls_denoise_batch");
   if (!streams || !io || n < 1 || n > kDenoiseBatchMax) {
     set_error("wrls_denoise_batch: NULL argument or n = %d outside [1, %d]", n, kDenoiseBatchMax);
     return WRLS_ERR_INVALID_ARG;

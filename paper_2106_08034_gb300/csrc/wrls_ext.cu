@@ -377,6 +377,15 @@ __global__ void k_read_state_ext(const int W, const int H, const float* __restri
   for (int p = 0; p < nplanes; ++p) dst[p * npix + j] = src[p * ps];
 }
 
+__global__ void k_write_state_ext(const int W, const int H, float* __restrict__ cur, const int pitch,
+                                  const size_t ps, const int nplanes, const float* __restrict__ src) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W || y >= H) return;
+  const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
+  float* dst = cur + (size_t)y * pitch + x;
+  for (int p = 0; p < nplanes; ++p) dst[p * ps] = src[p * npix + j];
+}
+
 template <int D, bool F>
 static cudaError_t launch_ext_t(const ExtParams& ep, const StateDesc& prev, const StateDesc& next, bool reset,
                                 const float* rad, const float* mot, const float* var, const float* gbuf,
@@ -429,6 +438,12 @@ cudaError_t launch_ext_update(const ExtParams& ep, int d, const StateDesc& prev,
 cudaError_t launch_ext_blend(const ExtParams& ep, int d, const StateDesc& cur, const float* gbuf, float* out,
                              cudaStream_t cs) {
   WRLS_EXT_DISPATCH(launch_ext_blend_t, ep, cur, gbuf, out, cs)
+}
+
+cudaError_t launch_write_state_ext(const StateDesc& cur, int nplanes, const float* src, cudaStream_t cs) {
+  const dim3 grid((cur.W + 127) / 128, cur.H);
+  k_write_state_ext<<<grid, 128, 0, cs>>>(cur.W, cur.H, (float*)cur.base, cur.pitch, cur.plane_stride, nplanes, src);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_read_state_ext(const StateDesc& cur, int nplanes, float* dst, cudaStream_t cs) {

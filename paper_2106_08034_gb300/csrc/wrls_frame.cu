@@ -39,6 +39,18 @@ __global__ void k_read_state(const int W, const int H, const SV cur, float* __re
   for (int p = 0; p < kNState; ++p) dst[p * npix + j] = v[p];
 }
 
+// Inverse of k_read_state: binary32 planes in, the state copy encoded in its format.
+template <class SV>
+__global__ void k_write_state(const int W, const int H, const SV cur, const float* __restrict__ src) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W || y >= H) return;
+  const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
+  float v[kNState];
+#pragma unroll
+  for (int p = 0; p < kNState; ++p) v[p] = src[p * npix + j];
+  cur.store((size_t)y * cur.pitch + x, v);
+}
+
 template <class SV>
 static cudaError_t launch_update_t(const KParams& kp, const StateDesc& prev, const SV& pv, const SV& nx,
                                   bool reset, const float* rad, const float* mot, int* err,
@@ -110,6 +122,17 @@ cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float
     case 2: return launch_blend_sv(kp, cfg, cur.f16(), cur.W, cur.H, out, cs);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_write_state(const StateDesc& cur, const float* src, cudaStream_t cs) {
+  const dim3 grid((cur.W + 127) / 128, cur.H);
+  switch (cur.precision) {
+    case 0: k_write_state<<<grid, 128, 0, cs>>>(cur.W, cur.H, cur.f32(), src); break;
+    case 1: k_write_state<<<grid, 128, 0, cs>>>(cur.W, cur.H, cur.bf16(), src); break;
+    case 2: k_write_state<<<grid, 128, 0, cs>>>(cur.W, cur.H, cur.f16(), src); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs) {

@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/wrls.h"
 #include "wrls_device.cuh"
 
@@ -53,6 +55,7 @@ cudaError_t launch_ext_update(const ExtParams& ep, int d, const StateDesc& prev,
 cudaError_t launch_ext_blend(const ExtParams& ep, int d, const StateDesc& cur, const float* gbuf, float* out,
                              cudaStream_t cs);
 cudaError_t launch_read_state_ext(const StateDesc& cur, int nplanes, float* dst, cudaStream_t cs);
+cudaError_t launch_write_state_ext(const StateDesc& cur, int nplanes, const float* src, cudaStream_t cs);
 
 // Host-side conversion of the public parameters (validated) into kernel parameters.
 bool make_kparams(const wrls_params& p, KParams* kp, const char** why);
@@ -90,6 +93,7 @@ cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& 
 cudaError_t launch_blend_two_wide(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
                                   cudaStream_t cs);
 cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs);
+cudaError_t launch_write_state(const StateDesc& cur, const float* src, cudaStream_t cs);
 // Fused wavefront kernel (update + blend in one persistent launch).
 size_t fused_scratch_bytes(int W, int H);
 // variant 1: blend with 2 rows per thread (all threads), 3 CTAs/SM; 2: 4 rows per thread, 2 CTAs/SM.
@@ -98,6 +102,15 @@ cudaError_t launch_fused(int variant, const KParams& kp, const StateDesc& prev, 
                          int epoch, cudaStream_t cs);
 
 void set_error(const char* fmt, ...);
+
+// NVTX range around an entry point (visible in Nsight timelines; a no-op call when no tool is
+// attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace wrls
 

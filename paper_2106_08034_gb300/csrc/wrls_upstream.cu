@@ -171,6 +171,7 @@ void wrls_recon_params_default(wrls_recon_params* p) {
 
 wrls_status wrls_reconstruct(int width, int height, int spp, const float* samples, const wrls_recon_params* p,
                              float* radiance, float* variance, void* cuda_stream) {
+  NvtxRange nvtx("wrls_reconstruct");
   if (!p || p->struct_size != sizeof(wrls_recon_params)) {
     set_error("wrls_reconstruct: params NULL or struct_size != sizeof(wrls_recon_params)");
     return WRLS_ERR_INVALID_ARG;
@@ -208,6 +209,7 @@ wrls_status wrls_reconstruct(int width, int height, int spp, const float* sample
 
 wrls_status wrls_velocity_from_world(int width, int height, const float* world, const float* prev_view_proj,
                                      int miss_policy, float* motion, void* cuda_stream) {
+  NvtxRange nvtx("wrls_velocity_from_world");
   if (!in_range(width, height) || !world || !prev_view_proj || !motion || miss_policy < 0 || miss_policy > 1) {
     set_error("wrls_velocity_from_world: bad size (%d x %d), NULL pointer or miss_policy %d", width, height,
               miss_policy);

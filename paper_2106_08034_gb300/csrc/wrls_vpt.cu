@@ -255,6 +255,7 @@ extern "C" {
 
 wrls_status wrls_render_vpt(const wrls_vpt_scene* sc, int width, int height, int spp, uint32_t frame,
                             float* samples, float* world, float* features, void* cuda_stream) {
+  NvtxRange nvtx("wrls_render_vpt");
   if (!sc || sc->struct_size != sizeof(wrls_vpt_scene)) {
     set_error("wrls_render_vpt: scene NULL or struct_size != sizeof(wrls_vpt_scene)");
     return WRLS_ERR_INVALID_ARG;

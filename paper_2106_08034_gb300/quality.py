@@ -113,3 +113,67 @@ def vpt_ablation(width: int = 320, height: int = 180, frames: int = 24, spp: int
     torch.cuda.synchronize()
     spec = synth.SceneSpec(width, height, frames, seed=seed)
     return {name: score_sequence(spec, ov, device, skip=skip, frames=ins) for name, ov in VPT_MODES.items()}
+
+
+def edit_recovery(spec: Optional[synth.SceneSpec] = None, device="cuda", window: int = 10,
+                  band: float = 1.5) -> Dict[str, object]:
+    """Output error around a transfer-function edit and a light move, which the paper handles
+    without any reset of the models (Sec. 5.2): relMSE per frame, and per event the mean over
+    the `window` frames before it, the peak in the `window` frames after it, the settled level
+    (mean over frames t0 + window .. t0 + 2 window - 1) and the number of frames until the error
+    is within `band` x the settled level (None if it does not get there within the window)."""
+    import dataclasses
+    if spec is None:
+        spec = dataclasses.replace(synth.orbit_edit_1080p_120f(), width=480, height=272, firefly_frac=0.0)
+    p = W.wrls_params_default()
+    s = W.Stream(spec.width, spec.height, p)
+    sc = synth.Scene(spec)
+    out = torch.empty(3, spec.height, spec.width, device=device)
+    rel = []
+    for t in range(spec.frames):
+        f = sc.frame(t, device=device)
+        truth = f["truth"].to(device)
+        s.denoise(f["radiance"].to(device), f["motion"].to(device), out)
+        rel.append(float(((out - truth) ** 2 / (truth * truth + 1e-2)).mean()))
+    W.wrls_stream_check(s.handle)
+    s.close()
+    events = {}
+    for name, t0 in (("tf_edit", spec.tf_edit_frame), ("light_move", spec.light_move_frame)):
+        if t0 is None or t0 < window or t0 + 2 * window > spec.frames:
+            continue
+        before = sum(rel[t0 - window:t0]) / window
+        settled = sum(rel[t0 + window:t0 + 2 * window]) / window
+        back = next((i for i in range(window) if rel[t0 + i] <= band * settled), None)
+        events[name] = {"frame": t0, "relmse_before": before, "relmse_peak": max(rel[t0:t0 + window]),
+                        "relmse_settled": settled, "frames_to_settle": back}
+    return {"relmse_per_frame": rel, "events": events}
+
+
+def runtime_vs_content(sizes=((960, 540), (1920, 1080)), motions=("static", "pan", "orbit"),
+                       seeds=(5, 6), frames: int = 10, skip: int = 3, device="cuda") -> Dict[str, object]:
+    """GPU time per frame (update + blend kernels, CUDA events of wrls_stream_enable_timing)
+    for sequences of equal size but different content (seeds) and motion, and across sizes:
+    the paper states that the cost depends only on the resolution (Sec. 7)."""
+    res = {}
+    for (w, h) in sizes:
+        per = {}
+        for m in motions:
+            for sd in seeds:
+                spec = synth.SceneSpec(w, h, frames, seed=sd, motion=m, firefly_frac=0.05)
+                sc = synth.Scene(spec)
+                fr = [sc.frame(t, device=device) for t in range(frames)]
+                s = W.Stream(w, h, W.wrls_params_default())
+                out = torch.empty(3, h, w, device=device)
+                for t in range(skip):
+                    s.denoise(fr[t]["radiance"], fr[t]["motion"], out)
+                W.wrls_stream_enable_timing(s.handle, True)
+                for t in range(skip, frames):
+                    s.denoise(fr[t]["radiance"], fr[t]["motion"], out)
+                u, b, n = W.wrls_stream_kernel_times(s.handle)
+                W.wrls_stream_check(s.handle)
+                s.close()
+                per["%s/%d" % (m, sd)] = (u + b) / n * 1e3
+        ts = list(per.values())
+        res["%dx%d" % (w, h)] = {"us_per_frame": per, "spread": max(ts) / min(ts),
+                                 "ns_per_px": sum(ts) / len(ts) * 1e3 / (w * h)}
+    return res

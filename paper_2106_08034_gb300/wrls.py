@@ -34,7 +34,7 @@ N_STATE = 25
 EXPORTED = [
     "wrls_params_default", "wrls_state_bytes", "wrls_stream_create", "wrls_stream_set_cuda_stream",
     "wrls_denoise_frame", "wrls_denoise_frame_host", "wrls_stream_reset", "wrls_stream_destroy",
-    "wrls_stream_read_state", "wrls_stream_frames", "wrls_last_error",
+    "wrls_stream_read_state", "wrls_stream_write_state", "wrls_stream_frames", "wrls_last_error",
     "wrls_stream_enable_timing", "wrls_stream_kernel_times", "wrls_stream_check",
     "wrls_stream_autotune", "wrls_stream_set_blend_config", "wrls_stream_set_pipeline",
     "wrls_stream_set_debug",
@@ -119,6 +119,7 @@ def lib():
         "wrls_stream_reset": (i, [vp]),
         "wrls_stream_destroy": (None, [vp]),
         "wrls_stream_read_state": (i, [vp, vp]),
+        "wrls_stream_write_state": (i, [vp, vp]),
         "wrls_stream_frames": (ctypes.c_uint64, [vp]),
         "wrls_last_error": (ctypes.c_char_p, []),
         "wrls_stream_enable_timing": (i, [vp, i]),
@@ -277,6 +278,10 @@ def wrls_stream_read_state(stream: int, dst) -> None:
     _check(lib().wrls_stream_read_state(stream, _ptr(dst)))
 
 
+def wrls_stream_write_state(stream: int, src) -> None:
+    _check(lib().wrls_stream_write_state(stream, _ptr(src)))
+
+
 def wrls_stream_frames(stream: int) -> int:
     return int(lib().wrls_stream_frames(stream))
 
@@ -400,6 +405,9 @@ class Stream:
 
     def read_state(self, dst) -> None:
         wrls_stream_read_state(self.handle, dst)
+
+    def write_state(self, src) -> None:
+        wrls_stream_write_state(self.handle, src)
 
     @property
     def state_planes(self) -> int:

@@ -108,6 +108,10 @@ def test_input_step_arguments_are_checked_on_the_host(lib):
     assert lib.wrls_velocity_from_world(8, 8, 256, m, 0, 4096, None) == W.WRLS_ERR_INVALID_ARG
 
 
+def test_write_state_arguments_are_checked_on_the_host(lib):
+    assert lib.wrls_stream_write_state(None, None) == W.WRLS_ERR_INVALID_ARG
+
+
 def test_denoise_batch_arguments_are_checked_on_the_host(lib):
     assert lib.wrls_denoise_batch(None, None, 1) == W.WRLS_ERR_INVALID_ARG
     import ctypes

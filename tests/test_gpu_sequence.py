@@ -190,3 +190,41 @@ def test_host_sequence_equals_per_frame_host_calls(kw, chunks):
     s.close()
     for t in range(spec.frames):
         assert torch.equal(got[t], ref[t]), t
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(state_precision=1), dict(n_features=synth.N_FEATURES, n_gbuf=2, weight_mode=2)])
+def test_state_checkpoint_resume(kw):
+    """wrls_stream_read_state of stream A loaded into a fresh stream B with
+    wrls_stream_write_state resumes A: with the binary32 state B's next frames equal A's bit for
+    bit (also on the extended path); with BF16 they agree within the parity tolerance."""
+    spec = synth.SceneSpec(150, 84, 12, seed=67, motion="orbit", firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    p = W.wrls_params_default(**kw)
+    a = W.Stream(spec.width, spec.height, p)
+    b = W.Stream(spec.width, spec.height, p)
+    out = torch.empty(3, spec.height, spec.width, device="cuda")
+    ins = [(f["radiance"].cuda(), f["motion"].cuda(), f["variance"].cuda(), f["features"].cuda()) for f in fr]
+    for t in range(6):
+        a.denoise(ins[t][0], ins[t][1], out, variance=ins[t][2], features=ins[t][3])
+    npl = a.state_planes
+    st = torch.empty(npl, spec.height, spec.width, device="cuda")
+    a.read_state(st)
+    b.write_state(st)
+    st_b = torch.empty_like(st)
+    b.read_state(st_b)
+    if kw.get("state_precision", 0) == 0:
+        assert torch.equal(st_b, st)
+    oa = torch.empty_like(out)
+    ob = torch.empty_like(out)
+    for t in range(6, spec.frames):
+        a.denoise(ins[t][0], ins[t][1], oa, variance=ins[t][2], features=ins[t][3])
+        b.denoise(ins[t][0], ins[t][1], ob, variance=ins[t][2], features=ins[t][3])
+        if kw.get("state_precision", 0) == 0:
+            assert torch.equal(oa, ob), t
+        else:
+            assert rel_err(ob.cpu().numpy(), oa.cpu().numpy()) <= REL_TOL * 10, t
+    W.wrls_stream_check(a.handle)
+    W.wrls_stream_check(b.handle)
+    assert W.lib().wrls_stream_write_state(None, st.data_ptr()) == W.WRLS_ERR_INVALID_ARG
+    a.close()
+    b.close()
