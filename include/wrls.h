@@ -218,6 +218,23 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst);
  */
 wrls_status wrls_stream_write_state(wrls_stream* s, const float* src);
 
+/*
+ * State health (not in the paper): the covariance wind-up that the optional reset guard
+ * p_trace_max bounds, positive definiteness of P and non-finite values, computed from the
+ * current state copy on the stream's CUDA stream; the call waits for the result. trace(P) and
+ * the diagonal are taken over the block the predictor uses (the 1 x 1 block with
+ * feature_mode 1). WRLS_ERR_STATE before the first frame; a small device buffer is allocated
+ * on the first call (WRLS_ERR_OOM if that fails).
+ */
+typedef struct wrls_state_stats {
+    uint64_t frames;        /* frames denoised since create */
+    double p_trace_max;     /* max over pixels of trace(P) */
+    double p_trace_mean;    /* mean over pixels of trace(P) */
+    double p_diag_min;      /* min over pixels of the smallest diagonal entry of P (> 0 for SPD P) */
+    uint64_t nonfinite;     /* state values (beta, P, z) that are NaN or infinite */
+} wrls_state_stats;
+wrls_status wrls_stream_state_stats(wrls_stream* s, wrls_state_stats* out);
+
 /* Frames denoised since create. */
 uint64_t wrls_stream_frames(const wrls_stream* s);
 

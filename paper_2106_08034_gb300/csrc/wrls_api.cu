@@ -181,14 +181,6 @@ bool make_kparams(const wrls_params& p, KParams* kp, const char** why) {
 
 using namespace wrls;
 
-#define WRLS_CHECK_CUDA(call, what)                                                     \
-  do {                                                                                  \
-    cudaError_t e_ = (call);                                                            \
-    if (e_ != cudaSuccess) {                                                            \
-      set_error("%s: %s", what, cudaGetErrorString(e_));                                \
-      return WRLS_ERR_CUDA;                                                             \
-    }                                                                                   \
-  } while (0)
 
 static bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 
@@ -807,6 +799,7 @@ void wrls_stream_destroy(wrls_stream* s) {
   cudaFree(s->mem);
   if (s->mem3) cudaFree(s->mem3);
   if (s->staging) cudaFree(s->staging);
+  if (s->stats) cudaFree(s->stats);
   cudaGetLastError();
   if (prev_dev != s->device) cudaSetDevice(prev_dev);
   delete s;

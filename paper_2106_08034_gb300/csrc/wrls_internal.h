@@ -103,6 +103,16 @@ cudaError_t launch_fused(int variant, const KParams& kp, const StateDesc& prev, 
 
 void set_error(const char* fmt, ...);
 
+// Return WRLS_ERR_CUDA with a message from an entry point when a CUDA call fails.
+#define WRLS_CHECK_CUDA(call, what)                      \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) {                             \
+      set_error("%s: %s", what, cudaGetErrorString(e_)); \
+      return WRLS_ERR_CUDA;                              \
+    }                                                    \
+  } while (0)
+
 // NVTX range around an entry point (visible in Nsight timelines; a no-op call when no tool is
 // attached).
 struct NvtxRange {
@@ -138,6 +148,7 @@ struct wrls_stream {
   int device = 0;
   uint64_t frames = 0;
   float* staging = nullptr;     // device I/O buffers of wrls_denoise_frame_host
+  void* stats = nullptr;        // wrls_stream_state_stats accumulators (allocated on first use)
   // wrls_denoise_sequence_host: a ring of device I/O slots and copy streams
   static constexpr int kHostSlots = 3;
   float* ring = nullptr;        // kHostSlots slots of (radiance, motion, output, variance, G-buffers)

@@ -34,7 +34,7 @@ N_STATE = 25
 EXPORTED = [
     "wrls_params_default", "wrls_state_bytes", "wrls_stream_create", "wrls_stream_set_cuda_stream",
     "wrls_denoise_frame", "wrls_denoise_frame_host", "wrls_stream_reset", "wrls_stream_destroy",
-    "wrls_stream_read_state", "wrls_stream_write_state", "wrls_stream_frames", "wrls_last_error",
+    "wrls_stream_read_state", "wrls_stream_write_state", "wrls_stream_state_stats", "wrls_stream_frames", "wrls_last_error",
     "wrls_stream_enable_timing", "wrls_stream_kernel_times", "wrls_stream_check",
     "wrls_stream_autotune", "wrls_stream_set_blend_config", "wrls_stream_set_pipeline",
     "wrls_stream_set_debug",
@@ -97,6 +97,12 @@ class wrls_frame_io(ctypes.Structure):
                 ("motion", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 
+class wrls_state_stats(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_uint64), ("p_trace_max", ctypes.c_double),
+                ("p_trace_mean", ctypes.c_double), ("p_diag_min", ctypes.c_double),
+                ("nonfinite", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -120,6 +126,7 @@ def lib():
         "wrls_stream_destroy": (None, [vp]),
         "wrls_stream_read_state": (i, [vp, vp]),
         "wrls_stream_write_state": (i, [vp, vp]),
+        "wrls_stream_state_stats": (i, [vp, ctypes.POINTER(wrls_state_stats)]),
         "wrls_stream_frames": (ctypes.c_uint64, [vp]),
         "wrls_last_error": (ctypes.c_char_p, []),
         "wrls_stream_enable_timing": (i, [vp, i]),
@@ -280,6 +287,13 @@ def wrls_stream_read_state(stream: int, dst) -> None:
 
 def wrls_stream_write_state(stream: int, src) -> None:
     _check(lib().wrls_stream_write_state(stream, _ptr(src)))
+
+
+def wrls_stream_state_stats(stream: int) -> dict:
+    """State health: frames, trace(P) max / mean, smallest P diagonal, non-finite values."""
+    st = wrls_state_stats()
+    _check(lib().wrls_stream_state_stats(stream, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in wrls_state_stats._fields_}
 
 
 def wrls_stream_frames(stream: int) -> int:

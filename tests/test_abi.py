@@ -110,6 +110,7 @@ def test_input_step_arguments_are_checked_on_the_host(lib):
 
 def test_write_state_arguments_are_checked_on_the_host(lib):
     assert lib.wrls_stream_write_state(None, None) == W.WRLS_ERR_INVALID_ARG
+    assert lib.wrls_stream_state_stats(None, None) == W.WRLS_ERR_INVALID_ARG
 
 
 def test_denoise_batch_arguments_are_checked_on_the_host(lib):

@@ -228,3 +228,44 @@ def test_state_checkpoint_resume(kw):
     assert W.lib().wrls_stream_write_state(None, st.data_ptr()) == W.WRLS_ERR_INVALID_ARG
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(state_precision=1), dict(feature_mode=1),
+                                dict(n_features=synth.N_FEATURES, n_gbuf=2, weight_mode=2),
+                                dict(p_trace_max=3.0)])
+def test_state_stats_match_the_state(kw):
+    """wrls_stream_state_stats agrees with the state read back: trace(P) max and mean and the
+    smallest diagonal over the used block, no non-finite values; with the reset guard on,
+    trace(P) never exceeds max(p_trace_max, trace(P0))."""
+    spec = synth.SceneSpec(141, 77, 9, seed=68, motion="orbit", firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    p = W.wrls_params_default(**kw)
+    s = W.Stream(spec.width, spec.height, p)
+    with pytest.raises(W.WrlsError):
+        W.wrls_stream_state_stats(s.handle)          # no frame yet
+    out = torch.empty(3, spec.height, spec.width, device="cuda")
+    for f in fr:
+        s.denoise(f["radiance"].cuda(), f["motion"].cuda(), out, variance=f["variance"].cuda(),
+                  features=f["features"].cuda())
+    st = W.wrls_stream_state_stats(s.handle)
+    planes = torch.empty(s.state_planes, spec.height, spec.width, device="cuda")
+    s.read_state(planes)
+    pl = planes.double().cpu()
+    if "n_gbuf" in kw:
+        d = int(round((-7 + (49 + 8 * (s.state_planes - 3)) ** 0.5) / 2))  # 3d + d(d+1)/2 + 3 planes
+        idx, e = [], 3 * d
+        for a in range(d):
+            idx.append(e)
+            e += d - a
+    else:
+        idx = [12] if kw.get("feature_mode", 0) == 1 else [12, 16, 19, 21]
+    diag = pl[idx]
+    tr = diag.sum(0)
+    assert st["frames"] == spec.frames and st["nonfinite"] == 0
+    assert st["p_trace_max"] == pytest.approx(float(tr.max()), rel=1e-5)
+    assert st["p_trace_mean"] == pytest.approx(float(tr.mean()), rel=1e-5)
+    assert st["p_diag_min"] == pytest.approx(float(diag.min()), rel=1e-5) and st["p_diag_min"] > 0
+    if "p_trace_max" in kw:
+        assert st["p_trace_max"] <= max(kw["p_trace_max"], 4 * p.p0_delta) * (1 + 1e-6)
+    W.wrls_stream_check(s.handle)
+    s.close()
