@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "denoised Mpix/s plain FP32 vs batched BF16-state at stated err; p99 frame latency"
 BYTES_UPDATE_F32 = 220   # per pixel: state read 100 + radiance 12 + motion 8 + state write 100
 BYTES_PATH_F32 = 232     # per pixel and frame for the whole path: + out 12
+BYTES_UPDATE_16 = 128    # 16-bit state: state read 54 (25 x 2 + P scale 4) + 20 + state write 54
+BYTES_PATH_16 = 140      # + out 12
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_update launch on a
 # 1920x1080 frame, from the ncu capture summarised in profiles/k_update_pan_1080p.md (same
 # kernel build). Writes still held in L2 when the kernel ends are not counted by ncu.
@@ -65,6 +67,8 @@ def parse():
                     help="time only the sequence entry (with --pipeline, default 0, and --overlap)")
     ap.add_argument("--overlap", type=int, default=1, help="blend CTAs per SM with --seq")
     ap.add_argument("--no-seq", action="store_true", help="do not try the sequence entry")
+    ap.add_argument("--state", default="f32", choices=["f32", "bf16", "f16"],
+                    help="state format of the main leg (the headline workload is f32; the others for profiling)")
     ap.add_argument("--blend-config", type=int, default=-1,
                     help="use this blend tile configuration instead of autotuning (profiling captures)")
     return ap.parse_args()
@@ -563,8 +567,11 @@ def run_wrls(args):
     torch.cuda.synchronize()
 
     cs = torch.cuda.Stream(device=dev)
-    p = W.wrls_params_default()
+    prec = {"f32": 0, "bf16": 1, "f16": 2}[args.state]
+    p = W.wrls_params_default(state_precision=prec)
     s = W.Stream(Wd, Hd, p, cuda_stream=cs)
+    bytes_update = BYTES_UPDATE_F32 if prec == 0 else BYTES_UPDATE_16
+    bytes_path = BYTES_PATH_F32 if prec == 0 else BYTES_PATH_16
     out = torch.empty(3, Hd, Wd, device=dev)
 
     outs = [out] + [torch.empty(3, Hd, Wd, device=dev) for _ in range(2)]
@@ -704,13 +711,13 @@ def run_wrls(args):
     if best_pipeline in (0, 3):
         kname = ("k_update" if best_pipeline == 0 else "k_update_pipe") + \
             " (reproject + Eq. 12-14 update; the blend is a separate kernel)"
-        kbytes = BYTES_UPDATE_F32
-        if best_pipeline == 0 and (Wd, Hd) == (1920, 1080):
+        kbytes = bytes_update
+        if best_pipeline == 0 and (Wd, Hd) == (1920, 1080) and prec == 0:
             traffic = TRAFFIC_PER_LAUNCH["k_update"]
         if mode["seq"]:
             kname += "; timed while overlapping the previous frame's blend"
     else:
-        kname, kbytes = "k_fused (reproject + Eq. 12-14 update + 5x5 blend, one launch)", BYTES_PATH_F32
+        kname, kbytes = "k_fused (reproject + Eq. 12-14 update + 5x5 blend, one launch)", bytes_path
     achieved = kbytes * px / (upd_per / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -722,9 +729,9 @@ def run_wrls(args):
                 "pipeline": best_pipeline, "entry": "wrls_denoise_sequence" if mode["seq"] else "wrls_denoise_frame",
                 "pipeline_ms_per_frame": {str(k): round(v, 5) for k, v in pipe_ms.items()},
                 "blend_autotune_ms": [round(t, 5) for t in blend_times], "blend_config": blend_cfg,
-                "path": {"bytes_per_px": BYTES_PATH_F32,
-                         "achieved": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9, 1),
-                         "frac": round(BYTES_PATH_F32 * px * frames_total / world / (ms / 1e3) / 1e9 / peak, 4)}}
+                "path": {"bytes_per_px": bytes_path,
+                         "achieved": round(bytes_path * px * frames_total / world / (ms / 1e3) / 1e9, 1),
+                         "frac": round(bytes_path * px * frames_total / world / (ms / 1e3) / 1e9 / peak, 4)}}
 
     batched = None
     if not args.no_batched:
@@ -766,7 +773,7 @@ def run_wrls(args):
             "data": "synthetic",
             "config": {"workload": "pan_1080p_120f: 1920x1080, 120 frames, pan 1.7 px/frame, "
                                    "log-normal noise, 5% x50 fireflies",
-                       "step": "one pass over the 120 frames", "state": "f32",
+                       "step": "one pass over the 120 frames", "state": args.state,
                        "l2": "inputs larger than L2: state ping-pong 2 x 207 MB per frame",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
