@@ -41,6 +41,12 @@ def oracle_params_from(p):
                           blend_mode=p.blend_mode, feature_mode=p.feature_mode, init_mode=p.init_mode)
 
 
+def ext_params_from(p):
+    """OracleExtParams with the same settings as a wrls_params struct (extended path)."""
+    base = oracle_params_from(p)
+    return O.OracleExtParams(**{**base.__dict__, "n_gbuf": p.n_gbuf, "reproj_filter": p.reproj_filter})
+
+
 def cpu_frames(spec, count=None):
     sc = synth.Scene(spec)
     T = spec.frames if count is None else count

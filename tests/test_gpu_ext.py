@@ -10,7 +10,7 @@ import oracle as O
 from paper_2106_08034_gb300 import synth
 from paper_2106_08034_gb300 import wrls as W
 
-from helpers import REL_TOL, cpu_frames, oracle_params_from, rel_err
+from helpers import REL_TOL, cpu_frames, ext_params_from, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -21,11 +21,6 @@ def _built():
     B.build()
     assert torch.cuda.is_available(), "these tests need a CUDA GPU"
     W.lib()
-
-
-def ext_params_from(p):
-    base = oracle_params_from(p)
-    return O.OracleExtParams(**{**base.__dict__, "n_gbuf": p.n_gbuf, "reproj_filter": p.reproj_filter})
 
 
 def params(**kw):

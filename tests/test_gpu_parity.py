@@ -10,7 +10,7 @@ import oracle as O
 from paper_2106_08034_gb300 import synth
 from paper_2106_08034_gb300 import wrls as W
 
-from helpers import FLOOR, REL_TOL, cpu_frames, oracle_params_from, oracle_z_planes, rel_err, relmse
+from helpers import FLOOR, REL_TOL, cpu_frames, ext_params_from, oracle_params_from, oracle_z_planes, rel_err, relmse
 
 pytestmark = pytest.mark.gpu
 
@@ -86,6 +86,79 @@ def test_degenerate_sizes(wh):
     w, h = wh
     spec = synth.SceneSpec(w, h, 6, seed=34, motion="orbit", firefly_frac=0.1)
     run_pair(cpu_frames(spec), w, h)
+
+
+@pytest.mark.parametrize("wh", [(72, 20), (75, 21), (130, 27), (200, 20)])
+def test_two_wide_blend_at_its_smallest_sizes(wh):
+    """Blend configurations 8 and 9 where their TMA boxes (72 or 80 columns x 12 or 20 rows)
+    cover most or all of the image: binary32 against the oracle every frame; BF16 and FP16
+    bitwise equal to the one-CTA-per-tile blend."""
+    w, h = wh
+    spec = synth.SceneSpec(w, h, 6, seed=35, motion="orbit", firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    for cfg in (8, 9):
+        s = W.Stream(w, h)
+        W.wrls_stream_set_blend_config(s.handle, cfg)
+        st = O.OracleStream(w, h, oracle_params_from(W.wrls_params_default()))
+        out = torch.empty(3, h, w, device="cuda")
+        for f in fr:
+            s.denoise(f["radiance"].cuda(), f["motion"].cuda(), out)
+            ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
+            assert rel_err(out.cpu().numpy(), ref) <= REL_TOL, cfg
+        W.wrls_stream_check(s.handle)
+        s.close()
+    for prec in (1, 2):
+        outs = []
+        for cfg in (0, 8, 9):
+            s = W.Stream(w, h, W.wrls_params_default(state_precision=prec))
+            W.wrls_stream_set_blend_config(s.handle, cfg)
+            out = torch.empty(3, h, w, device="cuda")
+            for f in fr:
+                s.denoise(f["radiance"].cuda(), f["motion"].cuda(), out)
+            W.wrls_stream_check(s.handle)
+            outs.append(out.cpu())
+            s.close()
+        assert torch.equal(outs[1], outs[0]) and torch.equal(outs[2], outs[0]), prec
+
+
+@pytest.mark.parametrize("wh", [(1, 1), (1, 37), (41, 1), (33, 9)])
+def test_degenerate_sizes_sequence_and_extended(wh):
+    """The sequence entry (three state copies, blend on a second CUDA stream) and the extended
+    path on degenerate images: sequence bitwise equal to per-frame calls, both at parity with
+    the oracle."""
+    w, h = wh
+    spec = synth.SceneSpec(w, h, 6, seed=36, motion="orbit", firefly_frac=0.1)
+    fr = cpu_frames(spec)
+    p = W.wrls_params_default()
+    ref = run_pair(fr, w, h, p)
+    assert max(ref) <= REL_TOL
+    per = []
+    s = W.Stream(w, h, p)
+    for f in fr:
+        o = torch.empty(3, h, w, device="cuda")
+        s.denoise(f["radiance"].cuda(), f["motion"].cuda(), o)
+        per.append(o)
+    W.wrls_stream_check(s.handle)
+    s.close()
+    s = W.Stream(w, h, p)
+    seq = [torch.empty(3, h, w, device="cuda") for _ in fr]
+    W.wrls_denoise_sequence(s.handle, [(f["radiance"].cuda(), None, None, f["motion"].cuda(), seq[t])
+                                       for t, f in enumerate(fr)])
+    W.wrls_stream_check(s.handle)
+    s.close()
+    for a, b in zip(per, seq):
+        assert torch.equal(a, b)
+    pe = W.wrls_params_default(n_features=synth.N_FEATURES, n_gbuf=3)
+    se = W.Stream(w, h, pe)
+    ost = O.OracleExtStream(w, h, ext_params_from(pe))
+    out = torch.empty(3, h, w, device="cuda")
+    for f in fr:
+        se.denoise(f["radiance"].cuda(), f["motion"].cuda(), out, variance=f["variance"].cuda(),
+                   features=f["features"].cuda())
+        r = ost.frame(f["radiance"].numpy(), f["motion"].numpy(), f["variance"].numpy(), f["features"].numpy())
+        assert rel_err(out.cpu().numpy(), r[0]) <= REL_TOL
+    W.wrls_stream_check(se.handle)
+    se.close()
 
 
 @pytest.mark.parametrize("pipeline", [0, 3])
