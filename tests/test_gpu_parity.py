@@ -88,6 +88,47 @@ def test_degenerate_sizes(wh):
     run_pair(cpu_frames(spec), w, h)
 
 
+@pytest.mark.parametrize("wh", [(16384, 24), (24, 16384)])
+def test_maximum_dimensions(wh):
+    """The largest width and height the stream accepts (16384), every pixel of 3 frames
+    against the oracle."""
+    w, h = wh
+    spec = synth.SceneSpec(w, h, 3, seed=37, motion="orbit", firefly_frac=0.05)
+    run_pair(cpu_frames(spec), w, h, check_z=False)
+
+
+def test_large_frame_sampled_crops():
+    """8192 x 8192 (67 Mpx, 13.4 GB of binary32 state in two copies), static camera, 3 frames:
+    sampled crops (corners, edges, centre) equal the oracle run on the crop plus a 3-pixel
+    margin; with zero motion a pixel's output depends only on its 7 x 7 neighbourhood (3 x 3
+    clamp box of each of the 5 x 5 blended models)."""
+    w = h = 8192
+    spec = synth.SceneSpec(w, h, 3, seed=38, motion="static", firefly_frac=0.05)
+    sc = synth.Scene(spec)
+    s = W.Stream(w, h)
+    out = torch.empty(3, h, w, device="cuda")
+    c, m = 40, 3
+    corners = [(0, 0), (w - c, 0), (0, h - c), (w - c, h - c), (w // 2 - 17, h // 2 + 5), (w // 3, 0), (0, h // 3)]
+    crops = []
+    for (x0, y0) in corners:
+        ax0, ay0 = max(x0 - m, 0), max(y0 - m, 0)
+        ax1, ay1 = min(x0 + c + m, w), min(y0 + c + m, h)
+        crops.append((x0, y0, ax0, ay0, ax1, ay1, O.OracleStream(ax1 - ax0, ay1 - ay0)))
+    for t in range(spec.frames):
+        f = sc.frame(t, device="cuda")
+        s.denoise(f["radiance"], f["motion"], out)
+        rad = f["radiance"]
+        for (x0, y0, ax0, ay0, ax1, ay1, st) in crops:
+            r = rad[:, ay0:ay1, ax0:ax1].cpu().numpy()
+            ref, _, _ = st.frame(r, np.zeros((2,) + r.shape[1:], np.float32))
+            got = out[:, y0:y0 + c, x0:x0 + c].cpu().numpy()
+            exp = ref[:, y0 - ay0:y0 - ay0 + c, x0 - ax0:x0 - ax0 + c]
+            assert rel_err(got, exp) <= REL_TOL, (t, x0, y0)
+        del f, rad
+    W.wrls_stream_check(s.handle)
+    s.close()
+
+
 @pytest.mark.parametrize("wh", [(72, 20), (75, 21), (130, 27), (200, 20)])
 def test_two_wide_blend_at_its_smallest_sizes(wh):
     """Blend configurations 8 and 9 where their TMA boxes (72 or 80 columns x 12 or 20 rows)
