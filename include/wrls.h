@@ -356,8 +356,12 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n);
 void wrls_batch_destroy(wrls_batch* b);
 
 /*
- * One batched tick without an executor object: frame io[i] of stream streams[i] (io[i].stream
- * may be NULL or must equal streams[i]), 1 <= n <= 256, with the rules of wrls_batch_tick.
+ * One batched tick without an executor object (the per-frame computation of Sec. 5.3 for the
+ * frames of many streams; batching itself is not in the paper): frame io[i] of stream
+ * streams[i] (io[i].stream may be NULL or must equal streams[i]), 1 <= n <= 256, with the
+ * rules of wrls_batch_tick. Errors: WRLS_ERR_INVALID_ARG for a NULL or mismatched stream, a
+ * repeated stream or n outside [1, 256] (nothing is launched), WRLS_ERR_OOM / WRLS_ERR_CUDA
+ * from creating the executor or launching.
  * The library keeps one executor per device, created on the first call on that device
  * (allocation as in wrls_batch_create) and kept until the process exits; calls are
  * serialised by a lock. The tick runs on streams[0]'s CUDA stream. Asynchronous.
