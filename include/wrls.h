@@ -103,7 +103,7 @@ typedef struct wrls_params {
 typedef struct wrls_stream wrls_stream;
 struct wrls_frame_io; /* one frame's buffers, defined with the batched tick below */
 
-/* Fill *p with the defaults above. */
+/* Fill *p with the defaults above (the paper's constants where it gives them: Sec. 6). */
 void wrls_params_default(wrls_params* p);
 
 /* Device bytes a stream of w x h pixels holds for its state (two copies: the
@@ -111,13 +111,15 @@ void wrls_params_default(wrls_params* p);
  * Used for admission by device memory. */
 size_t wrls_state_bytes(int width, int height, const wrls_params* p);
 
-/* Create a stream for w x h frames (1 <= w, h <= 16384). Allocates the state with
+/* Create a stream for w x h frames (1 <= w, h <= 16384). Allocates the per-pixel state of
+ * Sec. 5.3 (beta of Eq. 5, P of Eq. 10-11, z of Eq. 12; two copies, the history buffer) with
  * cudaMalloc on the current device (WRLS_ERR_OOM on failure). The first frame after
  * create (or after wrls_stream_reset) restarts every pixel. On success *out owns the
  * stream; release it with wrls_stream_destroy. */
 wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls_stream** out);
 
-/* Set the CUDA stream (a cudaStream_t passed as void*) that later calls enqueue on.
+/* Set the CUDA stream (a cudaStream_t passed as void*) that later calls enqueue on (not in
+ * the paper).
  * NULL selects the legacy default stream (the default after create). */
 wrls_status wrls_stream_set_cuda_stream(wrls_stream* s, void* cuda_stream);
 
@@ -141,7 +143,7 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
                                const float* features, const float* motion, float* out);
 
 /*
- * Same as wrls_denoise_frame with HOST buffers (pinned memory gives asynchronous copies):
+ * Same as wrls_denoise_frame (Sec. 5.3) with HOST buffers (pinned memory gives asynchronous copies):
  * copies radiance and motion to device buffers the stream owns (allocated on the first
  * call and kept until destroy), denoises, and copies the result back to `out`. Returns
  * after enqueuing; `out` is valid once the stream's CUDA stream is synchronised.
@@ -152,8 +154,10 @@ wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const
                                     const float* features, const float* motion, float* out);
 
 /*
- * Denoise n consecutive frames of one stream in one call, for callers that hold several
- * frames at once (offline denoising of a recorded sequence, throughput runs). Results are
+ * Denoise n consecutive frames of one stream in one call (the per-frame computation of
+ * Sec. 5.3; running the blend of one frame beside the update of the next is not in the
+ * paper), for callers that hold several frames at once (offline denoising of a recorded
+ * sequence, throughput runs). Results are
  * those of n calls of wrls_denoise_frame. The frames' updates run in order on the stream's
  * CUDA stream; the blend of frame t runs on a second CUDA stream that the library creates
  * on the first call, so it overlaps the update of frame t+1 (both read the state of frame t).
@@ -172,7 +176,8 @@ wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const
 wrls_status wrls_denoise_sequence(wrls_stream* s, const struct wrls_frame_io* frames, int n);
 
 /*
- * wrls_denoise_sequence with HOST buffers (pinned memory gives asynchronous copies): for
+ * wrls_denoise_sequence (Sec. 5.3 per frame) with HOST buffers (pinned memory gives
+ * asynchronous copies): for
  * each frame the inputs (radiance, motion; variance and G-buffer planes when the parameters
  * use them) are copied to one of three device slots on a copy stream, the frame is denoised
  * as by wrls_denoise_sequence, and the output is copied back on a second copy stream, so
@@ -187,20 +192,22 @@ wrls_status wrls_denoise_sequence(wrls_stream* s, const struct wrls_frame_io* fr
  */
 wrls_status wrls_denoise_sequence_host(wrls_stream* s, const struct wrls_frame_io* frames, int n);
 
-/* CTAs per SM of the persistent blend kernels (blend configurations 4-9) when they overlap
- * an update in wrls_denoise_sequence: fewer leave the update room on every SM. 0 = as many
+/* Not in the paper: CTAs per SM of the persistent blend kernels (blend configurations 4-9)
+ * when they overlap an update in wrls_denoise_sequence: fewer leave the update room on every SM. 0 = as many
  * as fit; default 2 (measured at 1080p with configuration 9: 126 us per frame with 2, 3 or
  * no cap, 206 us with 1). */
 wrls_status wrls_stream_set_overlap(wrls_stream* s, int blend_ctas_per_sm);
 
-/* The next frame restarts every pixel (frame-0 behaviour). */
+/* The next frame restarts every pixel (frame-0 behaviour: beta and P at their initial
+ * values, z from the sample; the paper restarts a pixel only on disocclusion, Sec. 5.3). */
 wrls_status wrls_stream_reset(wrls_stream* s);
 
 /* Synchronise the stream's pending work and free it. NULL is a no-op. */
 void wrls_stream_destroy(wrls_stream* s);
 
 /*
- * Copy the current per-pixel state, decoded to binary32, into `dst` (device,
+ * Copy the current per-pixel state of Sec. 5.3 (beta Eq. 5, P Eq. 10-11, z Eq. 12), decoded
+ * to binary32, into `dst` (device,
  * 25 x H x W planar): planes 0-11 beta[c][a] (channel c, coefficient a, plane c*4+a),
  * planes 12-21 the upper triangle of P row by row (00,01,02,03,11,12,13,22,23,33),
  * planes 22-24 z. Streams on the extended path write 3d + d(d+1)/2 + 3 planes in the
@@ -236,11 +243,11 @@ typedef struct wrls_state_stats {
 } wrls_state_stats;
 wrls_status wrls_stream_state_stats(wrls_stream* s, wrls_state_stats* out);
 
-/* Frames denoised since create. */
+/* Frames denoised since create (0 for NULL). */
 uint64_t wrls_stream_frames(const wrls_stream* s);
 
 /*
- * Autotuner of the blend kernel's tile shape (two-kernel pipeline): times every blend tile
+ * Autotuner of the blend kernel's tile shape (two-kernel pipeline; not in the paper): times every blend tile
  * configuration on the
  * stream's current state, `reps` launches each (>= 1), on the stream's CUDA stream, and
  * keeps the fastest for later frames. Configurations (output tile rows x output rows per
@@ -265,7 +272,8 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
 wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen);
 
 /*
- * Choose how wrls_denoise_frame runs a frame. 0 (default after create): an update kernel
+ * Choose how wrls_denoise_frame runs a frame (kernel organisation, not in the paper; every
+ * choice computes Sec. 5.3 with bitwise identical results). 0 (default after create): an update kernel
  * followed by a blend kernel (blend tile chosen by wrls_stream_set_blend_config /
  * wrls_stream_autotune). 1 or 2: one persistent
  * "wavefront" kernel that claims 32 x 8 update tiles in raster order and, a few tiles behind,
@@ -281,12 +289,13 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
  */
 wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused);
 
-/* Select a blend tile configuration (0..WRLS_BLEND_CONFIGS-1) directly; configurations
+/* Select a blend tile configuration (0..WRLS_BLEND_CONFIGS-1; kernel tiling, not in the
+ * paper) directly; configurations
  * 4-7 need the binary32 state (WRLS_ERR_INVALID_ARG otherwise). */
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config);
 
 /*
- * Test hook for the failure path of the bounded device-side waits. With
+ * Test hook for the failure path of the bounded device-side waits (not in the paper). With
  * WRLS_DEBUG_WITHHOLD_STAGE_COPY set, the update kernel of the two-kernel pipeline arms the
  * mbarrier of each tile's state-window copy but does not issue the copy, so the tile's
  * bounded wait runs out (about one second of SM clocks); the kernel then records
@@ -296,13 +305,13 @@ wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config);
 #define WRLS_DEBUG_WITHHOLD_STAGE_COPY 1u
 wrls_status wrls_stream_set_debug(wrls_stream* s, uint32_t flags);
 
-/* Synchronise the stream's CUDA stream and report device-side failures of the frames
+/* Not in the paper: synchronise the stream's CUDA stream and report device-side failures of the frames
  * since the last check: WRLS_ERR_TIMEOUT if a kernel's bounded wait for its own bulk
  * copy gave up (that frame's output and state are then unreliable). Clears the record. */
 wrls_status wrls_stream_check(wrls_stream* s);
 
 /*
- * Kernel tracing. With timing enabled, every frame records CUDA events on the stream's
+ * Kernel tracing (not in the paper). With timing enabled, every frame records CUDA events on the stream's
  * CUDA stream before and after each of its kernels (temporal update, spatial blend).
  * wrls_stream_kernel_times synchronises the recorded events, adds their durations to
  * *update_ms and *blend_ms (milliseconds, summed over frames), sets *frames to the number
@@ -340,7 +349,9 @@ typedef struct wrls_frame_io {
 
 typedef struct wrls_batch wrls_batch;
 
-/* Create a batch executor for up to max_streams frames per tick. */
+/* Create a batch executor for up to max_streams frames per tick (batching is not in the
+ * paper; each frame is the computation of Sec. 5.3). WRLS_ERR_INVALID_ARG outside
+ * [1, 4096], WRLS_ERR_OOM / WRLS_ERR_CUDA if its buffers, streams or events fail. */
 wrls_status wrls_batch_create(int max_streams, wrls_batch** out);
 
 /* Set the CUDA stream (cudaStream_t as void*) ticks run on; NULL = legacy default. */
