@@ -103,7 +103,8 @@ typedef struct wrls_params {
 typedef struct wrls_stream wrls_stream;
 struct wrls_frame_io; /* one frame's buffers, defined with the batched tick below */
 
-/* Fill *p with the defaults above (the paper's constants where it gives them: Sec. 6). */
+/* Fill *p with the defaults above (the paper's constants where it gives them: lambda, h,
+ * alpha and the 5x5 window of Sec. 5.2-6). */
 void wrls_params_default(wrls_params* p);
 
 /* Device bytes a stream of w x h pixels holds for its state (two copies: the
