@@ -273,8 +273,6 @@ static wrls_status enqueue_update(wrls_stream* s, const float* radiance, const f
     e = launch_ext_update(s->ep, s->dim, prev, next, s->need_reset, radiance, motion,
                           s->prm.weight_mode == 2 ? variance : nullptr, s->prm.n_gbuf > 0 ? features : nullptr,
                           s->cs);
-  else if (s->pipeline == 3)
-    e = launch_update_pipelined(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs);
   else
     e = launch_update(s->kp, prev, next, s->need_reset, radiance, motion, s->err, s->cs);
   if (e != cudaSuccess) {
@@ -401,9 +399,8 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
   s->ep.reproj_filter = p->reproj_filter;
   s->ep.wv_k = (float)(3.0 * 1.4426950408889634 / ((double)p->h * (double)p->h));
   cudaGetDevice(&s->device);
-  // both state copies, then the error word (+0), the fused kernel's counters (+64) and tile
-  // flags (+256)
-  const size_t scratch = fused_scratch_bytes(width, height);
+  // both state copies, then the device error word
+  const size_t scratch = 256;
   cudaError_t e = cudaMalloc(&s->mem, 2 * copy + scratch);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -413,8 +410,6 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
   }
   s->mem_bytes = 2 * copy + scratch;
   s->err = (int*)((char*)s->mem + 2 * copy);
-  s->work = (int*)((char*)s->mem + 2 * copy + 64);
-  s->flags = (int*)((char*)s->mem + 2 * copy + 256);
   e = cudaMemset(s->err, 0, scratch);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -468,26 +463,14 @@ wrls_status wrls_denoise_frame(wrls_stream* s, const float* radiance, const floa
   st = timing_slot(s, &ev);
   if (st != WRLS_OK) return st;
   if (ev) WRLS_CHECK_CUDA(cudaEventRecord(ev[0], s->cs), "wrls_denoise_frame: event record");
-  if (!s->ext && (s->pipeline == 1 || s->pipeline == 2)) {
-    const StateDesc& prev = s->state[s->cur];
-    const StateDesc& next = s->state[next_copy(s)];
-    WRLS_CHECK_CUDA(launch_fused(s->pipeline, s->kp, prev, next, s->need_reset, radiance, motion, out, s->err, s->work,
-                                 s->flags, (int)((s->frames + 1) & 0x7fffffff), s->cs),
-                    "wrls_denoise_frame: fused kernel launch");
-    if (ev) {
-      WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
-      WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
-    }
-  } else {
-    st = enqueue_update(s, radiance, variance, features, motion, "wrls_denoise_frame");
-    if (st != WRLS_OK) return st;
-    if (ev) {
-      WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
-      WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
-    }
-    st = enqueue_blend(s, s->kp, features, out, s->cs, "wrls_denoise_frame");
-    if (st != WRLS_OK) return st;
+  st = enqueue_update(s, radiance, variance, features, motion, "wrls_denoise_frame");
+  if (st != WRLS_OK) return st;
+  if (ev) {
+    WRLS_CHECK_CUDA(cudaEventRecord(ev[1], s->cs), "wrls_denoise_frame: event record");
+    WRLS_CHECK_CUDA(cudaEventRecord(ev[2], s->cs), "wrls_denoise_frame: event record");
   }
+  st = enqueue_blend(s, s->kp, features, out, s->cs, "wrls_denoise_frame");
+  if (st != WRLS_OK) return st;
   if (ev) {
     WRLS_CHECK_CUDA(cudaEventRecord(ev[3], s->cs), "wrls_denoise_frame: event record");
     s->t_pending++;
@@ -525,8 +508,7 @@ wrls_status wrls_denoise_sequence(wrls_stream* s, const wrls_frame_io* frames, i
       }
     }
   }
-  const bool overlap = s->ext || s->pipeline == 0 || s->pipeline == 3;
-  if (!overlap || n == 1) {
+  if (n == 1) {
     for (int i = 0; i < n; ++i) {
       const wrls_frame_io& f = frames[i];
       wrls_status st = wrls_denoise_frame(s, f.radiance, f.variance, f.features, f.motion, f.out);
@@ -614,14 +596,6 @@ wrls_status wrls_denoise_sequence_host(wrls_stream* s, const wrls_frame_io* fram
       set_error("wrls_denoise_sequence_host: frame %d names another stream or lacks a required buffer", i);
       return WRLS_ERR_INVALID_ARG;
     }
-  }
-  if (!s->ext && (s->pipeline == 1 || s->pipeline == 2)) {  // fused pipelines: one frame at a time
-    for (int i = 0; i < n; ++i) {
-      const wrls_frame_io& f = frames[i];
-      wrls_status st = wrls_denoise_frame_host(s, f.radiance, f.variance, f.features, f.motion, f.out);
-      if (st != WRLS_OK) return st;
-    }
-    return WRLS_OK;
   }
   wrls_status st = sequence_setup(s, "wrls_denoise_sequence_host");
   if (st != WRLS_OK) return st;
@@ -833,16 +807,6 @@ wrls_status wrls_stream_write_state(wrls_stream* s, const float* src) {
 }
 
 uint64_t wrls_stream_frames(const wrls_stream* s) { return s ? s->frames : 0; }
-
-wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused) {
-  if (!s || fused < 0 || fused > 3 || (s->ext && fused != 0)) {
-    set_error("wrls_stream_set_pipeline: bad stream or value %d (0, 3 = two kernels, 1, 2 = fused; "
-              "extended path: 0 only)", fused);
-    return WRLS_ERR_INVALID_ARG;
-  }
-  s->pipeline = fused;
-  return WRLS_OK;
-}
 
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config) {
   if (!s || !blend_config_ok(config, s->prm.state_precision, s->state[0].blend_tma_ok, s->state[0].blend_tma2_ok) ||

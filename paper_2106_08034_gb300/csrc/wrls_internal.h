@@ -85,21 +85,12 @@ inline int blend_sync_config(int cfg) {
   return (cfg >= 0 && cfg < kBlendConfigs) ? map[cfg] : 0;
 }
 cudaError_t launch_blend(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err, cudaStream_t cs);
-// Persistent, prefetching variant of the update kernel (pipeline 3).
-cudaError_t launch_update_pipelined(const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
-                                    const float* rad, const float* mot, int* err, cudaStream_t cs);
 cudaError_t launch_blend_pipelined(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
                                    cudaStream_t cs);
 cudaError_t launch_blend_two_wide(const KParams& kp, int cfg, const StateDesc& cur, float* out, int* err,
                                   cudaStream_t cs);
 cudaError_t launch_read_state(const StateDesc& cur, float* dst, cudaStream_t cs);
 cudaError_t launch_write_state(const StateDesc& cur, const float* src, cudaStream_t cs);
-// Fused wavefront kernel (update + blend in one persistent launch).
-size_t fused_scratch_bytes(int W, int H);
-// variant 1: blend with 2 rows per thread (all threads), 3 CTAs/SM; 2: 4 rows per thread, 2 CTAs/SM.
-cudaError_t launch_fused(int variant, const KParams& kp, const StateDesc& prev, const StateDesc& next, bool reset,
-                         const float* rad, const float* mot, float* out, int* err, int* work, int* flags,
-                         int epoch, cudaStream_t cs);
 
 void set_error(const char* fmt, ...);
 
@@ -137,9 +128,6 @@ struct wrls_stream {
   void* mem3 = nullptr;         // the third copy (wrls_denoise_sequence)
   void* mem = nullptr;          // both state copies, then the device error word
   int* err = nullptr;           // device error word (WRLS_ERR_TIMEOUT from a bounded wait)
-  int* work = nullptr;          // fused kernel: item and exit counters (zero between launches)
-  int* flags = nullptr;         // fused kernel: per-update-tile done flags (frame epochs)
-  int pipeline = 0;             // 0, 3 = update kernel + blend kernel (3: prefetching update); 1, 2 = fused
   size_t mem_bytes = 0;
   int cur = 0;                  // copy holding frame t-1 (the next frame writes next_copy())
   bool need_reset = true;

@@ -23,7 +23,7 @@ constexpr int kTileThreads = kTW * kTH;
 
 // Shared memory of an update tile: the staged previous-state window, the radiance tile with a
 // 1-pixel halo and the tap-footprint reduction. (The copy's mbarrier lives outside, so that a
-// fused kernel may reuse this space for a blend window between tiles.)
+// persistent kernel keeps it, and its phase, across the tiles it runs.)
 template <class SV>
 struct UpdateSmem {
   alignas(128) unsigned char stage[SV::kStageBytes];

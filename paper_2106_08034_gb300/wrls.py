@@ -36,7 +36,7 @@ EXPORTED = [
     "wrls_denoise_frame", "wrls_denoise_frame_host", "wrls_stream_reset", "wrls_stream_destroy",
     "wrls_stream_read_state", "wrls_stream_write_state", "wrls_stream_state_stats", "wrls_stream_frames", "wrls_last_error",
     "wrls_stream_enable_timing", "wrls_stream_kernel_times", "wrls_stream_check",
-    "wrls_stream_autotune", "wrls_stream_set_blend_config", "wrls_stream_set_pipeline",
+    "wrls_stream_autotune", "wrls_stream_set_blend_config",
     "wrls_stream_set_debug",
     "wrls_batch_create", "wrls_batch_set_cuda_stream", "wrls_batch_tick", "wrls_batch_destroy",
     "wrls_batch_tick_static", "wrls_denoise_sequence", "wrls_denoise_sequence_host", "wrls_stream_set_overlap",
@@ -133,7 +133,6 @@ def lib():
         "wrls_stream_check": (i, [vp]),
         "wrls_stream_autotune": (i, [vp, vp, i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
         "wrls_stream_set_blend_config": (i, [vp, i]),
-        "wrls_stream_set_pipeline": (i, [vp, i]),
         "wrls_stream_set_debug": (i, [vp, ctypes.c_uint32]),
         "wrls_stream_kernel_times": (i, [vp, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
@@ -309,15 +308,6 @@ def wrls_stream_autotune(stream: int, out, reps: int = 5):
     chosen = ctypes.c_int()
     _check(lib().wrls_stream_autotune(stream, _ptr(out), int(reps), times, ctypes.byref(chosen)))
     return [float(t) for t in times], int(chosen.value)
-
-
-def wrls_stream_set_pipeline(stream: int, fused: int) -> None:
-    """0 = update kernel + blend kernel (default), 1 / 2 = fused wavefront kernel variants,
-    3 = prefetching persistent update kernel + blend kernel."""
-    _check(lib().wrls_stream_set_pipeline(stream, int(fused)))
-
-
-WRLS_DEBUG_WITHHOLD_STAGE_COPY = 1
 
 
 def wrls_stream_set_debug(stream: int, flags: int) -> None:

@@ -152,8 +152,6 @@ def test_extended_streams_are_rejected_by_batched_ticks():
     assert e.value.status == W.WRLS_ERR_INVALID_ARG
     with pytest.raises(W.WrlsError):
         W.wrls_batch_tick_static([(s.handle, x, None, g, m, o)])
-    with pytest.raises(W.WrlsError):
-        W.wrls_stream_set_pipeline(s.handle, 1)
     with pytest.raises(W.WrlsError):  # the G-buffer planes are required
         s.denoise(x, m, o)
     W.wrls_batch_destroy(b)

@@ -23,13 +23,11 @@ def _built():
     W.lib()
 
 
-def run_pair(frames, width, height, params=None, hooks=None, check_z=True, tol=REL_TOL, pipeline=None):
+def run_pair(frames, width, height, params=None, hooks=None, check_z=True, tol=REL_TOL):
     """Denoise the frames with the GPU and with the oracle; assert parity every frame.
     Returns the per-frame max relative errors."""
     p = params if params is not None else W.wrls_params_default()
     s = W.Stream(width, height, p)
-    if pipeline is not None:
-        W.wrls_stream_set_pipeline(s.handle, pipeline)
     st = O.OracleStream(width, height, oracle_params_from(p))
     out = torch.empty(3, height, width, device="cuda")
     zbuf = torch.empty(W.N_STATE, height, width, device="cuda")
@@ -202,8 +200,7 @@ def test_degenerate_sizes_sequence_and_extended(wh):
     se.close()
 
 
-@pytest.mark.parametrize("pipeline", [0, 3])
-def test_missing_samples_and_bad_motion(pipeline):
+def test_missing_samples_and_bad_motion():
     spec = synth.SceneSpec(90, 60, 10, seed=35, motion="orbit", firefly_frac=0.05)
 
     def hooks(t, rad, mot):
@@ -217,7 +214,7 @@ def test_missing_samples_and_bad_motion(pipeline):
         if t == 6:
             rad[:, 10:13, 20:23] = float("nan")    # a 3x3 hole: clamp box of the centre is empty
         return rad, mot
-    run_pair(cpu_frames(spec), 90, 60, hooks=hooks, pipeline=pipeline)
+    run_pair(cpu_frames(spec), 90, 60, hooks=hooks)
 
 
 def test_reset_restarts_every_pixel():
@@ -252,16 +249,15 @@ def test_host_entry_matches_device_entry():
         assert torch.equal(od.cpu(), oh)
 
 
-@pytest.mark.parametrize("pipeline", [0, 1, 2])
-def test_batch_tick_equals_each_stream_alone(pipeline):
+@pytest.mark.parametrize("precision", [W.WRLS_STATE_F32, W.WRLS_STATE_BF16])
+def test_batch_tick_equals_each_stream_alone(precision):
     sizes = [(64, 48), (100, 33), (257, 129), (31, 7), (128, 128)]
     specs = [synth.SceneSpec(w, h, 5, seed=40 + i, motion="orbit", firefly_frac=0.05)
              for i, (w, h) in enumerate(sizes)]
     frames = [cpu_frames(sp) for sp in specs]
-    alone = [W.Stream(w, h) for (w, h) in sizes]
-    mixed = [W.Stream(w, h) for (w, h) in sizes]
-    for s in alone + mixed:
-        W.wrls_stream_set_pipeline(s.handle, pipeline)
+    p = W.wrls_params_default(state_precision=precision)
+    alone = [W.Stream(w, h, p) for (w, h) in sizes]
+    mixed = [W.Stream(w, h, p) for (w, h) in sizes]
     batch = W.wrls_batch_create(8)
     try:
         for t in range(5):
@@ -292,15 +288,22 @@ def test_full_size_pan_1080p_120_frames():
     s = W.Stream(spec.width, spec.height, p)
     st = O.OracleStream(spec.width, spec.height, oracle_params_from(p))
     out = torch.empty(3, spec.height, spec.width, device="cuda")
-    worst = 0.0
+    worst = worst_c = 0.0
+    n_c = 0
     for t in range(spec.frames):
         f = sc.frame(t)
         s.denoise(f["radiance"].cuda(), f["motion"].cuda(), out)
         ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
-        e = rel_err(out.cpu().numpy(), ref)
+        o = out.cpu().numpy()
+        e = rel_err(o, ref)
         worst = max(worst, e)
+        # the per-channel form, reported beside the per-pixel gate
+        ec = np.abs(o - ref) / np.maximum(np.abs(ref), FLOOR)
+        worst_c = max(worst_c, float(ec.max()))
+        n_c += int((ec.max(axis=0) > REL_TOL).sum())
         assert e <= REL_TOL, (t, e)
-    print("full-size worst rel err %.3g" % worst)
+    print("full-size worst rel err: per pixel %.3g; per channel %.3g (%d of %d pixel-frames above %.0e)"
+          % (worst, worst_c, n_c, spec.width * spec.height * spec.frames, REL_TOL))
 
 
 def test_blend_configs_bitwise_identical_and_autotune():
@@ -309,7 +312,6 @@ def test_blend_configs_bitwise_identical_and_autotune():
     outs = []
     for cfg in range(W.BLEND_CONFIGS):
         s = W.Stream(spec.width, spec.height)
-        W.wrls_stream_set_pipeline(s.handle, 0)
         W.wrls_stream_set_blend_config(s.handle, cfg)
         o = torch.empty(3, spec.height, spec.width, device="cuda")
         for f in fr:
@@ -387,7 +389,6 @@ def test_blend_configs_match_oracle(cfg):
     p = W.wrls_params_default()
     fr = cpu_frames(spec)
     s = W.Stream(spec.width, spec.height, p)
-    W.wrls_stream_set_pipeline(s.handle, 0)
     W.wrls_stream_set_blend_config(s.handle, cfg)
     st = O.OracleStream(spec.width, spec.height, oracle_params_from(p))
     out = torch.empty(3, spec.height, spec.width, device="cuda")
@@ -398,9 +399,8 @@ def test_blend_configs_match_oracle(cfg):
         assert rel_err(out.cpu().numpy(), ref) <= REL_TOL
 
 
-@pytest.mark.parametrize("pipeline", [0, 3])
 @pytest.mark.parametrize("kind", ["uniform", "random"])
-def test_staged_and_global_gather_paths(kind, pipeline):
+def test_staged_and_global_gather_paths(kind):
     """Uniform motion keeps every tile's tap footprint inside the staged window (TMA path);
     per-pixel random motion of a few pixels spreads it beyond (global-gather path)."""
     spec = synth.SceneSpec(160, 96, 8, seed=52, motion="static", firefly_frac=0.05)
@@ -414,40 +414,16 @@ def test_staged_and_global_gather_paths(kind, pipeline):
         else:
             mot.copy_((torch.rand(2, 96, 160, generator=g) - 0.5) * 12.0)
         return rad, mot
-    run_pair(fr, 160, 96, hooks=hooks, pipeline=pipeline)
+    run_pair(fr, 160, 96, hooks=hooks)
 
 
-@pytest.mark.parametrize("pipeline", [0, 1, 2, 3])
-def test_pipelines_match_oracle(pipeline):
+def test_pan_ragged_against_the_oracle():
     spec = synth.SceneSpec(181, 95, 24, seed=56, motion="pan", firefly_frac=0.05)
-    run_pair(cpu_frames(spec), spec.width, spec.height, pipeline=pipeline)
-
-
-@pytest.mark.parametrize("precision", [W.WRLS_STATE_F32, W.WRLS_STATE_BF16])
-def test_pipelines_bitwise_identical(precision):
-    """Two kernels, and both fused-kernel variants, give identical outputs and states."""
-    spec = synth.SceneSpec(333, 200, 6, seed=57, motion="orbit", firefly_frac=0.05)
-    fr = cpu_frames(spec)
-    res = []
-    for pipeline in (0, 1, 2, 3):
-        s = W.Stream(spec.width, spec.height, W.wrls_params_default(state_precision=precision))
-        W.wrls_stream_set_pipeline(s.handle, pipeline)
-        o = torch.empty(3, spec.height, spec.width, device="cuda")
-        st = torch.empty(W.N_STATE, spec.height, spec.width, device="cuda")
-        for f in fr:
-            s.denoise(f["radiance"].cuda(), f["motion"].cuda(), o)
-        s.read_state(st)
-        W.wrls_stream_check(s.handle)
-        torch.cuda.synchronize()
-        res.append((o.clone(), st.clone()))
-        s.close()
-    for o, st in res[1:]:
-        assert torch.equal(o, res[0][0]) and torch.equal(st, res[0][1])
+    run_pair(cpu_frames(spec), spec.width, spec.height)
 
 
 def test_pipelined_blend_rejected_for_16bit_state():
     s = W.Stream(64, 64, W.wrls_params_default(state_precision=W.WRLS_STATE_BF16))
-    W.wrls_stream_set_pipeline(s.handle, 0)
     with pytest.raises(W.WrlsError):
         W.wrls_stream_set_blend_config(s.handle, 4)
     W.wrls_stream_set_blend_config(s.handle, 3)
