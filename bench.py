@@ -13,6 +13,11 @@ N > 1 runs under torchrun: one independent replica per GPU (streams do not shard
 no collective on the data path), value = all ranks' pixels / max-over-ranks time.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (rank 0 only),
 one step = one 1080p frame of the same workload.
+
+The oracle runs in this arm only inside the CPU-baseline leg (rank 0, one GPU; skipped with
+--no-cpu-baseline): timed on a bounded sample of the pan workload, and run once over
+orbit_edit_1080p_120f, where its outputs give the state formats' error statement
+(``precision``) and its own rate a second CPU sample.
 """
 from __future__ import annotations
 
@@ -33,10 +38,36 @@ BYTES_UPDATE_F32 = 220   # per pixel: state read 100 + radiance 12 + motion 8 + 
 BYTES_PATH_F32 = 232     # per pixel and frame for the whole path: + out 12
 BYTES_UPDATE_16 = 128    # 16-bit state: state read 54 (25 x 2 + P scale 4) + 20 + state write 54
 BYTES_PATH_16 = 140      # + out 12
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_update launch on a
-# 1920x1080 frame, from the ncu capture summarised in profiles/k_update_pan_1080p.md (same
-# kernel build). Writes still held in L2 when the kernel ends are not counted by ncu.
-TRAFFIC_PER_LAUNCH = {"k_update": 248864768 + 168868352}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on a 1920x1080
+# frame of the pan workload, copied from an ncu capture, with a hash of the kernel's source
+# files at the time of that capture. The bench reports the figure only while the hash of the
+# current sources matches; after any change to those files it reports null until the
+# capture is taken again. Writes still held in L2 when the kernel ends are not counted.
+KERNEL_SOURCES = {"k_update<StateF32>": ("wrls_frame.cu", "wrls_tiles.cuh", "wrls_device.cuh")}
+TRAFFIC_CAPTURES = {
+    "k_update<StateF32>": {"bytes": 248864768 + 168868352, "sources_sha256_16": "",
+                           "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
+                                      "-k regex:k_update -s 8 -c 2, bench.py --frames 8 --steps 1 --state f32"},
+}
+
+
+def kernel_sources_sha(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2106_08034_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel: str):
+    """(bytes, note): the captured DRAM traffic of `kernel` if its sources are unchanged."""
+    cap = TRAFFIC_CAPTURES.get(kernel)
+    if cap is None:
+        return None, "no capture of this kernel"
+    if cap["sources_sha256_16"] != kernel_sources_sha(kernel):
+        return None, "kernel sources changed since the capture (%s)" % cap["capture"]
+    return cap["bytes"], "copied from an ncu capture of the same sources (%s)" % cap["capture"]
 # Extended path with the G-buffer predictor p = [1, z, g_1..g_4] (d = 8): the state is
 # 3d + d(d+1)/2 + 3 = 63 binary32 values (252 B) per pixel.
 BYTES_UPDATE_D8 = 252 + 12 + 8 + 16 + 252   # state read, radiance, motion, 4 G-buffer planes, state write
@@ -57,14 +88,14 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched BF16 16-stream leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-gbuf", action="store_true", help="skip the d = 8 G-buffer predictor leg")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the state-format error statement (orbit_edit_1080p_120f)")
     ap.add_argument("--no-inputs", action="store_true", help="skip the reconstruction / velocity leg")
     ap.add_argument("--no-vpt", action="store_true", help="skip the path tracer -> denoiser pipeline leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--batched-passes", type=int, default=3)
-    ap.add_argument("--pipeline", type=int, default=-1,
-                    help="run this pipeline instead of timing them all (profiling captures)")
     ap.add_argument("--seq", action="store_true",
-                    help="time only the sequence entry (with --pipeline, default 0, and --overlap)")
+                    help="time only the sequence entry (with --overlap blend CTAs per SM)")
     ap.add_argument("--overlap", type=int, default=1, help="blend CTAs per SM with --seq")
     ap.add_argument("--no-seq", action="store_true", help="do not try the sequence entry")
     ap.add_argument("--state", default="f32", choices=["f32", "bf16", "f16"],
@@ -346,35 +377,101 @@ def batched_leg(args, torch, W, synth, dev):
     }
 
 
-def bf16_error_statement(torch, W, synth, dev, frames=60):
-    """relMSE against the truth of the BF16-, FP16- and FP32-state paths on a 1280x720 orbit
-    sequence with fireflies, a transfer-function edit and a light move (GPU generated)."""
-    spec = synth.SceneSpec(1280, 720, frames, seed=77, motion="orbit", firefly_frac=0.05,
-                           tf_edit_frame=frames // 2, light_move_frame=(3 * frames) // 4)
-    sc = synth.Scene(spec)
-    fr = [sc.frame(t, device=dev) for t in range(frames)]
-    res = {}
-    outs = {}
-    for name, prec in [("f32", W.WRLS_STATE_F32), ("bf16", W.WRLS_STATE_BF16), ("f16", W.WRLS_STATE_F16)]:
-        s = W.Stream(spec.width, spec.height, W.wrls_params_default(state_precision=prec))
-        o = torch.empty(3, spec.height, spec.width, device=dev)
-        acc = 0.0
-        last = []
-        for f in fr:
-            s.denoise(f["radiance"], f["motion"], o)
-            t = f["truth"]
-            acc += float(((o - t) ** 2 / (t * t + 1e-2)).mean())
-            last.append(o.clone())
-        s.close()
-        res[name] = acc / frames
-        outs[name] = last
-    dev_bf16 = max(float(((a - b).abs().amax(0) / b.abs().amax(0).clamp_min(1e-2)).max())
-                   for a, b in zip(outs["bf16"], outs["f32"]))
-    return {"sequence": "1280x720 orbit, 60 frames, 5% fireflies, TF edit, light move",
-            "relmse_f32": round(res["f32"], 6), "relmse_bf16": round(res["bf16"], 6),
-            "relmse_f16": round(res["f16"], 6),
-            "bf16_over_f32": round(res["bf16"] / res["f32"], 5), "f16_over_f32": round(res["f16"] / res["f32"], 5),
-            "bf16_max_pixel_rel_dev_from_f32": round(dev_bf16, 5)}
+FORMATS = (("f32", 0), ("bf16", 1), ("f16", 2))
+
+
+class ErrStats:
+    """Running statistics of a per-pixel error field over frames: max (with its frame and
+    pixel), mean, and a log10 histogram for percentiles."""
+    LO, HI, BINS = -9.0, 1.0, 200
+
+    def __init__(self, torch, dev):
+        self.torch = torch
+        self.hist = torch.zeros(self.BINS, dtype=torch.float64, device=dev)
+        self.max = 0.0
+        self.where = None
+        self.sum = 0.0
+        self.n = 0
+
+    def add(self, err, t):
+        torch = self.torch
+        m = float(err.max())
+        if m > self.max:
+            k = int(err.argmax())
+            self.max, self.where = m, {"frame": t, "y": k // err.shape[1], "x": k % err.shape[1]}
+        self.sum += float(err.sum(dtype=torch.float64))
+        self.n += err.numel()
+        lg = torch.log10(err.double().clamp_min(10.0 ** self.LO))
+        self.hist += torch.histc(lg, bins=self.BINS, min=self.LO, max=self.HI)
+
+    def pct(self, q):
+        c = self.hist.cumsum(0)
+        k = int((c >= q * c[-1]).nonzero()[0])
+        return 10.0 ** (self.LO + (k + 1) * (self.HI - self.LO) / self.BINS)   # upper edge of the bin
+
+    def summary(self):
+        return {"max": float("%.4g" % self.max), "at": self.where, "mean": float("%.4g" % (self.sum / max(self.n, 1))),
+                "p99": float("%.3g" % self.pct(0.99)), "p99_9": float("%.3g" % self.pct(0.999))}
+
+
+def precision_leg(torch, W, synth, dev, oracle_stream=None):
+    """State-format error statement on orbit_edit_1080p_120f (1920x1080, 120 frames, camera
+    orbit, 5% x50 fireflies, transfer-function edit at frame 60, 30 deg light move at frame 90),
+    the binary32, BF16 and FP16 state formats side by side on the same inputs:
+      - with `oracle_stream` (the CPU-baseline leg passes the FP64 oracle): per format the
+        per-pixel relative error of the output against the oracle, max_c |d_c| / max(max_c
+        |ref_c|, 1e-2) (the parity metric), and the per-channel form |d_c| / max(|ref_c|, 1e-2),
+        over every pixel of every frame: max (frame, pixel), mean, 99th / 99.9th percentiles;
+      - relMSE against the truth, mean((out - I)^2 / (I^2 + 1e-2)), on this sequence and on the
+        same sequence without fireflies, and the 16-bit / binary32 ratios;
+      - the largest per-pixel deviation of each 16-bit output from the binary32 output."""
+    base = synth.orbit_edit_1080p_120f()
+    res = {"sequence": "orbit_edit_1080p_120f: 1920x1080, 120 frames, orbit, 5% x50 fireflies, "
+                       "TF edit at 60, light move at 90 (GPU-generated, the same inputs for every path)"}
+    t_oracle = 0.0
+    for fireflies in (True, False):
+        spec = base if fireflies else synth.SceneSpec(**{**base.__dict__, "firefly_frac": 0.0})
+        sc = synth.Scene(spec)
+        streams = {n: W.Stream(spec.width, spec.height, W.wrls_params_default(state_precision=p)) for n, p in FORMATS}
+        outs = {n: torch.empty(3, spec.height, spec.width, device=dev) for n, _ in FORMATS}
+        rmse = {n: 0.0 for n, _ in FORMATS}
+        vs_oracle = {n: (ErrStats(torch, dev), ErrStats(torch, dev)) for n, _ in FORMATS}
+        dev_f32 = {n: ErrStats(torch, dev) for n in ("bf16", "f16")}
+        use_oracle = fireflies and oracle_stream is not None
+        for t in range(spec.frames):
+            f = sc.frame(t, device=dev)
+            for n, _ in FORMATS:
+                streams[n].denoise(f["radiance"], f["motion"], outs[n])
+            tr = f["truth"]
+            for n, _ in FORMATS:
+                rmse[n] += float(((outs[n] - tr) ** 2 / (tr * tr + 1e-2)).mean(dtype=torch.float64))
+            for n in dev_f32:
+                dev_f32[n].add((outs[n] - outs["f32"]).abs().amax(0) / outs["f32"].abs().amax(0).clamp_min(1e-2), t)
+            if use_oracle:
+                c0 = time.perf_counter()
+                ref, _, _ = oracle_stream.frame(f["radiance"].cpu().numpy(), f["motion"].cpu().numpy())
+                t_oracle += time.perf_counter() - c0
+                ref = torch.from_numpy(ref).to(dev)
+                aref = ref.abs()
+                den_px = aref.amax(0).clamp_min(1e-2)
+                for n, _ in FORMATS:
+                    d = (outs[n].double() - ref).abs()
+                    vs_oracle[n][0].add(d.amax(0) / den_px, t)
+                    vs_oracle[n][1].add((d / aref.clamp_min(1e-2)).amax(0), t)
+        for s in streams.values():
+            W.wrls_stream_check(s.handle)
+            s.close()
+        key = "fireflies" if fireflies else "no_fireflies"
+        r = {"relmse_vs_truth": {n: float("%.6g" % (rmse[n] / spec.frames)) for n, _ in FORMATS}}
+        r["relmse_ratio"] = {n: round(rmse[n] / rmse["f32"], 5) for n in ("bf16", "f16")}
+        r["max_pixel_dev_from_f32"] = {n: dev_f32[n].summary() for n in dev_f32}
+        if use_oracle:
+            r["vs_oracle_per_pixel"] = {n: vs_oracle[n][0].summary() for n, _ in FORMATS}
+            r["vs_oracle_per_channel"] = {n: vs_oracle[n][1].summary() for n, _ in FORMATS}
+            px = spec.width * spec.height * spec.frames
+            r["oracle_mpix_s"] = round(px / t_oracle / 1e6, 3)
+        res[key] = r
+    return res
 
 
 def run_reference(args):
@@ -589,13 +686,15 @@ def run_wrls(args):
         for _ in range(args.warmup):
             step()
     cs.synchronize()
-    # tile configuration of the two-kernel pipeline, then the fastest pipeline (untimed)
-    W.wrls_stream_set_pipeline(s.handle, 0)
+    # blend tile configuration, then the faster entry (untimed): per-frame calls, or the
+    # sequence entry (blend of frame t beside the update of frame t+1) with 1 or 2 blend CTAs
+    # per SM
     if args.blend_config >= 0:
         W.wrls_stream_set_blend_config(s.handle, args.blend_config)
         blend_times, blend_cfg = [], args.blend_config
     else:
         blend_times, blend_cfg = W.wrls_stream_autotune(s.handle, out, reps=5)
+
     def time_step():
         step()
         a = torch.cuda.Event(enable_timing=True)
@@ -607,31 +706,20 @@ def run_wrls(args):
         return a.elapsed_time(b) / T
 
     pipe_ms = {}
-    for pipeline in ((0, 1, 2, 3) if args.pipeline < 0 else ()):
-        W.wrls_stream_set_pipeline(s.handle, pipeline)
-        pipe_ms[str(pipeline)] = time_step()
-    # the sequence entry over the two-kernel pipelines, with 1 or 2 blend CTAs per SM
-    seq_choices = [(pl, ov) for pl in (0, 3) for ov in (1, 2)] if args.pipeline < 0 and not args.no_seq else []
-    if args.seq:
-        seq_choices = [(max(args.pipeline, 0), args.overlap)]
+    if not args.seq:
+        pipe_ms["frame"] = time_step()
+    seq_choices = [] if args.no_seq else ([args.overlap] if args.seq else [1, 2])
     mode["seq"] = True
-    for pl, ov in seq_choices:
-        W.wrls_stream_set_pipeline(s.handle, pl)
+    for ov in seq_choices:
         W.wrls_stream_set_overlap(s.handle, ov)
-        pipe_ms["seq%d/%d" % (pl, ov)] = time_step()
+        pipe_ms["seq/%d" % ov] = time_step()
     mode["seq"] = False
-    if pipe_ms:
-        best = min(pipe_ms, key=pipe_ms.get)
-    else:
-        best = str(args.pipeline)
+    best = min(pipe_ms, key=pipe_ms.get)
+    overlap = 2
     if best.startswith("seq"):
         mode["seq"] = True
-        pl, ov = best[3:].split("/")
-        best_pipeline = int(pl)
-        W.wrls_stream_set_overlap(s.handle, int(ov))
-    else:
-        best_pipeline = int(best)
-    W.wrls_stream_set_pipeline(s.handle, best_pipeline)
+        overlap = int(best.split("/")[1])
+        W.wrls_stream_set_overlap(s.handle, overlap)
     W.wrls_stream_enable_timing(s.handle, True)
 
     clocks = ClockSampler(smi_device_id(torch, dev, local))
@@ -689,13 +777,11 @@ def run_wrls(args):
                 k = t % ring
                 W.wrls_denoise_frame_host(s2.handle, h_rad[k], None, None, h_mot[k], h_out[k])
         s2 = W.Stream(Wd, Hd, p, cuda_stream=cs)
-        W.wrls_stream_set_pipeline(s2.handle, best_pipeline)
         W.wrls_stream_set_blend_config(s2.handle, blend_cfg)
-        W.wrls_stream_set_overlap(s2.handle, int(best[3:].split("/")[1]) if best.startswith("seq") else 2)
+        W.wrls_stream_set_overlap(s2.handle, overlap)
         ms_seq = time_host(seq_host, s2)
         s2.close()
         s3 = W.Stream(Wd, Hd, p, cuda_stream=cs)
-        W.wrls_stream_set_pipeline(s3.handle, best_pipeline)
         W.wrls_stream_set_blend_config(s3.handle, blend_cfg)
         ms_frame = time_host(frame_host, s3)
         s3.close()
@@ -707,27 +793,23 @@ def run_wrls(args):
     peak, peak_kind = measured_peaks()
     upd_per = upd_ms / max(nfr, 1)
     bl_per = bl_ms / max(nfr, 1)
-    traffic = None
-    if best_pipeline in (0, 3):
-        kname = ("k_update" if best_pipeline == 0 else "k_update_pipe") + \
-            " (reproject + Eq. 12-14 update; the blend is a separate kernel)"
-        kbytes = bytes_update
-        if best_pipeline == 0 and (Wd, Hd) == (1920, 1080) and prec == 0:
-            traffic = TRAFFIC_PER_LAUNCH["k_update"]
-        if mode["seq"]:
-            kname += "; timed while overlapping the previous frame's blend"
-    else:
-        kname, kbytes = "k_fused (reproject + Eq. 12-14 update + 5x5 blend, one launch)", bytes_path
+    traffic, traffic_note = None, "no capture of this configuration"
+    kname = "k_update (reproject + Eq. 12-14 update; the blend is a separate kernel)"
+    kbytes = bytes_update
+    if (Wd, Hd) == (1920, 1080) and prec == 0:
+        traffic, traffic_note = captured_traffic("k_update<StateF32>")
+    if mode["seq"]:
+        kname += "; timed while overlapping the previous frame's blend"
     achieved = kbytes * px / (upd_per / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_source": traffic_note,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "bytes_per_px": kbytes,
-                "kernel_ms": {"update" if best_pipeline in (0, 3) else "fused": round(upd_per, 5),
-                              "blend": round(bl_per, 5)},
-                "pipeline": best_pipeline, "entry": "wrls_denoise_sequence" if mode["seq"] else "wrls_denoise_frame",
-                "pipeline_ms_per_frame": {str(k): round(v, 5) for k, v in pipe_ms.items()},
+                "kernel_ms": {"update": round(upd_per, 5), "blend": round(bl_per, 5)},
+                "entry": "wrls_denoise_sequence" if mode["seq"] else "wrls_denoise_frame",
+                "blend_ctas_per_sm": overlap if mode["seq"] else None,
+                "entry_ms_per_frame": {str(k): round(v, 5) for k, v in pipe_ms.items()},
                 "blend_autotune_ms": [round(t, 5) for t in blend_times], "blend_config": blend_cfg,
                 "path": {"bytes_per_px": bytes_path,
                          "achieved": round(bytes_path * px * frames_total / world / (ms / 1e3) / 1e9, 1),
@@ -736,7 +818,6 @@ def run_wrls(args):
     batched = None
     if not args.no_batched:
         batched = batched_leg(args, torch, W, synth, dev)
-        batched["error"] = bf16_error_statement(torch, W, synth, dev)
     gbuf = None
     if not args.no_gbuf:
         gbuf = gbuf_leg(torch, W, synth, dev, peak)
@@ -757,7 +838,17 @@ def run_wrls(args):
 
     small = small_stream_latency(torch, W, synth, dev)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    precision = None
+    cpu_leg = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if not args.no_precision:
+        # the state formats' error statement; against the FP64 oracle only inside the
+        # CPU-baseline leg (rank 0, one GPU), where the oracle also runs for timing
+        oracle_stream = None
+        if cpu_leg:
+            import oracle as O
+            oracle_stream = O.OracleStream(1920, 1080)
+        precision = precision_leg(torch, W, synth, dev, oracle_stream)
+    if cpu_leg:
         rate, n, dt, cores = cpu_oracle_rate(spec, args.cpu_seconds)
         rate1, n1, dt1 = cpu_single_thread_rate()
         cpu = {"value": round(rate, 4), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
@@ -777,8 +868,8 @@ def run_wrls(args):
                        "l2": "inputs larger than L2: state ping-pong 2 x 207 MB per frame",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched_bf16": batched, "gbuf_predictor_d8": gbuf, "input_steps": inputs, "vpt_pipeline": vpt, "small_stream": small, "serving": serving,
-            "gpu_launches": (2 if best_pipeline in (0, 3) else 1) * T * args.steps, "clocks": ck,
+            "batched_bf16": batched, "precision": precision, "gbuf_predictor_d8": gbuf, "input_steps": inputs, "vpt_pipeline": vpt, "small_stream": small, "serving": serving,
+            "gpu_launches": 2 * T * args.steps, "clocks": ck,
         }
         print(json.dumps(line), flush=True)
     s.close()

@@ -97,7 +97,7 @@ typedef struct wrls_params {
  * separate pair of kernels (one thread per pixel, binary32 state of 3d + d(d+1)/2 + 3 planes
  * per pixel: beta[c][a] at plane c*d + a, the upper triangle of P row by row, then z). They
  * need state_precision WRLS_STATE_F32 (WRLS_ERR_INVALID_ARG otherwise), take no blend tile
- * configuration or pipeline other than 0, and are not accepted by the batched ticks.
+ * configuration other than 0, and are not accepted by the batched ticks.
  */
 
 typedef struct wrls_stream wrls_stream;
@@ -170,8 +170,7 @@ wrls_status wrls_denoise_frame_host(wrls_stream* s, const float* radiance, const
  * returning, the stream's CUDA stream is made to wait for the last blend, so all n outputs
  * are complete once it is synchronised. frames[i].stream must be s or NULL; each frame
  * follows the rules of wrls_denoise_frame, and the output of frame i must not overlap any
- * buffer of frame i+1. With a fused pipeline (1, 2) or n = 1 the frames run one after
- * another. Kernel timing (wrls_stream_enable_timing) records each kernel on the CUDA stream
+ * buffer of frame i+1. With n = 1 the frame runs as wrls_denoise_frame. Kernel timing (wrls_stream_enable_timing) records each kernel on the CUDA stream
  * it runs on. Asynchronous.
  */
 wrls_status wrls_denoise_sequence(wrls_stream* s, const struct wrls_frame_io* frames, int n);
@@ -248,7 +247,7 @@ wrls_status wrls_stream_state_stats(wrls_stream* s, wrls_state_stats* out);
 uint64_t wrls_stream_frames(const wrls_stream* s);
 
 /*
- * Autotuner of the blend kernel's tile shape (two-kernel pipeline; not in the paper): times every blend tile
+ * Autotuner of the blend kernel's tile shape (not in the paper): times every blend tile
  * configuration on the
  * stream's current state, `reps` launches each (>= 1), on the stream's CUDA stream, and
  * keeps the fastest for later frames. Configurations (output tile rows x output rows per
@@ -272,24 +271,6 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
 #define WRLS_BLEND_CONFIGS 10
 wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* times_ms, int* chosen);
 
-/*
- * Choose how wrls_denoise_frame runs a frame (kernel organisation, not in the paper; every
- * choice computes Sec. 5.3 with bitwise identical results). 0 (default after create): an update kernel
- * followed by a blend kernel (blend tile chosen by wrls_stream_set_blend_config /
- * wrls_stream_autotune). 1 or 2: one persistent
- * "wavefront" kernel that claims 32 x 8 update tiles in raster order and, a few tiles behind,
- * blends 32 x 16 output tiles whose neighbourhoods are complete, so the memory-bound update
- * of some tiles overlaps the arithmetic-bound blend of others and the blend reads the new
- * state from L2 (1: each blend thread produces 2 rows, all 256 threads blend; 2: 4 rows,
- * 128 threads blend with more register reuse and fewer CTAs per SM). Its inter-CTA waits are
- * bounded (WRLS_ERR_TIMEOUT via wrls_stream_check). 3: as 0, with a persistent update kernel
- * that prefetches each tile's motion, radiance and state window (TMA) while the tile before it
- * is being updated. wrls_batch_tick_static runs pipeline 3 as 0. All give bitwise identical
- * results.
- * With the fused kernel the kernel timing reports the whole frame as the update time.
- */
-wrls_status wrls_stream_set_pipeline(wrls_stream* s, int fused);
-
 /* Select a blend tile configuration (0..WRLS_BLEND_CONFIGS-1; kernel tiling, not in the
  * paper) directly; configurations
  * 4-7 need the binary32 state (WRLS_ERR_INVALID_ARG otherwise). */
@@ -297,7 +278,7 @@ wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config);
 
 /*
  * Test hook for the failure path of the bounded device-side waits (not in the paper). With
- * WRLS_DEBUG_WITHHOLD_STAGE_COPY set, the update kernel of the two-kernel pipeline arms the
+ * WRLS_DEBUG_WITHHOLD_STAGE_COPY set, the update kernel arms the
  * mbarrier of each tile's state-window copy but does not issue the copy, so the tile's
  * bounded wait runs out (about one second of SM clocks); the kernel then records
  * WRLS_ERR_TIMEOUT in the stream's error word (read by wrls_stream_check) and returns. The
@@ -331,13 +312,11 @@ const char* wrls_last_error(void);
  * ---- Batched tick: all ready frames of many streams in one graph launch ----
  *
  * One tick processes one frame of each of n streams (of any sizes) with a single CUDA
- * graph launch. For streams on the two-kernel pipelines (0, 3) the graph holds each
- * stream's own update and blend kernels (with the stream's tuned blend tile), the streams
- * spread over four parallel branches so that the blend of one stream overlaps the update of
- * another; it is captured each tick and applied to the instantiated graph with
- * cudaGraphExecUpdate. With a fused pipeline (1, 2) one persistent kernel pulls (stream,
- * tile) work items from a device work list, replayed from a graph captured once per batch
- * shape. Results are identical to calling wrls_denoise_frame on each stream alone.
+ * graph launch. The graph holds each stream's own update and blend kernels (with the
+ * stream's tuned blend tile), the streams spread over four parallel branches so that the
+ * blend of one stream overlaps the update of another; it is captured each tick and applied to
+ * the instantiated graph with cudaGraphExecUpdate. Results are identical to calling
+ * wrls_denoise_frame on each stream alone.
  */
 typedef struct wrls_frame_io {
     wrls_stream* stream;
@@ -359,10 +338,8 @@ wrls_status wrls_batch_create(int max_streams, wrls_batch** out);
 wrls_status wrls_batch_set_cuda_stream(wrls_batch* b, void* cuda_stream);
 
 /* Run one tick over n frames (1 <= n <= max_streams; each stream at most once, all
- * streams of the same state precision and blend mode, none on the extended path). The
- * pipeline of the largest stream decides the form of the tick: on the two-kernel form every
- * stream uses its own update pipeline and blend tile configuration, on the fused form every
- * stream uses the fused variant of the largest stream. Asynchronous. */
+ * streams of the same state precision and blend mode, none on the extended path). Every
+ * stream uses its own blend tile configuration. Asynchronous. */
 wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n);
 
 /* Synchronise and free. NULL is a no-op. */
@@ -401,12 +378,16 @@ wrls_status wrls_denoise_batch(wrls_stream* const* streams, const struct wrls_fr
  *   cuda_stream    the cudaStream_t (as void*) to enqueue on; NULL = legacy default stream.
  *
  * The first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress) with that device current and caches it; make that first call
- * before any stream capture. Every call reuses the same array and overwrites what the
- * previous call left there (the work counters are cleared by each call), so calls whose
- * work overlaps on the GPU (on different CUDA streams, or from different host threads
- * without ordering) race: serialise them on one CUDA stream. Outputs equal those of
- * wrls_batch_tick. Asynchronous.
+ * (cudaGetSymbolAddress) with that device current and caches it for the life of the process;
+ * make that first call before any stream capture. The cached address, like every stream's
+ * state, belongs to the device's current context: after cudaDeviceReset do not call this
+ * entry point again in the same process. Each call writes its work table into the array
+ * with one small kernel whose parameter carries the table (no host buffer is read after the
+ * call returns, and no host-to-device copy is made) and clears the work counters there.
+ * Every call reuses the same array and overwrites what the previous call left there, so
+ * calls whose work overlaps on the GPU (on different CUDA streams, or from different host
+ * threads without ordering) race: serialise them on one CUDA stream. Outputs equal those of
+ * wrls_batch_tick bit for bit. Asynchronous.
  */
 #define WRLS_STATIC_BATCH_MAX 16
 wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n, void* cuda_stream);

@@ -1,17 +1,16 @@
 // Batched tick: one frame of each of n streams (of any sizes) in one CUDA graph launch.
 //
-// Two-kernel pipelines (the default): the graph holds each stream's own update and blend
+// wrls_batch_tick: the graph holds each stream's own update and blend
 // kernels (those of wrls_denoise_frame, with their parameters in the constant bank and the
 // stream's tuned blend tile), the streams' chains spread over kLanes parallel branches, so
 // that one stream's arithmetic-bound blend runs while another stream's memory-bound update
 // runs. The graph is captured every tick (input pointers and restart flags change) and
 // applied to the instantiated graph with cudaGraphExecUpdate.
 //
-// Fused pipelines and wrls_batch_tick_static: the host writes a table (header + one
-// FrameWork per frame, with each frame's first tile index) and persistent kernels pull
-// (stream, tile) work items from it: a CTA takes the next tile with an atomicAdd on a work
-// counter until the counter passes the total; no CTA ever waits on another. The fused tick
-// replays a graph captured once per (pinned table buffer, precision, blend mode, variant).
+// wrls_batch_tick_static: the host writes a table (header + one FrameWork per frame, with
+// each frame's first tile index) and persistent kernels pull (stream, tile) work items from
+// it: a CTA takes the next tile with an atomicAdd on a work counter until the counter passes
+// the total; no CTA ever waits on another.
 //
 // The tile bodies are those of the single-frame kernels, so every stream's output and
 // state are bitwise identical to denoising it alone.
@@ -24,7 +23,7 @@
 #include <vector>
 
 #include "wrls_internal.h"
-#include "wrls_fused.cuh"
+#include "wrls_tiles.cuh"
 
 namespace wrls {
 
@@ -50,17 +49,12 @@ struct alignas(128) FrameWork {
   int tiles_x;       // tiles per row (32 pixels wide, both phases)
   int begin_update;  // first work item of this frame in the update list (32 x 8 tiles)
   int begin_blend;   // first work item of this frame in the blend list (32 x TH tiles)
-  int begin_fused;   // first work item of this frame in the fused list
-  int* flags;        // the stream's tile flags (fused kernel)
-  int epoch;         // the frame's flag stamp
-  int lag;           // fused kernel: blends trail their dependencies by this many items
 };
 
 struct alignas(128) BatchHeader {
   int n;
   int total_update;
   int total_blend;
-  int total_fused;
 };
 
 template <class SV> __device__ __forceinline__ SV make_view(void* base, float* scale, size_t ps, int pitch);
@@ -76,10 +70,10 @@ template <> __device__ __forceinline__ StateF16 make_view<StateF16>(void* base, 
 
 // Claim the next work item of a list; returns its tile index within its frame (or -1 when
 // the list is exhausted) and the frame in *frame.
-// Lists: 0 = update tiles, 1 = blend tiles, 2 = fused items.
+// Lists: 0 = update tiles, 1 = blend tiles.
 template <int LIST>
 __device__ __forceinline__ int list_begin(const FrameWork& w) {
-  return LIST == 0 ? w.begin_update : (LIST == 1 ? w.begin_blend : w.begin_fused);
+  return LIST == 0 ? w.begin_update : w.begin_blend;
 }
 
 template <int LIST>
@@ -89,7 +83,7 @@ __device__ __forceinline__ int next_item(const BatchHeader* __restrict__ hdr,
   __syncthreads();
   if (threadIdx.x == 0) {
     const int t = atomicAdd(counter, 1);
-    const int total = LIST == 0 ? hdr->total_update : (LIST == 1 ? hdr->total_blend : hdr->total_fused);
+    const int total = LIST == 0 ? hdr->total_update : hdr->total_blend;
     int f = -1;
     if (t < total) {
       int lo = 0, hi = hdr->n - 1;  // last frame whose list begins at or before t
@@ -156,75 +150,11 @@ __global__ void __launch_bounds__(kTW * TH / R)
   }
 }
 
-// Fused wavefront over all frames of the tick: the frames' item lists are concatenated, so
-// every dependency of an item (same frame, smaller index) was claimed earlier.
-template <class SV, int MODE, int R, int MIN_CTAS>
-__global__ void __launch_bounds__(kTileThreads, MIN_CTAS)
-    k_batch_fused(const BatchHeader* __restrict__ hdr, const FrameWork* __restrict__ fw, int* counters) {
-  extern __shared__ unsigned char dsmem[];
-  unsigned char* base = align128(dsmem);
-  __shared__ int s_item, s_frame, s_ok;
-  __shared__ alignas(8) uint64_t bar;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  uint32_t phase = 0;
-  for (;;) {
-    int f;
-    const int lt = next_item<2>(hdr, fw, counters + 2, &s_item, &s_frame, &f);
-    if (lt < 0) break;
-    const FrameWork& w = fw[f];
-    if (threadIdx.x == 0 && w.stage_ok) {
-      acquire_tensormap(&w.maps.planes);
-      if constexpr (SV::kHasScale) acquire_tensormap(&w.maps.scale);
-    }
-    const SV prev = make_view<SV>(w.prev_base, w.prev_scale, w.plane_stride, w.pitch);
-    const SV next = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
-    if (!fused_item<SV, MODE, R>(base, &bar, phase, &s_ok, lt, w.kp, w.W, w.H, w.reset != 0, w.stage_ok != 0, prev,
-                                 next, &w.maps, w.rad, w.mot, w.out, w.err, w.flags, w.epoch, w.lag))
-      break;
-  }
-}
-
 static int sm_count() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return sms > 0 ? sms : 1;
-}
-
-template <class SV, int MODE, int R, int MIN_CTAS>
-static cudaError_t capture_fused_v(cudaStream_t cap, const void* h_table, void* d_table, size_t bytes,
-                                   int* d_counters, cudaGraphExec_t* exec) {
-  constexpr int fbytes = fused_smem_bytes<SV>();
-  cudaError_t e = cudaFuncSetAttribute(k_batch_fused<SV, MODE, R, MIN_CTAS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, fbytes);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_fused<SV, MODE, R, MIN_CTAS>, kTileThreads, fbytes);
-  if (e != cudaSuccess) return e;
-  const int grid = sm_count() * (occ > 0 ? occ : 1);
-  const BatchHeader* hdr = (const BatchHeader*)d_table;
-  const FrameWork* fw = (const FrameWork*)((char*)d_table + sizeof(BatchHeader));
-  cudaGraph_t g = nullptr;
-  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return e;
-  cudaMemcpyAsync(d_table, h_table, bytes, cudaMemcpyHostToDevice, cap);
-  cudaMemsetAsync(d_counters, 0, 4 * sizeof(int), cap);
-  k_batch_fused<SV, MODE, R, MIN_CTAS><<<grid, kTileThreads, fbytes, cap>>>(hdr, fw, d_counters);
-  e = cudaStreamEndCapture(cap, &g);
-  if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(exec, g, 0);
-  cudaGraphDestroy(g);
-  return e;
-}
-
-template <class SV>
-static cudaError_t capture_fused(int mode, int variant, cudaStream_t cap, const void* h, void* d, size_t bytes,
-                                 int* c, cudaGraphExec_t* exec) {
-  if (variant == 2)
-    return mode == 0 ? capture_fused_v<SV, 0, 4, 2>(cap, h, d, bytes, c, exec)
-                     : capture_fused_v<SV, 1, 4, 2>(cap, h, d, bytes, c, exec);
-  return mode == 0 ? capture_fused_v<SV, 0, 2, 3>(cap, h, d, bytes, c, exec)
-                   : capture_fused_v<SV, 1, 2, 3>(cap, h, d, bytes, c, exec);
 }
 
 static int blend_rows(int cfg) {
@@ -249,29 +179,10 @@ struct wrls_batch {
   cudaEvent_t ev_join[kLanes] = {};
   cudaGraphExec_t exec_chains = nullptr;    // the per-stream tick graph
   std::vector<int> order;                   // frames by pixel count, largest first
-  size_t table_bytes = 0;
-  void* d_table = nullptr;
-  int* d_counters = nullptr;
-  void* h_table[2] = {nullptr, nullptr};
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  // graph per (pinned slot, precision, blend mode, variant) for the fused tick
-  cudaGraphExec_t exec_fused[2][3][2][2] = {};
-  int fused_ctas = 0;  // resident CTAs of the fused kernel (sets the blends' lag)
-  int slot = 0;
   int device = 0;
 };
 
 static void batch_free(wrls_batch* b) {
-  for (int s = 0; s < 2; ++s) {
-    for (int p = 0; p < 3; ++p)
-      for (int m = 0; m < 2; ++m)
-        for (int v = 0; v < 2; ++v)
-          if (b->exec_fused[s][p][m][v]) cudaGraphExecDestroy(b->exec_fused[s][p][m][v]);
-    if (b->ev[s]) cudaEventDestroy(b->ev[s]);
-    if (b->h_table[s]) cudaFreeHost(b->h_table[s]);
-  }
-  if (b->d_table) cudaFree(b->d_table);
-  if (b->d_counters) cudaFree(b->d_counters);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (int k = 0; k < wrls_batch::kLanes; ++k) {
     if (b->lane[k]) cudaStreamDestroy(b->lane[k]);
@@ -315,9 +226,7 @@ static wrls_status tick_chains(wrls_batch* b, const wrls_frame_io* frames, int n
     cudaStream_t ln = b->lane[k];
     const StateDesc& prev = s->state[s->cur];
     const StateDesc& next = s->state[next_copy(s)];
-    e = s->pipeline == 3
-            ? launch_update_pipelined(s->kp, prev, next, s->need_reset, frames[i].radiance, frames[i].motion, s->err, ln)
-            : launch_update(s->kp, prev, next, s->need_reset, frames[i].radiance, frames[i].motion, s->err, ln);
+    e = launch_update(s->kp, prev, next, s->need_reset, frames[i].radiance, frames[i].motion, s->err, ln);
     if (e == cudaSuccess) e = launch_blend(s->kp, s->blend_cfg, next, frames[i].out, s->err, ln);
   }
   for (int k = 0; k < lanes && e == cudaSuccess; ++k) {
@@ -372,15 +281,7 @@ wrls_status wrls_batch_create(int max_streams, wrls_batch** out) {
     return WRLS_ERR_OOM;
   }
   cudaGetDevice(&b->device);
-  b->fused_ctas = 3 * sm_count();
-  b->table_bytes = sizeof(BatchHeader) + (size_t)max_streams * sizeof(FrameWork);
-  cudaError_t e = cudaMalloc(&b->d_table, b->table_bytes);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counters, 4 * sizeof(int));
-  for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
-    e = cudaMallocHost(&b->h_table[s], b->table_bytes);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[s], cudaEventDisableTiming);
-  }
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   for (int k = 0; k < wrls_batch::kLanes && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&b->lane[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
@@ -436,95 +337,7 @@ wrls_status wrls_batch_tick(wrls_batch* b, const wrls_frame_io* frames, int n) {
         return WRLS_ERR_INVALID_ARG;
       }
   }
-  {
-    // the pipeline of the largest stream decides the tick's form
-    int pl = 1;
-    size_t most = 0;
-    for (int i = 0; i < n; ++i) {
-      const size_t px = (size_t)frames[i].stream->W * frames[i].stream->H;
-      if (px > most) {
-        most = px;
-        pl = frames[i].stream->pipeline == 3 ? 0 : frames[i].stream->pipeline;
-      }
-    }
-    if (pl == 0) return tick_chains(b, frames, n);
-  }
-  const int slot = b->slot;
-  cudaError_t e = cudaEventSynchronize(b->ev[slot]);  // the slot's previous copy has run
-  if (e != cudaSuccess) { set_error("wrls_batch_tick: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
-  BatchHeader* hdr = (BatchHeader*)b->h_table[slot];
-  FrameWork* fw = (FrameWork*)((char*)b->h_table[slot] + sizeof(BatchHeader));
-  // fused tick: the fused variant of the largest stream
-  int pipeline = 1;
-  {
-    size_t most = 0;
-    for (int i = 0; i < n; ++i) {
-      const size_t px = (size_t)frames[i].stream->W * frames[i].stream->H;
-      if (px > most) {
-        most = px;
-        pipeline = frames[i].stream->pipeline;
-      }
-    }
-  }
-  int items_f = 0;
-  for (int i = 0; i < n; ++i) {
-    wrls_stream* s = frames[i].stream;
-    const StateDesc& pv = s->state[s->cur];
-    const StateDesc& nx = s->state[next_copy(s)];
-    FrameWork& w = fw[i];
-    w.maps = pv.maps;
-    w.stage_ok = pv.stage_ok ? 1 : 0;
-    w.err = s->err;
-    w.kp = s->kp;
-    w.prev_base = pv.base;
-    w.prev_scale = pv.scale;
-    w.next_base = nx.base;
-    w.next_scale = nx.scale;
-    w.plane_stride = pv.plane_stride;
-    w.rad = frames[i].radiance;
-    w.mot = frames[i].motion;
-    w.out = frames[i].out;
-    w.pitch = pv.pitch;
-    w.W = s->W;
-    w.H = s->H;
-    w.reset = s->need_reset ? 1 : 0;
-    w.tiles_x = (s->W + kTW - 1) / kTW;
-    w.begin_fused = items_f;
-    w.flags = s->flags;
-    w.epoch = (int)((s->frames + 1) & 0x7fffffff);
-    w.lag = fused_lag(s->W, s->H, b->fused_ctas);
-    items_f += fused_items(s->W, s->H, w.lag);
-  }
-  hdr->n = n;
-  hdr->total_fused = items_f;
-  cudaGraphExec_t& ex = b->exec_fused[slot][prec][mode][pipeline == 2 ? 1 : 0];
-  if (!ex) {
-    const size_t bytes = b->table_bytes;
-    void* h = b->h_table[slot];
-    switch (prec) {
-      case 0: e = capture_fused<StateF32>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-      case 1: e = capture_fused<StateBF16>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-      default: e = capture_fused<StateF16>(mode, pipeline, b->cap, h, b->d_table, bytes, b->d_counters, &ex); break;
-    }
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      ex = nullptr;
-      set_error("wrls_batch_tick: graph capture failed: %s", cudaGetErrorString(e));
-      return WRLS_ERR_CUDA;
-    }
-  }
-  e = cudaGraphLaunch(ex, b->cs);
-  if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], b->cs);
-  if (e != cudaSuccess) { set_error("wrls_batch_tick: graph launch: %s", cudaGetErrorString(e)); return WRLS_ERR_CUDA; }
-  for (int i = 0; i < n; ++i) {
-    wrls_stream* s = frames[i].stream;
-    s->cur = next_copy(s);
-    s->need_reset = false;
-    s->has_frame = true;
-    s->frames++;
-  }
-  b->slot ^= 1;
-  return WRLS_OK;
+  return tick_chains(b, frames, n);
 }
 
 wrls_status wrls_denoise_batch(wrls_stream* const* streams, const wrls_frame_io* io, int n) {
@@ -571,8 +384,6 @@ wrls_status wrls_denoise_batch(wrls_stream* const* streams, const wrls_frame_io*
 void wrls_batch_destroy(wrls_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->cs);
-  for (int s = 0; s < 2; ++s)
-    if (b->ev[s]) cudaEventSynchronize(b->ev[s]);
   batch_free(b);
 }
 
@@ -584,14 +395,41 @@ void wrls_batch_destroy(wrls_batch* b) {
 // the two work counters live in the file-scope array below instead of cudaMalloc'ed memory.
 // Host code must not pass the array's name to a kernel (on the host it names a stand-in, not
 // device memory): its device address is looked up once per device with
-// cudaGetSymbolAddress, on the first call made with that device current, and cached.
+// cudaGetSymbolAddress, on the first call made with that device current, and cached. The host
+// builds the table on its stack and hands it to k_static_fill by value (a kernel parameter),
+// which writes it into the array and clears the counters: no host buffer is read after the
+// call returns and no pageable copy is made.
 
-constexpr int kStaticBatchMax = 16;  // frames per call
+constexpr int kStaticBatchMax = WRLS_STATIC_BATCH_MAX;  // frames per call
+static_assert(kStaticBatchMax == 16, "the documented size of the static array assumes 16 frames");
 constexpr size_t kStaticTableBytes = sizeof(BatchHeader) + kStaticBatchMax * sizeof(FrameWork);
 constexpr size_t kStaticCountersOffset = (kStaticTableBytes + 255) / 256 * 256;
-constexpr size_t kStaticScratchBytes = kStaticCountersOffset + 256;
+constexpr size_t kStaticScratchBytes = 10752;  // the size the header states
+static_assert(kStaticCountersOffset + 2 * sizeof(int) <= kStaticScratchBytes, "table and counters exceed the array");
+static_assert(kStaticTableBytes % 16 == 0, "the fill kernel copies 16-byte words");
+static_assert(kStaticTableBytes <= 32000, "the table is passed as one kernel parameter");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct alignas(16) StaticTable {
+  unsigned char bytes[kStaticTableBytes];
+};
+
+// Copy the host-built table (a kernel parameter) into the static array at `scratch` and clear
+// the two work counters; then release the tensor maps in the table to the tensormap proxy
+// (the batch kernels acquire them before their first bulk copy).
+__global__ void __launch_bounds__(256) k_static_fill(const __grid_constant__ StaticTable tab, const int nbytes,
+                                                     unsigned char* __restrict__ scratch) {
+  const uint4* src = reinterpret_cast<const uint4*>(tab.bytes);
+  uint4* dst = reinterpret_cast<uint4*>(scratch);
+  for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x) dst[i] = src[i];
+  if (threadIdx.x == 0) {
+    int* counters = reinterpret_cast<int*>(scratch + kStaticCountersOffset);
+    counters[0] = 0;
+    counters[1] = 0;
+  }
+  asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+}
 
 static std::mutex g_static_mu;
 static void* g_static_addr[256] = {};  // device address of g_static_scratch per device ordinal
@@ -701,12 +539,12 @@ extern "C" wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n
     if (px > most) { most = px; cfg = blend_sync_config(frames[i].stream->blend_cfg); }
   }
   const int th_b = blend_rows(cfg);
-  // The table is built on the stack and copied with cudaMemcpyAsync from pageable memory,
-  // which returns once the bytes are staged, so the stack buffer may go out of scope.
-  alignas(128) unsigned char host_table[kStaticTableBytes];
-  memset(host_table, 0, sizeof(host_table));
-  BatchHeader* hdr = (BatchHeader*)host_table;
-  FrameWork* fw = (FrameWork*)(host_table + sizeof(BatchHeader));
+  // The table is built on the stack and passed by value to k_static_fill: the launch copies
+  // the parameter, so the stack buffer may go out of scope when the call returns.
+  StaticTable host_table;
+  memset(&host_table, 0, sizeof(host_table));
+  BatchHeader* hdr = (BatchHeader*)host_table.bytes;
+  FrameWork* fw = (FrameWork*)(host_table.bytes + sizeof(BatchHeader));
   int tiles_u = 0, tiles_b = 0;
   for (int i = 0; i < n; ++i) {
     wrls_stream* s = frames[i].stream;
@@ -740,9 +578,9 @@ extern "C" wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n
   hdr->total_blend = tiles_b;
   cudaStream_t cs = (cudaStream_t)cuda_stream;
   int* counters = (int*)((unsigned char*)scratch + kStaticCountersOffset);
-  const size_t bytes = sizeof(BatchHeader) + (size_t)n * sizeof(FrameWork);
-  cudaError_t e = cudaMemcpyAsync(scratch, host_table, bytes, cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), cs);
+  const int bytes = (int)(sizeof(BatchHeader) + (size_t)n * sizeof(FrameWork));
+  k_static_fill<<<1, 256, 0, cs>>>(host_table, (bytes + 15) / 16 * 16, (unsigned char*)scratch);
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     switch (prec) {
       case 0: e = launch_static<StateF32>(mode, cfg, cs, scratch, counters); break;

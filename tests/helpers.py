@@ -55,3 +55,11 @@ def cpu_frames(spec, count=None):
 
 def oracle_z_planes(st):
     return st.z.reshape(st.H, st.W, 3).transpose(2, 0, 1)
+
+
+def rel_err_channel(gpu, ref):
+    """Max per-channel relative error |gpu_c - ref_c| / max(|ref_c|, FLOOR) of (C, H, W) colour
+    arrays: the stricter channel-by-channel form, reported beside the per-pixel parity metric."""
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.abs(gpu - ref) / np.maximum(np.abs(ref), FLOOR)))

@@ -29,6 +29,12 @@ def test_header_and_binding_agree():
     assert _declared_functions() == sorted(W.EXPORTED)
 
 
+def test_header_constants_match_the_binding():
+    src = open(os.path.join(ROOT, "include", "wrls.h")).read()
+    m = re.search(r"#define\s+WRLS_STATIC_BATCH_MAX\s+(\d+)", src)
+    assert m and int(m.group(1)) == W.STATIC_BATCH_MAX
+
+
 def test_every_declared_symbol_is_exported(lib):
     for name in _declared_functions():
         assert hasattr(lib, name), name

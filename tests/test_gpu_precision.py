@@ -1,0 +1,128 @@
+"""State-format precision of the CUDA path against the FP64 oracle (Sec. 5.2, Eq. 10-11, 14:
+the recursion that the stored state carries from frame to frame).
+
+- A gate that can fail: on a firefly-free orbit sequence with a transfer-function edit and a
+  light move, the relMSE against the truth of the BF16 / FP16 state paths stays within 1 % of
+  the binary32 path's, and their error against the oracle stays within the bounds stated here.
+- Long runs: 1200 frames (more than twice the effective memory 1/(1 - lambda) = 500 frames
+  of lambda = 0.998) at 128 x 128, static camera and pan, 5 % fireflies: the binary32 state
+  still meets the parity bound on every frame, and trace(P) read back from the device follows
+  the oracle's; the BF16 state's error stays bounded.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2106_08034_gb300 import synth
+from paper_2106_08034_gb300 import wrls as W
+
+from helpers import FLOOR, REL_TOL, cpu_frames, oracle_params_from, rel_err, rel_err_channel, relmse
+
+pytestmark = pytest.mark.gpu
+
+# Bounds of the 16-bit state formats against the oracle (per-pixel metric of the parity gate,
+# helpers.rel_err), measured on the sequences below with margin: the mean over pixels and
+# frames, and the worst pixel. BF16 keeps 8 significant bits (relative rounding 2^-9), FP16 11.
+BOUND_16 = {W.WRLS_STATE_BF16: {"mean": 2e-3, "max": 0.5}, W.WRLS_STATE_F16: {"mean": 5e-4, "max": 0.2}}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2106_08034_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    W.lib()
+
+
+def per_pixel_err(gpu, ref):
+    """Per-pixel relative error field (H, W) of the parity metric."""
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return np.max(np.abs(gpu - ref), axis=0) / np.maximum(np.max(np.abs(ref), axis=0), FLOOR)
+
+
+@pytest.mark.parametrize("precision", [W.WRLS_STATE_BF16, W.WRLS_STATE_F16])
+def test_16bit_state_gate_without_fireflies(precision):
+    """320x180, 120 frames, orbit, transfer-function edit at frame 60, light move at frame 90,
+    no fireflies (relMSE ~ 1e-2, so that 1 % of it is a real bound)."""
+    spec = synth.SceneSpec(320, 180, 120, seed=81, motion="orbit", firefly_frac=0.0,
+                           tf_edit_frame=60, light_move_frame=90)
+    fr = cpu_frames(spec)
+    st = O.OracleStream(spec.width, spec.height, oracle_params_from(W.wrls_params_default()))
+    streams = {p: W.Stream(spec.width, spec.height, W.wrls_params_default(state_precision=p))
+               for p in (W.WRLS_STATE_F32, precision)}
+    outs = {p: torch.empty(3, spec.height, spec.width, device="cuda") for p in streams}
+    rm = {p: [] for p in streams}
+    errs = {p: [] for p in streams}
+    for f in fr:
+        for p, s in streams.items():
+            s.denoise(f["radiance"].cuda(), f["motion"].cuda(), outs[p])
+        ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
+        for p in streams:
+            o = outs[p].cpu().numpy()
+            rm[p].append(relmse(o, f["truth"].numpy()))
+            errs[p].append(per_pixel_err(o, ref))
+    for s in streams.values():
+        W.wrls_stream_check(s.handle)
+        s.close()
+    r32, r16 = float(np.mean(rm[W.WRLS_STATE_F32])), float(np.mean(rm[precision]))
+    e16 = np.stack(errs[precision])
+    print("relMSE f32 %.6f  16-bit %.6f  ratio %.5f;  16-bit vs oracle: mean %.3g  p99.9 %.3g  max %.3g;"
+          "  f32 vs oracle max %.3g" % (r32, r16, r16 / r32, e16.mean(), np.quantile(e16, 0.999), e16.max(),
+                                        np.max(errs[W.WRLS_STATE_F32])))
+    assert 0.003 < r32 < 0.1, "the firefly-free relMSE is what makes the 1 % gate sensitive"
+    assert r16 <= 1.01 * r32
+    assert np.max(errs[W.WRLS_STATE_F32]) <= REL_TOL
+    assert e16.mean() <= BOUND_16[precision]["mean"]
+    assert e16.max() <= BOUND_16[precision]["max"]
+
+
+@pytest.mark.parametrize("motion", ["static", "pan"])
+def test_long_run_against_the_oracle(motion):
+    """1200 frames at 128 x 128 with 5 % x50 fireflies: binary32 state within the parity bound
+    on every frame, trace(P) on the device within 1e-3 of the oracle's, BF16 state bounded.
+    Prints the worst error of each 100-frame block."""
+    T = 1200
+    spec = synth.SceneSpec(128, 128, 8, seed=82, motion=motion, firefly_frac=0.05)
+    sc = synth.Scene(spec)
+    p32 = W.wrls_params_default()
+    st = O.OracleStream(128, 128, oracle_params_from(p32))
+    s32 = W.Stream(128, 128, p32)
+    s16 = W.Stream(128, 128, W.wrls_params_default(state_precision=W.WRLS_STATE_BF16))
+    o32 = torch.empty(3, 128, 128, device="cuda")
+    o16 = torch.empty_like(o32)
+    block32, block32c, block16, traces = [], [], [], []
+    w32 = w32c = w16 = 0.0
+    sum16, n16 = 0.0, 0
+    for t in range(T):
+        f = sc.frame(t)
+        s32.denoise(f["radiance"].cuda(), f["motion"].cuda(), o32)
+        s16.denoise(f["radiance"].cuda(), f["motion"].cuda(), o16)
+        ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
+        e32 = rel_err(o32.cpu().numpy(), ref)
+        e32c = rel_err_channel(o32.cpu().numpy(), ref)
+        pe16 = per_pixel_err(o16.cpu().numpy(), ref)
+        w32, w32c, w16 = max(w32, e32), max(w32c, e32c), max(w16, float(pe16.max()))
+        sum16 += float(pe16.sum())
+        n16 += pe16.size
+        assert e32 <= REL_TOL, "frame %d: binary32 state error %.3g" % (t, e32)
+        if (t + 1) % 100 == 0:
+            g = W.wrls_stream_state_stats(s32.handle)
+            tr = np.trace(st.P, axis1=1, axis2=2)
+            traces.append((t + 1, g["p_trace_max"], float(tr.max())))
+            block32.append(w32)
+            block32c.append(w32c)
+            block16.append(w16)
+            assert abs(g["p_trace_max"] - tr.max()) <= 1e-3 * tr.max()
+            assert g["nonfinite"] == 0
+            w32 = w32c = w16 = 0.0
+    for s in (s32, s16):
+        W.wrls_stream_check(s.handle)
+        s.close()
+    print("%s: per 100 frames, worst error vs oracle  f32 %s  f32 per-channel %s  bf16 %s  (bf16 mean %.3g);"
+          "  trace(P) max device/oracle %s" % (
+              motion, ["%.2e" % e for e in block32], ["%.2e" % e for e in block32c], ["%.2e" % e for e in block16],
+              sum16 / n16, ["%d: %.4g/%.4g" % x for x in traces]))
+    assert sum16 / n16 <= BOUND_16[W.WRLS_STATE_BF16]["mean"]
+    assert max(block16) <= BOUND_16[W.WRLS_STATE_BF16]["max"]

@@ -1,13 +1,14 @@
 """The batched tick that allocates nothing (wrls_batch_tick_static), through the C ABI.
 
-Some callers cannot allocate device memory (a plugin inside a host application that owns
+Some callers cannot allocate device memory: a plugin inside a host application that owns
 the device memory budget, or a frame loop that cannot afford an allocation's implicit
-synchronisation). For them the library keeps the batched tick's work table and work
+synchronisation. For them the library keeps the batched tick's work table and work
 counters in a static device array instead of the cudaMalloc'ed buffers of wrls_batch_create.
-This test checks that entry point against the allocating one on two calls in a row, and
-that it rejects more frames than its static table holds. It is collected last so that a
-run stopping at the first failure has already run every other test; it passes alone in a
-fresh process as well.
+This test checks that entry point against the allocating one, bit for bit, on two calls in a
+row, with binary32 and BF16 state and with one stream large enough (at least 2^19 pixels)
+to run the two-wide blend configuration in the allocating tick; and that it rejects more
+frames than its static table holds. It is collected last so that a run stopping at the first
+failure has already run every other test; it passes alone in a fresh process as well.
 """
 import pytest
 import torch
@@ -15,11 +16,11 @@ import torch
 from paper_2106_08034_gb300 import synth
 from paper_2106_08034_gb300 import wrls as W
 
-from helpers import REL_TOL, cpu_frames, rel_err
+from helpers import cpu_frames
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(200, 120), (64, 48), (257, 129), (31, 7)]
+SIZES = [(200, 120), (64, 48), (1024, 520), (257, 129), (31, 7)]   # 1024 x 520 >= 2^19 pixels
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,13 +31,15 @@ def _built():
     W.lib()
 
 
-def test_static_tick_matches_allocating_tick_on_two_calls():
+@pytest.mark.parametrize("precision", [W.WRLS_STATE_F32, W.WRLS_STATE_BF16])
+def test_static_tick_matches_allocating_tick_on_two_calls(precision):
     specs = [synth.SceneSpec(w, h, 2, seed=60 + i, motion="orbit", firefly_frac=0.05)
              for i, (w, h) in enumerate(SIZES)]
     frames = [cpu_frames(sp) for sp in specs]
     cs = torch.cuda.Stream()
-    ref_streams = [W.Stream(w, h, cuda_stream=cs) for (w, h) in SIZES]
-    new_streams = [W.Stream(w, h, cuda_stream=cs) for (w, h) in SIZES]
+    p = W.wrls_params_default(state_precision=precision)
+    ref_streams = [W.Stream(w, h, p, cuda_stream=cs) for (w, h) in SIZES]
+    new_streams = [W.Stream(w, h, p, cuda_stream=cs) for (w, h) in SIZES]
     batch = W.wrls_batch_create(len(SIZES))
     W.wrls_batch_set_cuda_stream(batch, cs)
     try:
@@ -57,7 +60,7 @@ def test_static_tick_matches_allocating_tick_on_two_calls():
             cs.synchronize()
             for o_ref, o_new in zip(outs_ref, outs_new):
                 assert torch.isfinite(o_new).all()
-                assert rel_err(o_new.cpu().numpy(), o_ref.cpu().numpy()) <= REL_TOL
+                assert torch.equal(o_new, o_ref)
         for s in new_streams:
             W.wrls_stream_check(s.handle)
             assert W.wrls_stream_frames(s.handle) == 2
