@@ -43,11 +43,17 @@ typedef enum {
     WRLS_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
 } wrls_status;
 
-/* Storage format of the per-pixel state (computation is always binary32). */
+/* Storage format of the per-pixel state (computation is always binary32). The 16-bit formats
+ * store beta, z and the Cholesky factor of P / s (s a per-pixel power of two, P / s = L L^T,
+ * so the decoded P is positive semi-definite) as 16-bit values, two per 32-bit word, with the
+ * exponent of s in the last word (52 B). With the paper's forgetting factor a frame changes the
+ * state by about (1 - lambda) = 0.2 % relative, less than BF16's rounding step and a few of
+ * FP16's: over long static histories the 16-bit states lag the binary32 one (FP16 by about
+ * 1e-2 of the colour, BF16 by several 1e-2); see the precision tests. */
 typedef enum {
     WRLS_STATE_F32 = 0,   /* 25 binary32 values per pixel (100 B) */
-    WRLS_STATE_BF16 = 1,  /* 25 bfloat16 values + one binary32 P scale (54 B) */
-    WRLS_STATE_F16 = 2    /* 25 binary16 values + one binary32 P scale (54 B) */
+    WRLS_STATE_BF16 = 1,  /* 25 bfloat16 values, P as a scaled Cholesky factor (52 B) */
+    WRLS_STATE_F16 = 2    /* 25 binary16 values, P as a scaled Cholesky factor (52 B) */
 } wrls_state_precision;
 
 /*
@@ -219,7 +225,7 @@ wrls_status wrls_stream_read_state(wrls_stream* s, float* dst);
  * Load a per-pixel state (checkpoint / resume, session migration; not in the paper): `src`
  * (device, caller-owned, same planar layout and plane count as wrls_stream_read_state) becomes
  * the stream's current state, encoded in its format (the 16-bit formats round beta and z and
- * store P scaled by its largest diagonal entry, as the update does); the next frame reprojects
+ * store the Cholesky factor of P scaled by a power of two, as the update does); the next frame reprojects
  * from it instead of starting over. Asynchronous on the stream's CUDA stream; `src` may be
  * reused once that stream has passed this call. A state read from a stream with the same
  * size and parameters resumes it exactly with the binary32 format.
@@ -256,8 +262,8 @@ uint64_t wrls_stream_frames(const wrls_stream* s);
  * double-buffered (4, 6: the next window arrives while the current one is blended) or single
  * (5, 7: more CTAs per SM) (binary32 state, images of at least 40 x 20 pixels); 8: 16 rows,
  * 9: 8 rows, with each thread blending 2 adjacent columns x 2 rows from a TMA-filled window
- * (64-column tiles; images of at least 72 x 20 pixels; with a 16-bit state the planes are
- * copied as 16-bit values, decoded in shared memory, and need a row pitch of at least 80). All configurations give bitwise identical outputs. Requires one
+ * (64-column tiles; images of at least 72 x 20 pixels; with a 16-bit state the packed
+ * words are copied as they are and decoded in shared memory). All configurations give bitwise identical outputs. Requires one
  * denoised frame; `out` (device, 3 x H x W) is overwritten and ends up holding the current
  * frame's output. times_ms (optional, WRLS_BLEND_CONFIGS entries) receives the mean time per
  * launch (-1 for a configuration the state format does not offer) and *chosen (optional)

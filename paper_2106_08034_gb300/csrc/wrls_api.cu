@@ -25,20 +25,12 @@ void set_error(const char* fmt, ...) {
 
 static size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
-size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_stride,
-                         size_t* scale_offset_bytes, int nplanes) {
+size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_stride, int nplanes) {
   const size_t p = round_up((size_t)W, 32);
   const size_t ps = round_up(p * (size_t)H, 64);
-  const size_t elem = precision == 0 ? 4 : 2;
-  size_t bytes = ps * elem * (size_t)nplanes;
-  size_t scale_off = 0;
-  if (precision != 0) {
-    scale_off = round_up(bytes, 256);
-    bytes = scale_off + ps * sizeof(float);
-  }
+  const size_t bytes = ps * 4 * (size_t)copy_planes(precision, nplanes);
   if (pitch) *pitch = (int)p;
   if (plane_stride) *plane_stride = ps;
-  if (scale_offset_bytes) *scale_offset_bytes = scale_off;
   return round_up(bytes, 256);
 }
 
@@ -65,62 +57,44 @@ bool encode_stage_maps(StateDesc& d, const char** why) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) { *why = "cuTensorMapEncodeTiled is not available from the driver"; return false; }
   const bool f32 = d.precision == 0;
-  const cuuint64_t elem = f32 ? 4 : 2;
-  const cuuint64_t dims[3] = {(cuuint64_t)d.pitch, (cuuint64_t)d.H, (cuuint64_t)kNState};
-  const cuuint64_t strides[2] = {(cuuint64_t)d.pitch * elem, (cuuint64_t)d.plane_stride * elem};
-  const cuuint32_t box[3] = {(cuuint32_t)kStageW, (cuuint32_t)kStageH, (cuuint32_t)kNState};
+  const cuuint32_t np = (cuuint32_t)copy_planes(d.precision, kNState);
+  // 32-bit elements in every format (binary32 values or packed 16-bit pairs)
+  const cuuint64_t dims[3] = {(cuuint64_t)d.pitch, (cuuint64_t)d.H, (cuuint64_t)np};
+  const cuuint64_t strides[2] = {(cuuint64_t)d.pitch * 4, (cuuint64_t)d.plane_stride * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)kStageW, (cuuint32_t)kStageH, np};
   const cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(&d.maps.planes, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
-                   d.base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for the state planes"; return false; }
-  if (!f32) {
-    const cuuint64_t dims2[2] = {(cuuint64_t)d.pitch, (cuuint64_t)d.H};
-    const cuuint64_t strides2[1] = {(cuuint64_t)d.pitch * 4};
-    const cuuint32_t box2[2] = {(cuuint32_t)kStageW, (cuuint32_t)kStageH};
-    r = enc(&d.maps.scale, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.scale, dims2, strides2, box2, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for the P-scale plane"; return false; }
+  const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+  auto encode = [&](CUtensorMap* m, const cuuint32_t* bx) {
+    return enc(m, dt, 3, d.base, dims, strides, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  };
+  if (encode(&d.maps.planes, box) != CUDA_SUCCESS) {
+    *why = "cuTensorMapEncodeTiled failed for the state planes";
+    return false;
   }
   d.stage_ok = true;
-  if (f32 && d.H >= 20) {
-    const cuuint32_t bb16[3] = {(cuuint32_t)kBlendBoxW, 20, 12}, bz16[3] = {(cuuint32_t)kBlendBoxW, 20, 3};
-    const cuuint32_t bb8[3] = {(cuuint32_t)kBlendBoxW, 12, 12}, bz8[3] = {(cuuint32_t)kBlendBoxW, 12, 3};
+  if (d.H < 20) return true;
+  // blend windows: binary32 12 beta + 3 z planes; 16-bit formats 6 beta + 2 z word planes
+  const cuuint32_t nb = f32 ? 12 : 6, nz = f32 ? 3 : 2;
+  if (f32) {
+    const cuuint32_t bb16[3] = {(cuuint32_t)kBlendBoxW, 20, nb}, bz16[3] = {(cuuint32_t)kBlendBoxW, 20, nz};
+    const cuuint32_t bb8[3] = {(cuuint32_t)kBlendBoxW, 12, nb}, bz8[3] = {(cuuint32_t)kBlendBoxW, 12, nz};
     CUtensorMap* m[4] = {&d.bmaps.beta16, &d.bmaps.z16, &d.bmaps.beta8, &d.bmaps.z8};
     const cuuint32_t* bx[4] = {bb16, bz16, bb8, bz8};
-    for (int i = 0; i < 4; ++i) {
-      r = enc(m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, d.base, dims, strides, bx[i], es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for a blend window"; return false; }
-    }
+    for (int i = 0; i < 4; ++i)
+      if (encode(m[i], bx[i]) != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for a blend window"; return false; }
     d.blend_tma_ok = true;
-    if (d.pitch >= kBlendBoxW2) {
-      const cuuint32_t wb16[3] = {(cuuint32_t)kBlendBoxW2, 20, 12}, wz16[3] = {(cuuint32_t)kBlendBoxW2, 20, 3};
-      const cuuint32_t wb8[3] = {(cuuint32_t)kBlendBoxW2, 12, 12}, wz8[3] = {(cuuint32_t)kBlendBoxW2, 12, 3};
-      CUtensorMap* m2[4] = {&d.bmaps.beta16w, &d.bmaps.z16w, &d.bmaps.beta8w, &d.bmaps.z8w};
-      const cuuint32_t* bx2[4] = {wb16, wz16, wb8, wz8};
-      for (int i = 0; i < 4; ++i) {
-        r = enc(m2[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, d.base, dims, strides, bx2[i], es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for a two-wide blend window"; return false; }
-      }
-      d.blend_tma2_ok = true;
-    }
-  } else if (!f32 && d.H >= 20 && d.pitch >= kBlendBoxW2 + 8) {
-    // two-wide blend windows of the 16-bit planes: 80-column boxes from x - 8 (16 bytes)
-    const cuuint32_t w = (cuuint32_t)(kBlendBoxW2 + 8);
-    const cuuint32_t hb16[3] = {w, 20, 12}, hz16[3] = {w, 20, 3}, hb8[3] = {w, 12, 12}, hz8[3] = {w, 12, 3};
+  }
+  if (d.pitch >= kBlendBoxW2) {
+    const cuuint32_t wb16[3] = {(cuuint32_t)kBlendBoxW2, 20, nb}, wz16[3] = {(cuuint32_t)kBlendBoxW2, 20, nz};
+    const cuuint32_t wb8[3] = {(cuuint32_t)kBlendBoxW2, 12, nb}, wz8[3] = {(cuuint32_t)kBlendBoxW2, 12, nz};
     CUtensorMap* m2[4] = {&d.bmaps.beta16w, &d.bmaps.z16w, &d.bmaps.beta8w, &d.bmaps.z8w};
-    const cuuint32_t* bx2[4] = {hb16, hz16, hb8, hz8};
-    for (int i = 0; i < 4; ++i) {
-      r = enc(m2[i], CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, d.base, dims, strides, bx2[i], es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) { *why = "cuTensorMapEncodeTiled failed for a 16-bit two-wide blend window"; return false; }
-    }
+    const cuuint32_t* bx2[4] = {wb16, wz16, wb8, wz8};
+    for (int i = 0; i < 4; ++i)
+      if (encode(m2[i], bx2[i]) != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled failed for a two-wide blend window";
+        return false;
+      }
     d.blend_tma2_ok = true;
   }
   return true;
@@ -305,9 +279,9 @@ static wrls_status enqueue_blend(wrls_stream* s, const KParams& kp, const float*
 // the allocation or the tensor-map encoding fails, and the stream keeps two copies.
 static bool add_third_copy(wrls_stream* s) {
   int pitch;
-  size_t ps, scale_off;
+  size_t ps;
   const int nplanes = s->state[0].nplanes;
-  const size_t copy = state_copy_layout(s->W, s->H, s->prm.state_precision, &pitch, &ps, &scale_off, nplanes);
+  const size_t copy = state_copy_layout(s->W, s->H, s->prm.state_precision, &pitch, &ps, nplanes);
   void* mem = nullptr;
   if (cudaMalloc(&mem, copy) != cudaSuccess) {
     cudaGetLastError();
@@ -315,7 +289,6 @@ static bool add_third_copy(wrls_stream* s) {
   }
   StateDesc d = s->state[0];
   d.base = mem;
-  d.scale = s->prm.state_precision ? (float*)((char*)mem + scale_off) : nullptr;
   const char* why = "";
   if (!s->ext && !encode_stage_maps(d, &why)) {
     cudaFree(mem);
@@ -364,7 +337,7 @@ size_t wrls_state_bytes(int width, int height, const wrls_params* p) {
   if (!p || !dims_ok(width, height) || (unsigned)p->state_precision > 2u) return 0;
   if (p->struct_size != sizeof(wrls_params)) return 0;
   const int np = uses_ext(*p) ? ext_planes(ext_dim(*p)) : kNState;
-  return 2 * state_copy_layout(width, height, p->state_precision, nullptr, nullptr, nullptr, np);
+  return 2 * state_copy_layout(width, height, p->state_precision, nullptr, nullptr, np);
 }
 
 const char* wrls_last_error(void) { return g_err; }
@@ -381,11 +354,11 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
   const char* why = "";
   if (!make_kparams(*p, &kp, &why)) { set_error("wrls_stream_create: %s", why); return WRLS_ERR_INVALID_ARG; }
   int pitch;
-  size_t ps, scale_off;
+  size_t ps;
   const bool ext = uses_ext(*p);
   const int dim = ext ? ext_dim(*p) : 4;
   const int nplanes = ext ? ext_planes(dim) : kNState;
-  const size_t copy = state_copy_layout(width, height, p->state_precision, &pitch, &ps, &scale_off, nplanes);
+  const size_t copy = state_copy_layout(width, height, p->state_precision, &pitch, &ps, nplanes);
   wrls_stream* s = new (std::nothrow) wrls_stream();
   if (!s) { set_error("wrls_stream_create: host allocation failed"); return WRLS_ERR_OOM; }
   s->W = width;
@@ -421,7 +394,6 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
   for (int i = 0; i < 2; ++i) {
     StateDesc& d = s->state[i];
     d.base = (char*)s->mem + i * copy;
-    d.scale = p->state_precision ? (float*)((char*)d.base + scale_off) : nullptr;
     d.precision = p->state_precision;
     d.W = width;
     d.H = height;

@@ -34,9 +34,7 @@ struct alignas(128) FrameWork {
   StageMaps maps;    // TMA tensor maps of the previous state copy
   KParams kp;
   void* prev_base;
-  float* prev_scale;
   void* next_base;
-  float* next_scale;
   size_t plane_stride;
   const float* rad;
   const float* mot;
@@ -57,15 +55,15 @@ struct alignas(128) BatchHeader {
   int total_blend;
 };
 
-template <class SV> __device__ __forceinline__ SV make_view(void* base, float* scale, size_t ps, int pitch);
-template <> __device__ __forceinline__ StateF32 make_view<StateF32>(void* base, float*, size_t ps, int pitch) {
+template <class SV> __device__ __forceinline__ SV make_view(void* base, size_t ps, int pitch);
+template <> __device__ __forceinline__ StateF32 make_view<StateF32>(void* base, size_t ps, int pitch) {
   return StateF32{(float*)base, ps, pitch};
 }
-template <> __device__ __forceinline__ StateBF16 make_view<StateBF16>(void* base, float* scale, size_t ps, int pitch) {
-  return StateBF16{(__nv_bfloat16*)base, scale, ps, pitch};
+template <> __device__ __forceinline__ StateBF16 make_view<StateBF16>(void* base, size_t ps, int pitch) {
+  return StateBF16{(uint32_t*)base, ps, pitch};
 }
-template <> __device__ __forceinline__ StateF16 make_view<StateF16>(void* base, float* scale, size_t ps, int pitch) {
-  return StateF16{(__half*)base, scale, ps, pitch};
+template <> __device__ __forceinline__ StateF16 make_view<StateF16>(void* base, size_t ps, int pitch) {
+  return StateF16{(uint32_t*)base, ps, pitch};
 }
 
 // Claim the next work item of a list; returns its tile index within its frame (or -1 when
@@ -122,12 +120,9 @@ __global__ void __launch_bounds__(kTileThreads)
     const int lt = next_item<0>(hdr, fw, counters + 0, &s_item, &s_frame, &f);
     if (lt < 0) break;
     const FrameWork& w = fw[f];
-    if (threadIdx.x == 0 && w.stage_ok) {
-      acquire_tensormap(&w.maps.planes);
-      if constexpr (SV::kHasScale) acquire_tensormap(&w.maps.scale);
-    }
-    const SV prev = make_view<SV>(w.prev_base, w.prev_scale, w.plane_stride, w.pitch);
-    const SV next = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
+    if (threadIdx.x == 0 && w.stage_ok) acquire_tensormap(&w.maps.planes);
+    const SV prev = make_view<SV>(w.prev_base, w.plane_stride, w.pitch);
+    const SV next = make_view<SV>(w.next_base, w.plane_stride, w.pitch);
     if (!update_tile(sm, &bar, phase, w.err, w.kp, w.W, w.H, w.reset != 0, w.stage_ok != 0, prev, next,
                      &w.maps, w.rad, w.mot, (lt % w.tiles_x) * kTW, (lt / w.tiles_x) * kTH))
       return;
@@ -144,7 +139,7 @@ __global__ void __launch_bounds__(kTW * TH / R)
     const int lt = next_item<1>(hdr, fw, counters + 1, &s_item, &s_frame, &f);
     if (lt < 0) break;
     const FrameWork& w = fw[f];
-    const SV cur = make_view<SV>(w.next_base, w.next_scale, w.plane_stride, w.pitch);
+    const SV cur = make_view<SV>(w.next_base, w.plane_stride, w.pitch);
     blend_tile<SV, TH, R, MODE>(sm_blend, w.kp, w.W, w.H, cur, w.out, (lt % w.tiles_x) * kTW,
                                 (lt / w.tiles_x) * TH);
   }
@@ -556,9 +551,7 @@ extern "C" wrls_status wrls_batch_tick_static(const wrls_frame_io* frames, int n
     w.err = s->err;
     w.kp = s->kp;
     w.prev_base = pv.base;
-    w.prev_scale = pv.scale;
     w.next_base = nx.base;
-    w.next_scale = nx.scale;
     w.plane_stride = pv.plane_stride;
     w.rad = frames[i].radiance;
     w.mot = frames[i].motion;

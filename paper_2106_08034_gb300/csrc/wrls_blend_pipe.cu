@@ -543,60 +543,43 @@ static cudaError_t launch_tma2_cfg(const KParams& kp, const StateDesc& cur, floa
 
 // ---- two-wide variant for the 16-bit state formats ---------------------------------------
 //
-// The 12 beta and 3 z planes arrive as 16-bit values: one TMA box per plane group of 80
-// columns (x origin tile x - 8, a 16-byte boundary) x (TH + 4) rows, landing in the upper part
-// of the binary32 window buffer. A conversion pass then writes the binary32 window of the
-// binary32 kernel (72 columns from tile x - 4, 16 planes with -rk) in three groups of five
-// planes: each thread reads its raw values of a group into registers, a barrier, then writes
-// the decoded group. The raw planes sit at the end of the buffer, placed so that the binary32
-// planes of a group never overlap the raw planes of a later group (static_assert below): one
-// buffer serves both, and the kernel keeps the shared memory, hence the occupancy, of the
-// binary32 kernel. The blend is blend_compute_soa2_packed / blend_compute_soa2 on the decoded
-// values, so the outputs equal those of the other blend configurations for the same state.
+// The 16-bit state stores two planes per 32-bit word (State16: word k = planes 2k, 2k + 1), so
+// the blend's inputs are 8 word planes (beta: words 0-5; z: words 11-12) with the geometry of
+// the binary32 planes: the same 72-column boxes from tile x - 4 (one TMA box for the 6 beta
+// words, one for the 2 z words). They land in the upper half of the binary32 window buffer
+// (raw word plane k in binary32 plane slot 8 + k) and are decoded in place, in three phases
+// separated by barriers: raw words 0-3 into binary32 planes 0-7 (slots 8-11 are read, 0-7
+// written); raw words 4-5 into planes 8-11 (slots 12-13 read, 8-11 written: raw words 0-3 are
+// consumed); raw words 6-7 into z planes 12-14 and the -rk plane 15, read into registers before
+// a barrier since they are overwritten. The blend is blend_compute_soa2_packed /
+// blend_compute_soa2 on the decoded values, so the outputs equal those of the other blend
+// configurations for the same state, and the kernel keeps the binary32 kernel's shared memory
+// and occupancy.
 template <int TH>
 struct TmaBlend2hGeom {
   static constexpr int SH = TH + 2 * kMaxRadius;
-  static constexpr int PLANE = TmaBlend2Geom<TH>::PLANE;  // binary32 plane: SH x 72
-  static constexpr int RAWW = kBlendBoxW2 + 8;              // 16-bit values a raw row (80)
-  static constexpr int RAWPLANE = SH * RAWW;
-  static constexpr int BUF_BYTES = 16 * PLANE * 4;
-  static constexpr int RAW_OFF = (BUF_BYTES - 15 * RAWPLANE * 2) / 128 * 128;
-  static constexpr uint32_t kTx = 15u * RAWPLANE * 2u;
-  static constexpr int kSmemBytes = BUF_BYTES + 128;
-  static constexpr int kPairs = SH * (kBlendBoxW2 / 2);     // column pairs of the binary32 window
-  static_assert(RAW_OFF >= 10 * (4 * PLANE - 2 * RAWPLANE),
-                "binary32 planes of a group would overlap raw planes of a later group");
-  static_assert(RAW_OFF + 15 * RAWPLANE * 2 <= BUF_BYTES, "raw planes exceed the buffer");
-  static_assert((12 * RAWPLANE * 2) % 128 == 0, "z box destination not 128-byte aligned");
+  static constexpr int PLANE = TmaBlend2Geom<TH>::PLANE;  // one plane: SH x 72 32-bit values
+  static constexpr int RAW = 8 * PLANE;                    // first raw word plane (in values)
+  static constexpr uint32_t kTx = 8u * PLANE * 4u;
+  static constexpr int kSmemBytes = TmaBlend2Geom<TH>::kSmemBytes;
+  static constexpr int kPairs = SH * (kBlendBoxW2 / 2);   // column pairs of a window plane
+  static_assert((6 * PLANE * 4) % 128 == 0, "z box destination not 128-byte aligned");
 };
-
-template <typename T>
-__device__ __forceinline__ float2 unpack16x2(uint32_t u);
-template <>
-__device__ __forceinline__ float2 unpack16x2<__nv_bfloat16>(uint32_t u) {
-  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));  // exact
-}
-template <>
-__device__ __forceinline__ float2 unpack16x2<__half>(uint32_t u) {
-  __half2 h;
-  memcpy(&h, &u, sizeof(h));
-  return __half22float2(h);
-}
 
 template <int TH, int R, int MODE, typename T>
 __global__ void __launch_bounds__(kTW * TH / R, 65536 / 128 / (kTW * TH / R))
     k_blend_tma2h(const KParams kp, const int W, const int H, const __grid_constant__ BlendMaps maps,
                   float* __restrict__ out, int* err) {
   using G = TmaBlend2hGeom<TH>;
+  using SV = State16<T>;
   constexpr int NT = kTW * TH / R;
   constexpr int P = G::PLANE;
   constexpr int TW2 = 2 * kTW;
-  constexpr int NJ = (G::kPairs + NT - 1) / NT;  // column pairs a thread converts
+  constexpr int NJ = (G::kPairs + NT - 1) / NT;  // column pairs a thread decodes per plane
   constexpr int HW = kBlendBoxW2 / 2;             // column pairs a row
   extern __shared__ unsigned char dsmem[];
-  unsigned char* buf = align128(dsmem);
-  float* sm = reinterpret_cast<float*>(buf);
-  const uint32_t* raw = reinterpret_cast<const uint32_t*>(buf + G::RAW_OFF);  // two values a word
+  float* sm = reinterpret_cast<float*>(align128(dsmem));
+  const uint2* raw = reinterpret_cast<const uint2*>(sm + G::RAW);  // (column 2cp, 2cp + 1) words
   __shared__ alignas(8) uint64_t bar;
   const CUtensorMap* mb = TH == 16 ? &maps.beta16w : &maps.beta8w;
   const CUtensorMap* mz = TH == 16 ? &maps.z16w : &maps.z8w;
@@ -609,9 +592,8 @@ __global__ void __launch_bounds__(kTW * TH / R, 65536 / 128 / (kTW * TH / R))
   uint32_t ph = 0u;
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, G::kTx);
-    tma_load_3d(buf + G::RAW_OFF, mb, (tile % tiles_x) * TW2 - 8, (tile / tiles_x) * TH - 2, 0, &bar);
-    tma_load_3d(buf + G::RAW_OFF + 12 * G::RAWPLANE * 2, mz, (tile % tiles_x) * TW2 - 8, (tile / tiles_x) * TH - 2,
-                kZ, &bar);
+    tma_load_3d(sm + G::RAW, mb, (tile % tiles_x) * TW2 - 4, (tile / tiles_x) * TH - 2, 0, &bar);
+    tma_load_3d(sm + G::RAW + 6 * P, mz, (tile % tiles_x) * TW2 - 4, (tile / tiles_x) * TH - 2, 11, &bar);
   }
   for (;;) {
     const int next = tile + gridDim.x;
@@ -623,41 +605,65 @@ __global__ void __launch_bounds__(kTW * TH / R, 65536 / 128 / (kTW * TH / R))
     }
     ph ^= 1u;
     const int bx0 = (tile % tiles_x) * TW2, by0 = (tile / tiles_x) * TH;
+    // in-image flags of a column pair (window pixels outside the image become far records)
+    auto inside = [&](int j, bool& in0, bool& in1) {
+      const int row = j / HW, cp = j % HW;
+      const int gx = bx0 - 4 + 2 * cp, gy = by0 - 2 + row;
+      const bool rin = gy >= 0 && gy < H;
+      in0 = rin && gx >= 0 && gx < W;
+      in1 = rin && gx + 1 >= 0 && gx + 1 < W;
+    };
+    // beta words 0-5 -> binary32 planes 0-11 (phase 1: words 0-3, phase 2: words 4-5)
 #pragma unroll
-    for (int g = 0; g < 3; ++g) {
-      uint32_t v[NJ][5];
+    for (int ph2 = 0; ph2 < 2; ++ph2) {
 #pragma unroll
       for (int jj = 0; jj < NJ; ++jj) {
         const int j = threadIdx.x + jj * NT;
         if (j < G::kPairs) {
-          const int w = (j / HW) * (G::RAWW / 2) + j % HW + 2;  // raw columns 2cp+4, 2cp+5
+          bool in0, in1;
+          inside(j, in0, in1);
 #pragma unroll
-          for (int q = 0; q < 5; ++q) v[jj][q] = raw[(5 * g + q) * (G::RAWPLANE / 2) + w];
+          for (int k = ph2 * 4; k < (ph2 ? 6 : 4); ++k) {
+            const uint2 w = raw[(k * P) / 2 + j];
+            const float2 a = SV::unpack(w.x), b = SV::unpack(w.y);  // (plane 2k, 2k+1) of columns 0, 1
+            const float2 lo = make_float2(in0 ? a.x : 0.0f, in1 ? b.x : 0.0f);
+            const float2 hi = make_float2(in0 ? a.y : 0.0f, in1 ? b.y : 0.0f);
+            reinterpret_cast<float2*>(sm + (2 * k) * P)[j] = lo;
+            reinterpret_cast<float2*>(sm + (2 * k + 1) * P)[j] = hi;
+          }
         }
       }
-      __syncthreads();  // the group's raw values are read before its binary32 planes are written
+      __syncthreads();  // raw words of this phase read before the next phase overwrites them
+    }
+    // z words 6-7 (z0 z1 | z2 e) -> planes 12-14 and -rk (plane 15): read first, they are overwritten
+    {
+      uint2 zw[NJ][2];
 #pragma unroll
       for (int jj = 0; jj < NJ; ++jj) {
         const int j = threadIdx.x + jj * NT;
         if (j < G::kPairs) {
-          const int row = j / HW, cp = j % HW;
-          const int gx = bx0 - 4 + 2 * cp, gy = by0 - 2 + row;
-          const bool rin = gy >= 0 && gy < H;
-          const bool in0 = rin && gx >= 0 && gx < W, in1 = rin && gx + 1 >= 0 && gx + 1 < W;
-          float2 f[5];
+          zw[jj][0] = raw[(6 * P) / 2 + j];
+          zw[jj][1] = raw[(7 * P) / 2 + j];
+        }
+      }
+      __syncthreads();
 #pragma unroll
-          for (int q = 0; q < 5; ++q) {
-            const float far = (5 * g + q) < 12 ? 0.0f : kFarZ;
-            f[q] = unpack16x2<T>(v[jj][q]);
-            if (!in0) f[q].x = far;
-            if (!in1) f[q].y = far;
-            *reinterpret_cast<float2*>(sm + (5 * g + q) * P + row * kBlendBoxW2 + 2 * cp) = f[q];
-          }
-          if (g == 2) {
-            const float2 nr = make_float2(in0 ? -blend_rk(f[2].x, f[3].x, f[4].x, kp.eps, kp.range_k) : -0.0f,
-                                          in1 ? -blend_rk(f[2].y, f[3].y, f[4].y, kp.eps, kp.range_k) : -0.0f);
-            *reinterpret_cast<float2*>(sm + 15 * P + row * kBlendBoxW2 + 2 * cp) = nr;
-          }
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int j = threadIdx.x + jj * NT;
+        if (j < G::kPairs) {
+          bool in0, in1;
+          inside(j, in0, in1);
+          const float2 a01 = SV::unpack(zw[jj][0].x), b01 = SV::unpack(zw[jj][0].y);
+          const float a2 = SV::unpack(zw[jj][1].x).x, b2 = SV::unpack(zw[jj][1].y).x;
+          const float2 z0 = make_float2(in0 ? a01.x : kFarZ, in1 ? b01.x : kFarZ);
+          const float2 z1 = make_float2(in0 ? a01.y : kFarZ, in1 ? b01.y : kFarZ);
+          const float2 z2 = make_float2(in0 ? a2 : kFarZ, in1 ? b2 : kFarZ);
+          reinterpret_cast<float2*>(sm + 12 * P)[j] = z0;
+          reinterpret_cast<float2*>(sm + 13 * P)[j] = z1;
+          reinterpret_cast<float2*>(sm + 14 * P)[j] = z2;
+          reinterpret_cast<float2*>(sm + 15 * P)[j] =
+              make_float2(in0 ? -blend_rk(z0.x, z1.x, z2.x, kp.eps, kp.range_k) : -0.0f,
+                          in1 ? -blend_rk(z0.y, z1.y, z2.y, kp.eps, kp.range_k) : -0.0f);
         }
       }
     }
@@ -669,9 +675,8 @@ __global__ void __launch_bounds__(kTW * TH / R, 65536 / 128 / (kTW * TH / R))
     if (threadIdx.x == 0) {
       fence_proxy_async();
       mbar_expect_tx(&bar, G::kTx);
-      tma_load_3d(buf + G::RAW_OFF, mb, (next % tiles_x) * TW2 - 8, (next / tiles_x) * TH - 2, 0, &bar);
-      tma_load_3d(buf + G::RAW_OFF + 12 * G::RAWPLANE * 2, mz, (next % tiles_x) * TW2 - 8,
-                  (next / tiles_x) * TH - 2, kZ, &bar);
+      tma_load_3d(sm + G::RAW, mb, (next % tiles_x) * TW2 - 4, (next / tiles_x) * TH - 2, 0, &bar);
+      tma_load_3d(sm + G::RAW + 6 * P, mz, (next % tiles_x) * TW2 - 4, (next / tiles_x) * TH - 2, 11, &bar);
     }
     tile = next;
   }

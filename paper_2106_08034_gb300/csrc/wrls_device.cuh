@@ -111,15 +111,15 @@ constexpr int kStagePix = kStageW * kStageH;
 // WRLS_ERR_TIMEOUT through the stream's error word.
 constexpr long long kWaitLimit = 2000000000LL;
 
-// Tensor maps of one state copy: all planes as a 3-D tensor (x, y, plane) and, for the
-// 16-bit formats, the binary32 P-scale plane as a 2-D tensor.
+// Tensor map of one state copy: all planes as a 3-D tensor (x, y, plane) of 32-bit elements
+// (binary32 values, or the packed 16-bit pairs of the 16-bit formats).
 struct StageMaps {
   CUtensorMap planes;
-  CUtensorMap scale;
 };
 
-// Tensor maps of the blend windows of a binary32 state copy: the 12 beta planes and the 3 z
-// planes, boxes of kBlendBoxW columns x (TH + 4) rows, for blend tiles of TH = 16 and TH = 8.
+// Tensor maps of the blend windows of a state copy, boxes of kBlendBoxW (or kBlendBoxW2) columns
+// x (TH + 4) rows, for blend tiles of TH = 16 and TH = 8: binary32 state, the 12 beta planes and
+// the 3 z planes; 16-bit formats (two-wide boxes only), the 6 beta words and the 2 z words.
 constexpr int kBlendBoxW = 40;
 constexpr int kBlendBoxW2 = 72;  // two-wide blend tiles: 64 + 2 x 4 columns
 struct BlendMaps {
@@ -177,6 +177,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 // ---- state storage formats -------------------------------------------------------------
 // A view of one state copy: plane p of pixel (x, y) is at p * plane_stride + y * pitch + x.
+// Every format offers
+//   load(idx, v)          the 25 values, decoded (P with its scale applied)
+//   load_raw(idx, v, s)   the 25 values with P left unscaled, and the P scale s (value of P =
+//                         s * v[P]); the bilinear gather folds s into the tap weights
+//   load_beta_z(idx, b, z), store(idx, v), and the staged-window geometry of the update.
 
 struct StateF32 {
   float* base;
@@ -186,17 +191,15 @@ struct StateF32 {
 #pragma unroll
     for (int p = 0; p < kNState; ++p) v[p] = __ldg(base + p * plane_stride + idx);
   }
+  __device__ __forceinline__ void load_raw(size_t idx, float v[kNState], float& s) const {
+    load(idx, v);
+    s = 1.0f;
+  }
   __device__ __forceinline__ void load_beta_z(size_t idx, float b[12], float z[3]) const {
 #pragma unroll
     for (int p = 0; p < 12; ++p) b[p] = __ldg(base + p * plane_stride + idx);
 #pragma unroll
     for (int c = 0; c < 3; ++c) z[c] = __ldg(base + (kZ + c) * plane_stride + idx);
-  }
-  __device__ __forceinline__ void load_beta_z_l2(size_t idx, float b[12], float z[3]) const {
-#pragma unroll
-    for (int p = 0; p < 12; ++p) b[p] = __ldcg(base + p * plane_stride + idx);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) z[c] = __ldcg(base + (kZ + c) * plane_stride + idx);
   }
   // idx < 2^32: each plane's base is uniform over the warp and the pixel offset 32-bit
   __device__ __forceinline__ void store(size_t idx, const float v[kNState]) const {
@@ -205,87 +208,173 @@ struct StateF32 {
     for (int p = 0; p < kNState; ++p) (base + p * plane_stride)[i] = v[p];
   }
   // Staged window: [plane][kStageH][kStageW] binary32; box origin x multiple of 4 (16 B).
+  static constexpr int kPlanes = kNState;  // 32-bit planes of a copy
   static constexpr int kAlignX = 4;
-  static constexpr uint32_t kStageBytes = kNState * kStagePix * 4;
-  static constexpr uint32_t kTxBytes = kStageBytes;  // bytes the bulk copies deliver
-  static constexpr bool kHasScale = false;
-  static __device__ __forceinline__ void load_staged(const unsigned char* stage, int idx, float v[kNState]) {
+  static constexpr uint32_t kStageBytes = kPlanes * kStagePix * 4;
+  static constexpr uint32_t kTxBytes = kStageBytes;  // bytes the bulk copy delivers
+  static constexpr bool kScaled = false;
+  static __device__ __forceinline__ void load_staged(const unsigned char* stage, int idx, float v[kNState], float& s) {
     const float* f = (const float*)stage;
 #pragma unroll
     for (int p = 0; p < kNState; ++p) v[p] = f[p * kStagePix + idx];
+    s = 1.0f;
   }
 };
 
-// 16-bit storage: beta and z raw, P divided by a per-pixel binary32 scale s = max diag(P)
-// (plane 0 of `scale`), all arithmetic in binary32, round-to-nearest-even on store.
+// 16-bit storage in packed pairs. Word plane k (k = 0..11) holds the 16-bit values of slots
+// 2k (low half) and 2k + 1 (high half) of a pixel; word plane 12 holds z_2 in its low half and,
+// in its high half, the exponent e (16-bit two's complement, even) of the pixel's P scale
+// s = 2^e. Slots 0-11 are beta and 22-23 z_0, z_1, stored as they are; slots 12-21 hold the
+// Cholesky factor of P / s, P / s = L L^T with L lower triangular (l00, l10, l20, l30, l11,
+// l21, l31, l22, l32, l33 in the positions of P's upper triangle), so that the decoded P is
+// positive semi-definite whatever the rounding (a P rounded entry by entry to 16 bits loses its
+// definiteness when its eigenvalues spread more than the format's precision, after which the
+// recursion diverges). e = the even number in {f, f + 1} with f = floor(log2 max diag P) + 1,
+// clamped to [-126, 126], so |l_ij| <= 1 and scaling by s or 1/s is exact. Round to nearest
+// even on store (one cvt for two values), exact decode (BF16: a shift or a mask; FP16: the
+// conversion of a half2); all arithmetic binary32. 13 words = 52 bytes per pixel and copy.
 template <typename T>
 struct State16 {
-  T* base;
-  float* scale;
-  size_t plane_stride;
+  uint32_t* base;
+  size_t plane_stride;  // in words
   int pitch;
-  static __device__ __forceinline__ float to_f(T v);
-  static __device__ __forceinline__ T from_f(float v);
-  __device__ __forceinline__ void load(size_t idx, float v[kNState]) const {
-    const float s = __ldg(scale + idx);
+  static constexpr int kPlanes = 13;
+  static __device__ __forceinline__ float2 unpack(uint32_t u);          // (low, high) as binary32
+  static __device__ __forceinline__ uint32_t pack(float lo, float hi);  // round to nearest even
+  static __device__ __forceinline__ float scale_of(uint32_t w12) {      // 2^e from word 12
+    const int e = (int)(short)(w12 >> 16);
+    return __int_as_float((e + 127) << 23);
+  }
+  // P / s = L L^T from the factor in slots 12-21 (in place).
+  static __device__ __forceinline__ void chol_to_p(float v[kNState]) {
+    const float l00 = v[kP + 0], l10 = v[kP + 1], l20 = v[kP + 2], l30 = v[kP + 3];
+    const float l11 = v[kP + 4], l21 = v[kP + 5], l31 = v[kP + 6];
+    const float l22 = v[kP + 7], l32 = v[kP + 8], l33 = v[kP + 9];
+    v[kP + 0] = l00 * l00;
+    v[kP + 1] = l10 * l00;
+    v[kP + 2] = l20 * l00;
+    v[kP + 3] = l30 * l00;
+    v[kP + 4] = fmaf(l11, l11, l10 * l10);
+    v[kP + 5] = fmaf(l21, l11, l20 * l10);
+    v[kP + 6] = fmaf(l31, l11, l30 * l10);
+    v[kP + 7] = fmaf(l22, l22, fmaf(l21, l21, l20 * l20));
+    v[kP + 8] = fmaf(l32, l22, fmaf(l31, l21, l30 * l20));
+    v[kP + 9] = fmaf(l33, l33, fmaf(l32, l32, fmaf(l31, l31, l30 * l30)));
+  }
+  // Cholesky factor of the 4 x 4 P (upper triangle a[0..9]) in place; a pivot <= 0 (P
+  // singular in binary32 rounding, or an unused predictor entry) gives a zero column.
+  static __device__ __forceinline__ void p_to_chol(float a[10]) {
+    auto col = [](float piv, float& l, float& r) {
+      if (piv > 0.0f) {
+        r = rsqrtf(piv);
+        l = piv * r;
+      } else {
+        l = 0.0f;
+        r = 0.0f;
+      }
+    };
+    float l00, r0, l11, r1, l22, r2, l33, r3;
+    col(a[0], l00, r0);
+    const float l10 = a[1] * r0, l20 = a[2] * r0, l30 = a[3] * r0;
+    col(fmaf(-l10, l10, a[4]), l11, r1);
+    const float l21 = fmaf(-l20, l10, a[5]) * r1, l31 = fmaf(-l30, l10, a[6]) * r1;
+    col(fmaf(-l21, l21, fmaf(-l20, l20, a[7])), l22, r2);
+    const float l32 = fmaf(-l31, l21, fmaf(-l30, l20, a[8])) * r2;
+    col(fmaf(-l32, l32, fmaf(-l31, l31, fmaf(-l30, l30, a[9]))), l33, r3);
+    (void)r3;
+    a[0] = l00; a[1] = l10; a[2] = l20; a[3] = l30; a[4] = l11;
+    a[5] = l21; a[6] = l31; a[7] = l22; a[8] = l32; a[9] = l33;
+  }
+  static __device__ __forceinline__ void decode(const uint32_t w[kPlanes], float v[kNState], float& s) {
 #pragma unroll
-    for (int p = 0; p < kNState; ++p) {
-      float f = to_f(base[p * plane_stride + idx]);
-      v[p] = (p >= kP && p < kZ) ? f * s : f;
+    for (int k = 0; k < 12; ++k) {
+      const float2 f = unpack(w[k]);
+      v[2 * k] = f.x;
+      v[2 * k + 1] = f.y;
     }
+    v[24] = unpack(w[12]).x;
+    s = scale_of(w[12]);
+    chol_to_p(v);
+  }
+  __device__ __forceinline__ void load_raw(size_t idx, float v[kNState], float& s) const {
+    uint32_t w[kPlanes];
+#pragma unroll
+    for (int k = 0; k < kPlanes; ++k) w[k] = __ldg(base + k * plane_stride + idx);
+    decode(w, v, s);
+  }
+  __device__ __forceinline__ void load(size_t idx, float v[kNState]) const {
+    float s;
+    load_raw(idx, v, s);
+#pragma unroll
+    for (int p = kP; p < kZ; ++p) v[p] *= s;
   }
   __device__ __forceinline__ void load_beta_z(size_t idx, float b[12], float z[3]) const {
 #pragma unroll
-    for (int p = 0; p < 12; ++p) b[p] = to_f(base[p * plane_stride + idx]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) z[c] = to_f(base[(kZ + c) * plane_stride + idx]);
-  }
-  __device__ __forceinline__ void load_beta_z_l2(size_t idx, float b[12], float z[3]) const {
-    const unsigned short* u = (const unsigned short*)base;
-#pragma unroll
-    for (int p = 0; p < 12; ++p) b[p] = to_f(from_bits(__ldcg(u + p * plane_stride + idx)));
-#pragma unroll
-    for (int c = 0; c < 3; ++c) z[c] = to_f(from_bits(__ldcg(u + (kZ + c) * plane_stride + idx)));
-  }
-  static __device__ __forceinline__ T from_bits(unsigned short v);
-  // Staged window: [plane][kStageH][kStageW] 16-bit values, then (128-byte aligned) the
-  // [kStageH][kStageW] binary32 P scales; box origin x multiple of 8 (16 B).
-  static constexpr int kAlignX = 8;
-  static constexpr uint32_t kPlaneBytes = kNState * kStagePix * 2;
-  static constexpr uint32_t kScaleOffset = (kPlaneBytes + 127) / 128 * 128;
-  static constexpr uint32_t kStageBytes = kScaleOffset + kStagePix * 4;
-  static constexpr uint32_t kTxBytes = kPlaneBytes + kStagePix * 4;  // bytes the bulk copies deliver
-  static constexpr bool kHasScale = true;
-  static __device__ __forceinline__ void load_staged(const unsigned char* stage, int idx, float v[kNState]) {
-    const T* h = (const T*)stage;
-    const float s = ((const float*)(stage + kScaleOffset))[idx];
-#pragma unroll
-    for (int p = 0; p < kNState; ++p) {
-      const float f = to_f(h[p * kStagePix + idx]);
-      v[p] = (p >= kP && p < kZ) ? f * s : f;
+    for (int k = 0; k < 6; ++k) {
+      const float2 f = unpack(__ldg(base + k * plane_stride + idx));
+      b[2 * k] = f.x;
+      b[2 * k + 1] = f.y;
     }
+    const float2 z01 = unpack(__ldg(base + 11 * plane_stride + idx));
+    z[0] = z01.x;
+    z[1] = z01.y;
+    z[2] = unpack(__ldg(base + 12 * plane_stride + idx)).x;
   }
   __device__ __forceinline__ void store(size_t idx, const float v[kNState]) const {
-    float s = fmaxf(fmaxf(v[kP + 0], v[kP + 4]), fmaxf(v[kP + 7], v[kP + 9]));
-    if (!(s > 0.0f) || !isfinite(s)) s = 1.0f;
-    const float inv_s = 1.0f / s;
-    const uint32_t i = (uint32_t)idx;
-    scale[i] = s;
-#pragma unroll
-    for (int p = 0; p < kNState; ++p) {
-      float f = (p >= kP && p < kZ) ? v[p] * inv_s : v[p];
-      (base + p * plane_stride)[i] = from_f(f);
+    const float m = fmaxf(fmaxf(v[kP + 0], v[kP + 4]), fmaxf(v[kP + 7], v[kP + 9]));
+    int e = 0;
+    if (m > 0.0f && m <= 3.402823466e38f) {
+      const int f = ((__float_as_int(m) >> 23) & 0xff) - 126;  // m / 2^f in [0.5, 1) (normal m)
+      e = min(max(f + (f & 1), -126), 126);
     }
+    const float inv_s = __int_as_float((127 - e) << 23);
+    float a[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) a[q] = v[kP + q] * inv_s;
+    p_to_chol(a);
+    const uint32_t i = (uint32_t)idx;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const int p = 2 * k;
+      const float lo = (p >= kP && p < kZ) ? a[p - kP] : v[p];
+      const float hi = (p + 1 >= kP && p + 1 < kZ) ? a[p + 1 - kP] : v[p + 1];
+      (base + k * plane_stride)[i] = pack(lo, hi);
+    }
+    (base + 12 * plane_stride)[i] = (pack(v[24], 0.0f) & 0xffffu) | ((uint32_t)e << 16);
+  }
+  // Staged window: [word plane][kStageH][kStageW] 32-bit words; box origin x multiple of 4.
+  static constexpr int kAlignX = 4;
+  static constexpr uint32_t kStageBytes = kPlanes * kStagePix * 4;
+  static constexpr uint32_t kTxBytes = kStageBytes;
+  static constexpr bool kScaled = true;
+  static __device__ __forceinline__ void load_staged(const unsigned char* stage, int idx, float v[kNState], float& s) {
+    const uint32_t* u = (const uint32_t*)stage;
+    uint32_t w[kPlanes];
+#pragma unroll
+    for (int k = 0; k < kPlanes; ++k) w[k] = u[k * kStagePix + idx];
+    decode(w, v, s);
   }
 };
-template <> __device__ __forceinline__ float State16<__nv_bfloat16>::to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 State16<__nv_bfloat16>::from_f(float v) { return __float2bfloat16_rn(v); }
-template <> __device__ __forceinline__ float State16<__half>::to_f(__half v) { return __half2float(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 State16<__nv_bfloat16>::from_bits(unsigned short v) {
-  return __ushort_as_bfloat16(v);
+template <>
+__device__ __forceinline__ float2 State16<__nv_bfloat16>::unpack(uint32_t u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));  // exact
 }
-template <> __device__ __forceinline__ __half State16<__half>::from_bits(unsigned short v) { return __ushort_as_half(v); }
-template <> __device__ __forceinline__ __half State16<__half>::from_f(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ uint32_t State16<__nv_bfloat16>::pack(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <>
+__device__ __forceinline__ float2 State16<__half>::unpack(uint32_t u) {
+  __half2 h;
+  *reinterpret_cast<uint32_t*>(&h) = u;
+  return __half22float2(h);
+}
+template <>
+__device__ __forceinline__ uint32_t State16<__half>::pack(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
 
 using StateBF16 = State16<__nv_bfloat16>;
 using StateF16 = State16<__half>;
@@ -319,29 +408,42 @@ __device__ __forceinline__ void init_model(const KParams& kp, const float z[3], 
 // Bilinear interpolation of every state value from its four taps in a fixed rounding order,
 // st = ((w00 a + w10 b) + w01 c) + w11 d by fused multiply-adds; consecutive planes are taken in
 // packed pairs (same rounding per component). bilerp_top takes the taps (x0, y0), (x1, y0),
-// bilerp_bottom adds (x0, y1), (x1, y1).
-__device__ __forceinline__ void bilerp_top(float w00, float w10, const float a[kNState], const float b[kNState],
-                                           float st[kNState]) {
-  const float2 wa = make_float2(w00, w00), wb = make_float2(w10, w10);
+// bilerp_bottom adds (x0, y1), (x1, y1). The P planes take their own weights (the tap weight
+// times the tap's P scale, a power of two: the products are exact, so this equals scaling the
+// stored values first).
+__device__ __forceinline__ void bilerp_top(float w00, float w10, float q00, float q10, const float a[kNState],
+                                           const float b[kNState], float st[kNState]) {
 #pragma unroll
   for (int p = 0; p + 1 < kNState; p += 2) {
+    const bool isP = p >= kP && p < kZ;
+    const float2 wa = isP ? make_float2(q00, q00) : make_float2(w00, w00);
+    const float2 wb = isP ? make_float2(q10, q10) : make_float2(w10, w10);
     const float2 v = f2fma(wb, make_float2(b[p], b[p + 1]), f2mul(wa, make_float2(a[p], a[p + 1])));
     st[p] = v.x;
     st[p + 1] = v.y;
   }
   if (kNState % 2) st[kNState - 1] = fmaf(w10, b[kNState - 1], w00 * a[kNState - 1]);
 }
-__device__ __forceinline__ void bilerp_bottom(float w01, float w11, const float c[kNState], const float d[kNState],
-                                              float st[kNState]) {
-  const float2 wc = make_float2(w01, w01), wd = make_float2(w11, w11);
+__device__ __forceinline__ void bilerp_bottom(float w01, float w11, float q01, float q11, const float c[kNState],
+                                              const float d[kNState], float st[kNState]) {
 #pragma unroll
   for (int p = 0; p + 1 < kNState; p += 2) {
+    const bool isP = p >= kP && p < kZ;
+    const float2 wc = isP ? make_float2(q01, q01) : make_float2(w01, w01);
+    const float2 wd = isP ? make_float2(q11, q11) : make_float2(w11, w11);
     const float2 v = f2fma(wd, make_float2(d[p], d[p + 1]),
                            f2fma(wc, make_float2(c[p], c[p + 1]), make_float2(st[p], st[p + 1])));
     st[p] = v.x;
     st[p + 1] = v.y;
   }
   if (kNState % 2) st[kNState - 1] = fmaf(w11, d[kNState - 1], fmaf(w01, c[kNState - 1], st[kNState - 1]));
+}
+
+// P-plane weight of a tap: w times the tap's scale (binary32: the weight itself).
+template <class SV>
+__device__ __forceinline__ float scaled_weight(float w, float s) {
+  if constexpr (SV::kScaled) return w * s;
+  else return w;
 }
 
 // Bilinear fetch of the previous state at q = (qx, qy) (Sec. 5.3: models are reprojected,
@@ -354,13 +456,13 @@ __device__ __forceinline__ void gather_bilinear(const SV& prev, int W, int H, fl
   const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
   const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy);
   const float w01 = (1.0f - fx) * fy, w11 = fx * fy;
-  float a[kNState], b[kNState];
-  prev.load((size_t)y0 * prev.pitch + x0, a);
-  prev.load((size_t)y0 * prev.pitch + x1, b);
-  bilerp_top(w00, w10, a, b, st);
-  prev.load((size_t)y1 * prev.pitch + x0, a);
-  prev.load((size_t)y1 * prev.pitch + x1, b);
-  bilerp_bottom(w01, w11, a, b, st);
+  float a[kNState], b[kNState], sa, sb;
+  prev.load_raw((size_t)y0 * prev.pitch + x0, a, sa);
+  prev.load_raw((size_t)y0 * prev.pitch + x1, b, sb);
+  bilerp_top(w00, w10, scaled_weight<SV>(w00, sa), scaled_weight<SV>(w10, sb), a, b, st);
+  prev.load_raw((size_t)y1 * prev.pitch + x0, a, sa);
+  prev.load_raw((size_t)y1 * prev.pitch + x1, b, sb);
+  bilerp_bottom(w01, w11, scaled_weight<SV>(w01, sa), scaled_weight<SV>(w11, sb), a, b, st);
 }
 
 // Bilinear fetch from the staged window whose origin is (X0, Y0).
@@ -373,13 +475,13 @@ __device__ __forceinline__ void gather_bilinear_staged(const unsigned char* stag
   const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy);
   const float w01 = (1.0f - fx) * fy, w11 = fx * fy;
   const int r0 = (y0 - Y0) * kStageW, r1 = (y1 - Y0) * kStageW;
-  float a[kNState], b[kNState];
-  SV::load_staged(stage, r0 + x0 - X0, a);
-  SV::load_staged(stage, r0 + x1 - X0, b);
-  bilerp_top(w00, w10, a, b, st);
-  SV::load_staged(stage, r1 + x0 - X0, a);
-  SV::load_staged(stage, r1 + x1 - X0, b);
-  bilerp_bottom(w01, w11, a, b, st);
+  float a[kNState], b[kNState], sa, sb;
+  SV::load_staged(stage, r0 + x0 - X0, a, sa);
+  SV::load_staged(stage, r0 + x1 - X0, b, sb);
+  bilerp_top(w00, w10, scaled_weight<SV>(w00, sa), scaled_weight<SV>(w10, sb), a, b, st);
+  SV::load_staged(stage, r1 + x0 - X0, a, sa);
+  SV::load_staged(stage, r1 + x1 - X0, b, sb);
+  bilerp_bottom(w01, w11, scaled_weight<SV>(w01, sa), scaled_weight<SV>(w11, sb), a, b, st);
 }
 
 // Eq. 12 feature, Eq. 13 weight and the wRLS update (Eq. 8, 14, 9, 11) of one pixel.

@@ -11,30 +11,31 @@
 
 namespace wrls {
 
-// Geometry of one state copy in device memory. Planar: kNState planes of `elem` bytes
-// per value, each plane pitch x H values padded to a multiple of 64 values; for the
-// 16-bit formats one binary32 P-scale plane follows the 25 planes.
+// Geometry of one state copy in device memory. Planar: `nplanes` planes of 32-bit elements
+// (binary32 values: kNState, or the extended path's count; 16-bit formats: the 13 word
+// planes of packed pairs), each plane pitch x H elements padded to a multiple of 64.
 struct StateDesc {
   void* base = nullptr;
-  float* scale = nullptr;
   int precision = 0;
   int nplanes = kNState;
   int W = 0, H = 0, pitch = 0;
   size_t plane_stride = 0;  // in values
-  StageMaps maps{};          // TMA tensor maps of this copy (planes; P scales for 16-bit)
+  StageMaps maps{};          // TMA tensor map of this copy's planes
   bool stage_ok = false;     // maps encoded and the image is at least one staging box
-  BlendMaps bmaps{};         // TMA tensor maps of the blend windows (binary32 state)
+  BlendMaps bmaps{};         // TMA tensor maps of the blend windows
   bool blend_tma_ok = false; // 40-column blend maps encoded (binary32 state, image >= one box)
   bool blend_tma2_ok = false; // 72-column blend maps encoded
 
   StateF32 f32() const { return StateF32{(float*)base, plane_stride, pitch}; }
-  StateBF16 bf16() const { return StateBF16{(__nv_bfloat16*)base, scale, plane_stride, pitch}; }
-  StateF16 f16() const { return StateF16{(__half*)base, scale, plane_stride, pitch}; }
+  StateBF16 bf16() const { return StateBF16{(uint32_t*)base, plane_stride, pitch}; }
+  StateF16 f16() const { return StateF16{(uint32_t*)base, plane_stride, pitch}; }
 };
 
-// Bytes of one state copy of `nplanes` planes and its geometry.
-size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_stride,
-                         size_t* scale_offset_bytes, int nplanes = kNState);
+// 32-bit planes of one state copy: `nplanes` binary32 planes, or the 13 word planes of the
+// 16-bit formats.
+inline int copy_planes(int precision, int nplanes) { return precision == 0 ? nplanes : StateBF16::kPlanes; }
+// Bytes of one state copy and its geometry.
+size_t state_copy_layout(int W, int H, int precision, int* pitch, size_t* plane_stride, int nplanes = kNState);
 
 // ---- extended predictor and weights (wrls_ext.cu) ----
 // Kernel parameters of a stream whose predictor has G-buffer entries, that weights by the
@@ -69,8 +70,7 @@ bool encode_stage_maps(StateDesc& d, const char** why);
 // 4: 16x2, 5: 16x2, 6: 8x2, 7: 16x4 -- persistent, TMA-filled windows, double-buffered (4, 6)
 // or single (5, 7) (binary32 state, images of at least 40 x 20 pixels);
 // 8: 16 rows x 2 x 2, 9: 8 rows x 2 x 2 -- persistent, TMA-filled, each thread 2 columns x
-// 2 rows (any state format; images of at least 72 x 20 pixels, 16-bit formats a row pitch of
-// at least 80).
+// 2 rows (any state format; images of at least 72 x 20 pixels).
 constexpr int kBlendConfigs = 10;
 constexpr int kBlendSyncConfigs = 4;
 inline bool blend_config_ok(int cfg, int precision, bool tma_ok, bool tma2_ok) {

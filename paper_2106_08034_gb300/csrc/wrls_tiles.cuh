@@ -95,10 +95,7 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint64_t* bar, u
     if (fits) {
       fence_proxy_async();
       mbar_expect_tx(bar, SV::kTxBytes);
-      if (!kp.debug_withhold_copy) {
-        tma_load_3d(sm.stage, &maps->planes, X0, Y0, 0, bar);
-        if constexpr (SV::kHasScale) tma_load_2d(sm.stage + SV::kScaleOffset, &maps->scale, X0, Y0, bar);
-      }
+      if (!kp.debug_withhold_copy) tma_load_3d(sm.stage, &maps->planes, X0, Y0, 0, bar);
     }
   }
   // radiance tile with a 1-pixel halo; a missing sample (a non-finite channel) and a pixel
@@ -189,8 +186,7 @@ struct BlendGeom {
 };
 
 // Fill the shared window of the blend tile at (bx0, by0) from the state copy `cur`.
-// COHERENT: read through L2 only (the state was written by other CTAs of the same launch).
-template <class SV, int TH, int NT, bool COHERENT = false, int UNROLL = 4>
+template <class SV, int TH, int NT, int UNROLL = 4>
 __device__ __forceinline__ void blend_fill(float4* __restrict__ sb, float4* __restrict__ szr,
                                            const KParams& kp, const int W, const int H, const SV& cur,
                                            const int bx0, const int by0) {
@@ -201,8 +197,7 @@ __device__ __forceinline__ void blend_fill(float4* __restrict__ sb, float4* __re
     const int gx = bx0 - R0 + lx, gy = by0 - R0 + ly;
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
       float b[12], z[3];
-      if constexpr (COHERENT) cur.load_beta_z_l2((size_t)gy * cur.pitch + gx, b, z);
-      else cur.load_beta_z((size_t)gy * cur.pitch + gx, b, z);
+      cur.load_beta_z((size_t)gy * cur.pitch + gx, b, z);
       sb[3 * i + 0] = make_float4(b[0], b[1], b[2], b[3]);
       sb[3 * i + 1] = make_float4(b[4], b[5], b[6], b[7]);
       sb[3 * i + 2] = make_float4(b[8], b[9], b[10], b[11]);

@@ -310,6 +310,9 @@ def wrls_stream_autotune(stream: int, out, reps: int = 5):
     return [float(t) for t in times], int(chosen.value)
 
 
+WRLS_DEBUG_WITHHOLD_STAGE_COPY = 1
+
+
 def wrls_stream_set_debug(stream: int, flags: int) -> None:
     """Test hook: WRLS_DEBUG_WITHHOLD_STAGE_COPY makes the update kernel's bounded wait expire."""
     _check(lib().wrls_stream_set_debug(stream, int(flags)))

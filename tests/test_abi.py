@@ -52,7 +52,7 @@ def test_state_bytes(lib):
     assert b32 >= 2 * 25 * 4 * 1920 * 1080 and b32 < 2 * 25 * 4 * 1920 * 1088 + 4096
     p.state_precision = W.WRLS_STATE_BF16
     b16 = W.wrls_state_bytes(1920, 1080, p)
-    assert b16 >= 2 * 54 * 1920 * 1080 and b16 < 0.6 * b32
+    assert b16 >= 2 * 52 * 1920 * 1080 and b16 < 0.6 * b32
     assert W.wrls_state_bytes(0, 10, p) == 0 and W.wrls_state_bytes(10, 20000, p) == 0
 
 
