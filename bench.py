@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--no-inputs", action="store_true", help="skip the reconstruction / velocity leg")
     ap.add_argument("--no-vpt", action="store_true", help="skip the path tracer -> denoiser pipeline leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--coalesce-ms", type=float, default=2.0,
+                    help="serving: a tick waits for due frames this long while another is in flight")
     ap.add_argument("--batched-passes", type=int, default=3)
     ap.add_argument("--seq", action="store_true",
                     help="time only the sequence entry (with --overlap blend CTAs per SM)")
@@ -283,9 +285,11 @@ def small_stream_latency(torch, W, synth, dev, reps=200):
 
 
 def batched_leg(args, torch, W, synth, dev):
-    """16 concurrent streams of mixed sizes (mix16_60f), BF16 state, one graph-captured
-    persistent tick per frame index. Inputs: a ring of 8 generated frames per stream
-    (the kernels' work depends only on the resolution); 60 ticks per pass."""
+    """16 concurrent streams of mixed sizes (mix16_60f), 16-bit state (BF16, and FP16 beside
+    it), one CUDA graph launch per tick (each stream's update and blend kernels on four
+    parallel branches). Inputs: a ring of 8 generated frames per stream (the kernels' work
+    depends only on the resolution); 60 ticks per pass. The plain per-frame path on the same
+    workload is timed beside it (FP32 and 16-bit state)."""
     specs = synth.mix16_60f()
     ring = 8
     cs = torch.cuda.Stream(device=dev)
@@ -300,38 +304,43 @@ def batched_leg(args, torch, W, synth, dev):
             mot[t].copy_(f["motion"])
         data.append((rad, mot))
     torch.cuda.synchronize()
-    params = W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
-    streams = [W.Stream(sp.width, sp.height, params, cuda_stream=cs) for sp in specs]
     outs = [torch.empty(3, sp.height, sp.width, device=dev) for sp in specs]
-    batch = W.wrls_batch_create(len(specs))
-    W.wrls_batch_set_cuda_stream(batch, cs)
     px = sum(sp.width * sp.height for sp in specs)
-
-    def tick(t):
-        W.wrls_batch_tick(batch, [(streams[i].handle, data[i][0][t % ring], None, None,
-                                   data[i][1][t % ring], outs[i]) for i in range(len(specs))])
-    for t in range(8):
-        tick(t)
-    cs.synchronize()
-    big = max(range(len(specs)), key=lambda i: specs[i].width * specs[i].height)
-    times, cfg = W.wrls_stream_autotune(streams[big].handle, outs[big], reps=3)
     n_ticks = specs[0].frames * max(1, args.batched_passes)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_ticks)]
-    torch.cuda.synchronize()
-    for t in range(n_ticks):
-        ev[t][0].record(cs)
-        tick(t)
-        ev[t][1].record(cs)
-    ev[-1][1].synchronize()
-    total_ms = ev[0][0].elapsed_time(ev[-1][1])
-    per = sorted(a.elapsed_time(b) for a, b in ev)
-    for s in streams:
-        W.wrls_stream_check(s.handle)
-    W.wrls_batch_destroy(batch)
-    for s in streams:
-        s.close()
-    # the plain per-frame path on the same workload (FP32 state, and BF16 state for the cost
-    # of batching): every stream's frame through wrls_denoise_frame, stream after stream
+    peak = measured_peaks()[0]
+
+    def batched(prec):
+        params = W.wrls_params_default(state_precision=prec)
+        streams = [W.Stream(sp.width, sp.height, params, cuda_stream=cs) for sp in specs]
+        batch = W.wrls_batch_create(len(specs))
+        W.wrls_batch_set_cuda_stream(batch, cs)
+
+        def tick(t):
+            W.wrls_batch_tick(batch, [(streams[i].handle, data[i][0][t % ring], None, None,
+                                       data[i][1][t % ring], outs[i]) for i in range(len(specs))])
+        for t in range(8):
+            tick(t)
+        cs.synchronize()
+        big = max(range(len(specs)), key=lambda i: specs[i].width * specs[i].height)
+        times, cfg = W.wrls_stream_autotune(streams[big].handle, outs[big], reps=3)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_ticks)]
+        torch.cuda.synchronize()
+        for t in range(n_ticks):
+            ev[t][0].record(cs)
+            tick(t)
+            ev[t][1].record(cs)
+        ev[-1][1].synchronize()
+        total_ms = ev[0][0].elapsed_time(ev[-1][1])
+        per = sorted(a.elapsed_time(b) for a, b in ev)
+        for st in streams:
+            W.wrls_stream_check(st.handle)
+        W.wrls_batch_destroy(batch)
+        for st in streams:
+            st.close()
+        return total_ms, per, cfg
+
+    # the plain per-frame path on the same workload: every stream's frame through
+    # wrls_denoise_frame, stream after stream
     def per_frame_ms(prec):
         ps = [W.Stream(sp.width, sp.height, W.wrls_params_default(state_precision=prec), cuda_stream=cs)
               for sp in specs]
@@ -349,31 +358,42 @@ def batched_leg(args, torch, W, synth, dev):
             frame_tick(t)
         b.record(cs)
         b.synchronize()
-        for s in ps:
-            W.wrls_stream_check(s.handle)
-            s.close()
+        for st in ps:
+            W.wrls_stream_check(st.handle)
+            st.close()
         return a.elapsed_time(b)
+
+    def mpix(ms):
+        return round(n_ticks * px / (ms / 1e3) / 1e6, 1)
+
+    total_ms, per, cfg = batched(W.WRLS_STATE_BF16)
+    total16, per16, _ = batched(W.WRLS_STATE_F16)
     ms32 = per_frame_ms(W.WRLS_STATE_F32)
     ms16 = per_frame_ms(W.WRLS_STATE_BF16)
-    bytes_bf16 = BYTES_PATH_16
+
+    def pct(v, q):
+        return round(v[min(len(v) - 1, int(q * len(v)))], 4)
     return {
         "workload": ("mix16_60f: 16 streams (4x512^2, 4x1280x720, 4x1920x1080, 2x2560x1440, "
                      "2x3840x2160), orbit motion, 5%% fireflies; %d ticks of 16 frames" % n_ticks),
-        "value": round(n_ticks * px / (total_ms / 1e3) / 1e6, 1), "unit": "Mpix/s",
-        "state": "bf16 (+ binary32 P scale), binary32 compute", "mpix_per_tick": round(px / 1e6, 3),
-        "tick_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4),
-                    "max": round(per[-1], 4)},
+        "value": mpix(total_ms), "unit": "Mpix/s",
+        "state": "bf16 (packed pairs, P as a scaled Cholesky factor), binary32 compute",
+        "mpix_per_tick": round(px / 1e6, 3),
+        "tick_ms": {"p50": pct(per, 0.5), "p99": pct(per, 0.99), "max": round(per[-1], 4)},
         "frame_latency_note": "all 16 frames of a tick are released at its launch: frame latency = tick time",
-        "hbm_path_frac": round(bytes_bf16 * n_ticks * px / (total_ms / 1e3) / 1e9 / measured_peaks()[0], 4),
+        "hbm_path_frac": round(BYTES_PATH_16 * n_ticks * px / (total_ms / 1e3) / 1e9 / peak, 4),
+        "bytes_per_px": BYTES_PATH_16,
+        "f16_state": {"value": mpix(total16), "unit": "Mpix/s",
+                      "tick_ms": {"p50": pct(per16, 0.5), "p99": pct(per16, 0.99)},
+                      "hbm_path_frac": round(BYTES_PATH_16 * n_ticks * px / (total16 / 1e3) / 1e9 / peak, 4)},
         "blend_config_largest_stream": cfg, "launches_per_tick": 2 * len(specs),
         "tick_form": "one CUDA graph of each stream's update and blend kernels on 4 parallel branches",
         "plain_f32_per_frame_same_workload": {
-            "value": round(n_ticks * px / (ms32 / 1e3) / 1e6, 1), "unit": "Mpix/s",
-            "ms_per_tick": round(ms32 / n_ticks, 4),
+            "value": mpix(ms32), "unit": "Mpix/s", "ms_per_tick": round(ms32 / n_ticks, 4),
             "note": "the 16 frames of each tick through wrls_denoise_frame (FP32 state, default blend "
                     "configuration), stream after stream"},
-        "plain_bf16_per_frame_same_workload": {"value": round(n_ticks * px / (ms16 / 1e3) / 1e6, 1),
-                                               "unit": "Mpix/s", "ms_per_tick": round(ms16 / n_ticks, 4)},
+        "plain_bf16_per_frame_same_workload": {"value": mpix(ms16), "unit": "Mpix/s",
+                                               "ms_per_tick": round(ms16 / n_ticks, 4)},
     }
 
 
@@ -830,11 +850,19 @@ def run_wrls(args):
     serving = None
     if not args.no_serve:
         from paper_2106_08034_gb300 import serve
-        serving = serve.simulate(duration_s=args.serve_seconds, rate_budget_mpix_s="auto")
+        serving = serve.simulate(duration_s=args.serve_seconds, rate_budget_mpix_s="auto",
+                                 coalesce_s=args.coalesce_ms / 1e3)
         serving["workload"] = ("Poisson viewer sessions (2/s, lifetime U[10,60] s, 720p/1080p/1440p/2160p, "
                                "30-60 fps, <= 64 resident, BF16 state), warm-started at the stationary population; "
                                "admission by device memory and by a pixel-rate budget of 0.75 x the calibrated "
-                               "batched throughput")
+                               "batched throughput; a tick starts at once on an idle GPU, otherwise once the "
+                               "oldest due frame has waited coalesce_ms")
+        if args.coalesce_ms > 0:
+            base = serve.simulate(duration_s=min(args.serve_seconds, 5.0), rate_budget_mpix_s="auto",
+                                  coalesce_s=0.0, capacity_px_s=serving["calibrated_mpix_s"] * 1e6)
+            serving["without_coalescing"] = {k: base[k] for k in ("frames_per_tick", "mpix_per_s", "p50_ms", "p99_ms",
+                                                                  "gpu_busy_fraction", "mpix_per_gpu_s",
+                                                                  "missed_or_dropped", "duration_s")}
 
     small = small_stream_latency(torch, W, synth, dev)
     cpu = None

@@ -407,13 +407,13 @@ wrls_status wrls_stream_create(int width, int height, const wrls_params* p, wrls
       return WRLS_ERR_CUDA;
     }
   }
-  // Default blend configuration, from the measured ranking: the two-wide packed blend (9) for
-  // binary32 state on images of at least 2^19 pixels (some 1000 of its 64 x 8 tiles, several
-  // per SM); the one-CTA-per-tile 16 x 2 blend (2) for the 16-bit formats and small images,
-  // where one tile per CTA spreads the work over more SMs.
+  // Default blend configuration, from the measured ranking: on images of at least 2^19 pixels
+  // the two-wide packed blend, 64 x 8 tiles (9) for the binary32 state, 64 x 16 tiles (8) for
+  // the 16-bit formats (some 1000 tiles, several per SM); on smaller images the
+  // one-CTA-per-tile 16 x 2 blend (2), where one tile per CTA spreads the work over more SMs.
   if (!ext) {
     const bool big = (long long)width * height >= (1ll << 19);
-    s->blend_cfg = (p->state_precision == 0 && big && s->state[0].blend_tma2_ok) ? 9 : 2;
+    s->blend_cfg = (big && s->state[0].blend_tma2_ok) ? (p->state_precision == 0 ? 9 : 8) : 2;
   }
   *out = s;
   return WRLS_OK;

@@ -178,9 +178,9 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // ---- state storage formats -------------------------------------------------------------
 // A view of one state copy: plane p of pixel (x, y) is at p * plane_stride + y * pitch + x.
 // Every format offers
-//   load(idx, v)          the 25 values, decoded (P with its scale applied)
-//   load_raw(idx, v, s)   the 25 values with P left unscaled, and the P scale s (value of P =
-//                         s * v[P]); the bilinear gather folds s into the tap weights
+//   load(idx, v)          the 25 values, decoded (P itself)
+//   load_raw(idx, v, s)   the 25 values with P divided by a power-of-two scale s (binary32:
+//                         s = 1), which the bilinear gather folds into the tap weights
 //   load_beta_z(idx, b, z), store(idx, v), and the staged-window geometry of the update.
 
 struct StateF32 {
@@ -230,9 +230,13 @@ struct StateF32 {
 // positive semi-definite whatever the rounding (a P rounded entry by entry to 16 bits loses its
 // definiteness when its eigenvalues spread more than the format's precision, after which the
 // recursion diverges). e = the even number in {f, f + 1} with f = floor(log2 max diag P) + 1,
-// clamped to [-126, 126], so |l_ij| <= 1 and scaling by s or 1/s is exact. Round to nearest
-// even on store (one cvt for two values), exact decode (BF16: a shift or a mask; FP16: the
-// conversion of a half2); all arithmetic binary32. 13 words = 52 bytes per pixel and copy.
+// clamped to [-126, 126], so |l_ij| <= 1 and scaling by s = 2^e is exact. Each tap's P / s is
+// formed from its factor; its s is folded into the tap's bilinear weight, so the reprojection
+// interpolates P itself, as with the binary32 state (interpolating the factors instead, with
+// one L L^T per pixel, was measured to triple the error against the FP64 oracle under motion:
+// near restarts the taps' P differ by orders of magnitude). Round to nearest even on store (one
+// cvt for two values), exact decode (BF16: a shift or a mask; FP16: the conversion of a
+// half2); all arithmetic binary32. 13 words = 52 bytes per pixel and copy.
 template <typename T>
 struct State16 {
   uint32_t* base;
@@ -241,7 +245,7 @@ struct State16 {
   static constexpr int kPlanes = 13;
   static __device__ __forceinline__ float2 unpack(uint32_t u);          // (low, high) as binary32
   static __device__ __forceinline__ uint32_t pack(float lo, float hi);  // round to nearest even
-  static __device__ __forceinline__ float scale_of(uint32_t w12) {      // 2^e from word 12
+  static __device__ __forceinline__ float scale_of(uint32_t w12) {  // s = 2^e from word 12
     const int e = (int)(short)(w12 >> 16);
     return __int_as_float((e + 127) << 23);
   }
@@ -285,12 +289,13 @@ struct State16 {
     a[0] = l00; a[1] = l10; a[2] = l20; a[3] = l30; a[4] = l11;
     a[5] = l21; a[6] = l31; a[7] = l22; a[8] = l32; a[9] = l33;
   }
+  // beta, z and P / s (formed from the stored factor) in v; s.
   static __device__ __forceinline__ void decode(const uint32_t w[kPlanes], float v[kNState], float& s) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const float2 f = unpack(w[k]);
-      v[2 * k] = f.x;
-      v[2 * k + 1] = f.y;
+      const float2 u = unpack(w[k]);
+      v[2 * k] = u.x;
+      v[2 * k + 1] = u.y;
     }
     v[24] = unpack(w[12]).x;
     s = scale_of(w[12]);
@@ -408,9 +413,9 @@ __device__ __forceinline__ void init_model(const KParams& kp, const float z[3], 
 // Bilinear interpolation of every state value from its four taps in a fixed rounding order,
 // st = ((w00 a + w10 b) + w01 c) + w11 d by fused multiply-adds; consecutive planes are taken in
 // packed pairs (same rounding per component). bilerp_top takes the taps (x0, y0), (x1, y0),
-// bilerp_bottom adds (x0, y1), (x1, y1). The P planes take their own weights (the tap weight
-// times the tap's P scale, a power of two: the products are exact, so this equals scaling the
-// stored values first).
+// bilerp_bottom adds (x0, y1), (x1, y1). The P slots take their own weights: the tap weight
+// times the tap's scale, a power of two (the products are exact, so this equals scaling the
+// decoded values first).
 __device__ __forceinline__ void bilerp_top(float w00, float w10, float q00, float q10, const float a[kNState],
                                            const float b[kNState], float st[kNState]) {
 #pragma unroll
@@ -439,7 +444,7 @@ __device__ __forceinline__ void bilerp_bottom(float w01, float w11, float q01, f
   if (kNState % 2) st[kNState - 1] = fmaf(w11, d[kNState - 1], fmaf(w01, c[kNState - 1], st[kNState - 1]));
 }
 
-// P-plane weight of a tap: w times the tap's scale (binary32: the weight itself).
+// P-slot weight of a tap: w times the tap's scale (binary32: the weight itself).
 template <class SV>
 __device__ __forceinline__ float scaled_weight(float w, float s) {
   if constexpr (SV::kScaled) return w * s;

@@ -7,13 +7,17 @@ budget is set) the pixel rate of the admitted sessions plus its own width x heig
 stays within the rate budget -- a fraction of the throughput the GPU sustains, so that
 frames keep their deadline instead of queueing on the device; otherwise it waits in the
 queue until a departure frees room. Admitted sessions keep their state resident on the
-device across frames. Each round of the loop takes every session whose next frame is due,
-and denoises all of them with one ``wrls_batch_tick`` (one persistent, graph-captured
-launch pair over the (stream, tile) work list). Up to ``depth`` ticks are in flight, so
-sessions that arrive while others are on the GPU join the next tick and their work overlaps
-on the device. A frame's latency is the time from its release (its due time) to the
-completion of the tick that denoised it, observed on the host by polling the tick's CUDA
-event. If a session falls more than one frame behind, the older due frames are dropped.
+device across frames. A tick takes every session whose next frame is due and denoises all of
+them with one ``wrls_batch_tick``: one CUDA graph launch that holds each session's own
+update and blend kernels on four parallel branches, so that one session's blend runs beside
+another's update. Up to ``depth`` ticks are in flight. A tick starts at once when the GPU has
+nothing in flight; while a tick runs, due frames are coalesced and the next tick starts when
+the oldest of them has waited ``coalesce_s`` (or when no tick is in flight any more), so that
+busy periods run few, large ticks; sessions that arrive while others are on the GPU join the
+next tick and their work overlaps on the device. A frame's latency is the time from its
+release (its due time) to the completion of the tick that denoised it, observed on the host
+by polling the tick's CUDA event. If a session falls more than one frame behind, the older due
+frames are dropped.
 
 Inputs come from per-resolution rings of pre-generated frames on the device, read-only and
 shared by sessions of one resolution; session k's n-th processed frame is ring[n % len].
@@ -55,6 +59,7 @@ class Tick:
     event: torch.cuda.Event
     releases: List[Tuple[int, float]]   # (sid, release time) per frame
     pixels: int
+    start: Optional[torch.cuda.Event] = None
 
 
 class Server:
@@ -64,7 +69,7 @@ class Server:
                  params: Optional[W.wrls_params] = None, depth: int = 2, deadline_s: float = 1 / 60,
                  rings: Optional[Dict[Tuple[int, int], Tuple[torch.Tensor, torch.Tensor]]] = None,
                  cuda_stream: Optional[torch.cuda.Stream] = None, rate_budget_px_s: Optional[float] = None,
-                 device="cuda"):
+                 device="cuda", coalesce_s: float = 0.0):
         self.budget = int(hbm_budget_bytes)
         self.rate_budget = None if rate_budget_px_s is None else float(rate_budget_px_s)
         self.rate = 0.0              # pixel rate (px/s) of the admitted sessions
@@ -72,6 +77,7 @@ class Server:
         self.max_sessions = int(max_sessions)
         self.params = params if params is not None else W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
         self.depth = int(depth)
+        self.coalesce = float(coalesce_s)
         self.deadline = float(deadline_s)
         self.rings = rings if rings is not None else {}
         self.cs = cuda_stream if cuda_stream is not None else torch.cuda.Stream()
@@ -85,6 +91,8 @@ class Server:
         self.missed = 0
         self.frames_done = 0
         self.pixels_done = 0
+        self.gpu_ms = 0.0            # device time of the completed ticks (CUDA events)
+        self.ticks_done = 0
         self.admitted_total = 0
         self.max_concurrent = 0
         self.rejected_budget = 0
@@ -152,6 +160,15 @@ class Server:
             ready.append(s)
         return ready
 
+    def should_launch(self, ready: Sequence[Session], now: float) -> bool:
+        """Start a tick now? At once when nothing is in flight; otherwise (below `depth`) once
+        the oldest due frame has waited `coalesce_s`."""
+        if not ready or len(self.ticks) >= self.depth:
+            return False
+        if not self.ticks:
+            return True
+        return now - min(s.next_due for s in ready) >= self.coalesce
+
     def launch(self, ready: Sequence[Session]) -> None:
         io, rel, px = [], [], 0
         for s in ready:
@@ -162,10 +179,12 @@ class Server:
             px += s.width * s.height
             s.next_due += 1.0 / s.fps
             s.in_flight += 1
+        start = torch.cuda.Event(enable_timing=True)
+        start.record(self.cs)
         W.wrls_batch_tick(self.batch, io)
-        ev = torch.cuda.Event()
+        ev = torch.cuda.Event(enable_timing=True)
         ev.record(self.cs)
-        self.ticks.append(Tick(ev, rel, px))
+        self.ticks.append(Tick(ev, rel, px, start))
 
     def poll(self, now: float) -> None:
         done = [t for t in self.ticks if t.event.query()]
@@ -175,6 +194,9 @@ class Server:
         for t in done:
             self.ticks.remove(t)
             self.pixels_done += t.pixels
+            self.ticks_done += 1
+            if t.start is not None:
+                self.gpu_ms += t.start.elapsed_time(t.event)
             for sid, rel in t.releases:
                 lat = t_done - rel
                 self.latencies.append(lat)
@@ -254,7 +276,8 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
              resolutions=synth.SERVING_RESOLUTIONS, fps_range=(30.0, 60.0), max_sessions: int = 64,
              hbm_budget_bytes: Optional[int] = None, deadline_s: float = 1 / 60, depth: int = 2,
              seed: int = 5, warm_start: bool = True, params: Optional[W.wrls_params] = None,
-             rings=None, rate_budget_mpix_s=None, rate_fraction: float = 0.75) -> dict:
+             rings=None, rate_budget_mpix_s=None, rate_fraction: float = 0.75,
+             coalesce_s: float = 0.002, capacity_px_s: Optional[float] = None) -> dict:
     """Run the serving loop in real time for `duration_s`. Sessions arrive as a Poisson
     process; with warm_start the run starts from the stationary population (Poisson count
     with mean arrival_rate * mean lifetime, residual lifetimes uniform).
@@ -266,12 +289,13 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
     if hbm_budget_bytes is None:
         free, _ = torch.cuda.mem_get_info()
         hbm_budget_bytes = int(0.5 * free)
-    capacity = None
+    capacity = capacity_px_s
     if rate_budget_mpix_s == "auto":
-        capacity = calibrate_throughput(rings, params)
+        if capacity is None:
+            capacity = calibrate_throughput(rings, params)
         rate_budget_mpix_s = rate_fraction * capacity / 1e6
     srv = Server(hbm_budget_bytes, max_sessions=max_sessions, params=params, depth=depth,
-                 deadline_s=deadline_s, rings=rings,
+                 deadline_s=deadline_s, rings=rings, coalesce_s=coalesce_s,
                  rate_budget_px_s=None if rate_budget_mpix_s is None else rate_budget_mpix_s * 1e6)
     t0 = time.perf_counter()
     sid = 0
@@ -316,7 +340,7 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
             srv.poll(now)
             if len(srv.ticks) < srv.depth:
                 ready = srv.due_frames(now)
-                if ready:
+                if srv.should_launch(ready, now):
                     srv.launch(ready)
                     rounds += 1
         srv.cs.synchronize()
@@ -328,7 +352,11 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
         return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] * 1e3 if lat else None
     res = {
         "duration_s": round(wall, 3), "frames": srv.frames_done, "ticks": rounds,
+        "frames_per_tick": round(srv.frames_done / max(srv.ticks_done, 1), 2),
+        "coalesce_ms": round(coalesce_s * 1e3, 3), "depth": depth,
         "mpix_per_s": round(srv.pixels_done / wall / 1e6, 2),
+        "gpu_busy_fraction": round(srv.gpu_ms / 1e3 / wall, 4),
+        "mpix_per_gpu_s": round(srv.pixels_done / max(srv.gpu_ms / 1e3, 1e-9) / 1e6, 1),
         "p50_ms": round(pct(0.50), 3) if lat else None, "p99_ms": round(pct(0.99), 3) if lat else None,
         "deadline_ms": round(deadline_s * 1e3, 2),
         "missed_or_dropped": srv.missed, "admitted": srv.admitted_total,
