@@ -45,7 +45,7 @@ BYTES_PATH_16 = 136      # + out 12
 # capture is taken again. Writes still held in L2 when the kernel ends are not counted.
 KERNEL_SOURCES = {"k_update<StateF32>": ("wrls_frame.cu", "wrls_tiles.cuh", "wrls_device.cuh")}
 TRAFFIC_CAPTURES = {
-    "k_update<StateF32>": {"bytes": 248864768 + 168868352, "sources_sha256_16": "",
+    "k_update<StateF32>": {"bytes": 248868864 + 168551936, "sources_sha256_16": "258d46fc8a034a6f",
                            "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
                                       "-k regex:k_update -s 8 -c 2, bench.py --frames 8 --steps 1 --state f32"},
 }
@@ -857,12 +857,19 @@ def run_wrls(args):
                                "admission by device memory and by a pixel-rate budget of 0.75 x the calibrated "
                                "batched throughput; a tick starts at once on an idle GPU, otherwise once the "
                                "oldest due frame has waited coalesce_ms")
+        keys = ("frames_per_tick", "mpix_per_s", "p50_ms", "p99_ms", "gpu_busy_fraction", "mpix_per_gpu_s",
+                "missed_or_dropped", "admitted", "max_concurrent", "duration_s")
+        cap = serving["calibrated_mpix_s"] * 1e6
         if args.coalesce_ms > 0:
             base = serve.simulate(duration_s=min(args.serve_seconds, 5.0), rate_budget_mpix_s="auto",
-                                  coalesce_s=0.0, capacity_px_s=serving["calibrated_mpix_s"] * 1e6)
-            serving["without_coalescing"] = {k: base[k] for k in ("frames_per_tick", "mpix_per_s", "p50_ms", "p99_ms",
-                                                                  "gpu_busy_fraction", "mpix_per_gpu_s",
-                                                                  "missed_or_dropped", "duration_s")}
+                                  coalesce_s=0.0, capacity_px_s=cap)
+            serving["without_coalescing"] = {k: base[k] for k in keys}
+        # near capacity: twice the arrival rate, up to 128 resident sessions, rate budget 0.95 x
+        stress = serve.simulate(duration_s=min(args.serve_seconds, 5.0), arrival_rate=4.0, max_sessions=128,
+                                rate_budget_mpix_s="auto", rate_fraction=0.95, capacity_px_s=cap,
+                                coalesce_s=args.coalesce_ms / 1e3)
+        serving["near_capacity"] = {"workload": "Poisson 4/s, <= 128 resident, rate budget 0.95 x calibrated",
+                                    **{k: stress[k] for k in keys}}
 
     small = small_stream_latency(torch, W, synth, dev)
     cpu = None

@@ -147,3 +147,62 @@ def test_long_run_against_the_oracle(motion):
     for p in (W.WRLS_STATE_BF16, W.WRLS_STATE_F16):
         assert max(means[p]) <= LONG_16[p]["mean"], (names[p], means[p])
         assert max(worst[p]) <= LONG_16[p]["max"], (names[p], worst[p])
+
+
+@pytest.mark.parametrize("precision", [W.WRLS_STATE_BF16, W.WRLS_STATE_F16])
+def test_16bit_p_encoding_round_trip(precision):
+    """The 16-bit formats store P as the Cholesky factor of P / s, s a power of two: a state
+    written with wrls_stream_write_state and read back gives P within a few rounding steps of
+    the format relative to max diag P, positive semi-definite, over scales 1e-30 .. 1e30,
+    eigenvalue spreads up to 1e6, singular P (one predictor entry unused) and P = p0 I; beta and
+    z come back rounded to the format; a non-finite P stays non-finite (counted by the stats)."""
+    rng = np.random.default_rng(90)
+    Wd, Hd = 64, 32
+    n = Wd * Hd
+    st = np.zeros((25, n))
+    st[0:12] = rng.normal(0, 2, (12, n))
+    st[22:25] = rng.uniform(-3, 3, (3, n))
+    Ps = []
+    for j in range(n):
+        kind = j % 6
+        if kind == 5:
+            P = np.eye(4)                                    # a restarted pixel
+        else:
+            Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+            ev = 10.0 ** rng.uniform(-6 if kind < 3 else -2, 0, 4)
+            if kind == 4:
+                ev[3] = 0.0                                  # singular
+            P = (Q * ev) @ Q.T
+        P = P * 10.0 ** rng.uniform(-30, 30) if kind == 3 else P * 10.0 ** rng.uniform(-4, 4)
+        Ps.append(P)
+    iu = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
+    for q, (a, b) in enumerate(iu):
+        st[12 + q] = [P[a, b] for P in Ps]
+    src = torch.from_numpy(st.reshape(25, Hd, Wd).astype(np.float32)).cuda()
+    s = W.Stream(Wd, Hd, W.wrls_params_default(state_precision=precision))
+    s.write_state(src)
+    back = torch.empty_like(src)
+    s.read_state(back)
+    torch.cuda.synchronize()
+    got = back.double().cpu().numpy().reshape(25, n)
+    ref = src.double().cpu().numpy().reshape(25, n)   # the binary32 values that were written
+    step = 2.0 ** -8 if precision == W.WRLS_STATE_BF16 else 2.0 ** -11   # one rounding step
+    assert np.all(np.abs(got[0:12] - ref[0:12]) <= step * np.abs(ref[0:12]) + 1e-30)
+    assert np.all(np.abs(got[22:25] - ref[22:25]) <= step * np.abs(ref[22:25]) + 1e-30)
+    worst = 0.0
+    for j in range(n):
+        Pg = np.zeros((4, 4))
+        Pr = np.zeros((4, 4))
+        for q, (a, b) in enumerate(iu):
+            Pg[a, b] = Pg[b, a] = got[12 + q, j]
+            Pr[a, b] = Pr[b, a] = ref[12 + q, j]
+        m = np.max(np.diag(Pr))
+        worst = max(worst, np.max(np.abs(Pg - Pr)) / m)
+        assert np.min(np.linalg.eigvalsh(Pg)) >= -1e-6 * m, j     # positive semi-definite
+    print("worst |dP| / max diag P: %.3g (%.1f rounding steps)" % (worst, worst / step))
+    assert worst <= 8 * step
+    # a non-finite P entry stays non-finite and is counted
+    st[12 + 1, 0] = np.nan
+    s.write_state(torch.from_numpy(st.reshape(25, Hd, Wd).astype(np.float32)).cuda())
+    assert W.wrls_stream_state_stats(s.handle)["nonfinite"] > 0
+    s.close()
