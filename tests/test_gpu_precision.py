@@ -187,8 +187,9 @@ def test_16bit_p_encoding_round_trip(precision):
     got = back.double().cpu().numpy().reshape(25, n)
     ref = src.double().cpu().numpy().reshape(25, n)   # the binary32 values that were written
     step = 2.0 ** -8 if precision == W.WRLS_STATE_BF16 else 2.0 ** -11   # one rounding step
-    assert np.all(np.abs(got[0:12] - ref[0:12]) <= step * np.abs(ref[0:12]) + 1e-30)
-    assert np.all(np.abs(got[22:25] - ref[22:25]) <= step * np.abs(ref[22:25]) + 1e-30)
+    tiny = 0.0 if precision == W.WRLS_STATE_BF16 else 2.0 ** -25          # half FP16 subnormal step
+    assert np.all(np.abs(got[0:12] - ref[0:12]) <= step * np.abs(ref[0:12]) + tiny)
+    assert np.all(np.abs(got[22:25] - ref[22:25]) <= step * np.abs(ref[22:25]) + tiny)
     worst = 0.0
     for j in range(n):
         Pg = np.zeros((4, 4))
