@@ -63,3 +63,22 @@ def test_no_rate_budget_admits_by_memory_only(fake_gpu):
     for i in range(10):
         srv.request(serve.Session(i, 3840, 2160, 60.0, 0.0, 100.0), 0.0)
     assert len(srv.active) == 10 and srv.waited_rate == 0
+
+
+def test_tick_coalescing_rule(fake_gpu):
+    """A tick starts at once when nothing is in flight; while one is in flight, only once the
+    oldest due frame has waited coalesce_s; never beyond `depth` ticks in flight."""
+    srv = _server(max_sessions=8, depth=2, coalesce_s=0.002)
+    a = serve.Session(0, 640, 360, 60.0, 0.0, 100.0)
+    b = serve.Session(1, 640, 360, 60.0, 0.0, 100.0)
+    a.next_due, b.next_due = 1.000, 1.0015
+    assert not srv.should_launch([], 1.0)
+    assert srv.should_launch([a, b], 1.0016)                       # idle GPU: start at once
+    srv.ticks.append(serve.Tick(event=None, releases=[], pixels=0))
+    assert not srv.should_launch([a, b], 1.0016)                   # busy: oldest waited 1.6 ms
+    assert srv.should_launch([a, b], 1.0021)                       # busy: oldest waited 2.1 ms
+    srv.ticks.append(serve.Tick(event=None, releases=[], pixels=0))
+    assert not srv.should_launch([a, b], 1.0100)                   # depth reached
+    srv2 = _server(max_sessions=8, depth=2, coalesce_s=0.0)        # no coalescing window
+    srv2.ticks.append(serve.Tick(event=None, releases=[], pixels=0))
+    assert srv2.should_launch([a], 1.0)
