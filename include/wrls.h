@@ -53,7 +53,8 @@ typedef enum {
 typedef enum {
     WRLS_STATE_F32 = 0,   /* 25 binary32 values per pixel (100 B) */
     WRLS_STATE_BF16 = 1,  /* 25 bfloat16 values, P as a scaled Cholesky factor (52 B) */
-    WRLS_STATE_F16 = 2    /* 25 binary16 values, P as a scaled Cholesky factor (52 B) */
+    WRLS_STATE_F16 = 2    /* 25 binary16 values, P as a scaled Cholesky factor (52 B); beta and z
+                             (and so the radiance) must stay below 65504 in magnitude */
 } wrls_state_precision;
 
 /*

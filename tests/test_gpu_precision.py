@@ -36,7 +36,11 @@ BOUND_16 = {W.WRLS_STATE_BF16: {"mean": 3e-3, "max": 0.25}, W.WRLS_STATE_F16: {"
 # lag the binary32 one more the longer a pixel's history: a frame changes the state by about
 # (1 - lambda) = 0.2 % relative, less than BF16's rounding step (0.4 %) and a few of FP16's
 # steps, so part of each update rounds away.
-LONG_16 = {W.WRLS_STATE_BF16: {"mean": 0.08, "max": 12.0}, W.WRLS_STATE_F16: {"mean": 6e-3, "max": 1.5}}
+# relMSE against the truth over the last 300 frames within 1 % above the binary32 path's (measured
+# ratios: BF16 0.985 / 1.000 / 0.887, FP16 0.999 / 1.000 / 1.000 for static / pan / static without
+# fireflies; BF16's is lower on long static runs, where its rounded slopes of beta stay smaller).
+LONG_16 = {W.WRLS_STATE_BF16: {"mean": 0.08, "max": 12.0, "relmse_ratio": 1.01},
+           W.WRLS_STATE_F16: {"mean": 6e-3, "max": 1.5, "relmse_ratio": 1.01}}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -91,15 +95,16 @@ def test_16bit_state_gate_without_fireflies(precision, edits):
     assert e16.max() <= BOUND_16[precision]["max"]
 
 
-@pytest.mark.parametrize("motion", ["static", "pan"])
-def test_long_run_against_the_oracle(motion):
-    """1200 frames at 128 x 128 with 5 % x50 fireflies. Binary32 state: within the parity bound
+@pytest.mark.parametrize("motion,fireflies", [("static", 0.05), ("pan", 0.05), ("static", 0.0)])
+def test_long_run_against_the_oracle(motion, fireflies):
+    """1200 frames at 128 x 128 with 5 % x50 fireflies (and a firefly-free static run, where the
+    relMSE comparison with the truth is sensitive). Binary32 state: within the parity bound
     on every frame, trace(P) on the device within 1e-3 of the oracle's. 16-bit states: bounded
     (the static camera is their worst case: every frame changes the state by about 1 - lambda
     relative, below the 16-bit rounding step). Prints the worst and mean error of each
     100-frame block."""
     T = 1200
-    spec = synth.SceneSpec(128, 128, 8, seed=82, motion=motion, firefly_frac=0.05)
+    spec = synth.SceneSpec(128, 128, 8, seed=82, motion=motion, firefly_frac=fireflies)
     sc = synth.Scene(spec)
     p32 = W.wrls_params_default()
     st = O.OracleStream(128, 128, oracle_params_from(p32))
@@ -111,6 +116,7 @@ def test_long_run_against_the_oracle(motion):
     wc, traces = [], []
     bw = {p: 0.0 for p in precs}
     bs = {p: 0.0 for p in precs}
+    rm = {p: [] for p in precs}         # relMSE against the truth over the last 300 frames
     bwc = 0.0
     for t in range(T):
         f = sc.frame(t)
@@ -118,9 +124,12 @@ def test_long_run_against_the_oracle(motion):
             streams[p].denoise(f["radiance"].cuda(), f["motion"].cuda(), outs[p])
         ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
         for p in precs:
-            e = per_pixel_err(outs[p].cpu().numpy(), ref)
+            o = outs[p].cpu().numpy()
+            e = per_pixel_err(o, ref)
             bw[p] = max(bw[p], float(e.max()))
             bs[p] += float(e.mean())
+            if t >= T - 300:
+                rm[p].append(relmse(o, f["truth"].numpy()))
         bwc = max(bwc, rel_err_channel(outs[W.WRLS_STATE_F32].cpu().numpy(), ref))
         e32 = rel_err(outs[W.WRLS_STATE_F32].cpu().numpy(), ref)
         assert e32 <= REL_TOL, "frame %d: binary32 state error %.3g" % (t, e32)
@@ -140,13 +149,17 @@ def test_long_run_against_the_oracle(motion):
         W.wrls_stream_check(s.handle)
         s.close()
     names = {W.WRLS_STATE_F32: "f32", W.WRLS_STATE_BF16: "bf16", W.WRLS_STATE_F16: "f16"}
-    print("%s, per 100 frames: %s; f32 per-channel worst %s; trace(P) max device/oracle %s" % (
-        motion, "; ".join("%s worst %s mean %s" % (names[p], " ".join("%.2e" % e for e in worst[p]),
-                                                  " ".join("%.2e" % e for e in means[p])) for p in precs),
-        " ".join("%.2e" % e for e in wc), ["%d: %.4g/%.4g" % x for x in traces]))
+    r = {p: float(np.mean(rm[p])) for p in precs}
+    print("%s, fireflies %.2f, per 100 frames: %s; f32 per-channel worst %s; trace(P) max device/oracle %s; "
+          "relMSE vs truth (last 300 frames) %s" % (
+              motion, fireflies, "; ".join("%s worst %s mean %s" % (names[p], " ".join("%.2e" % e for e in worst[p]),
+                                                        " ".join("%.2e" % e for e in means[p])) for p in precs),
+              " ".join("%.2e" % e for e in wc), ["%d: %.4g/%.4g" % x for x in traces],
+              ", ".join("%s %.6f (x%.4f)" % (names[p], r[p], r[p] / r[W.WRLS_STATE_F32]) for p in precs)))
     for p in (W.WRLS_STATE_BF16, W.WRLS_STATE_F16):
         assert max(means[p]) <= LONG_16[p]["mean"], (names[p], means[p])
         assert max(worst[p]) <= LONG_16[p]["max"], (names[p], worst[p])
+        assert r[p] <= LONG_16[p]["relmse_ratio"] * r[W.WRLS_STATE_F32], (names[p], r)
 
 
 @pytest.mark.parametrize("precision", [W.WRLS_STATE_BF16, W.WRLS_STATE_F16])
