@@ -220,3 +220,47 @@ def test_16bit_p_encoding_round_trip(precision):
     s.write_state(torch.from_numpy(st.reshape(25, Hd, Wd).astype(np.float32)).cuda())
     assert W.wrls_stream_state_stats(s.handle)["nonfinite"] > 0
     s.close()
+
+
+@pytest.mark.parametrize("precision", [W.WRLS_STATE_BF16, W.WRLS_STATE_F16])
+@pytest.mark.parametrize("wh,kind", [((160, 96), "random"), ((33, 9), "orbit"), ((1, 37), "orbit")])
+def test_16bit_global_gather_and_small_images(precision, wh, kind):
+    """The 16-bit state where the update reads its taps from global memory (per-pixel random
+    motion of a few pixels spreads a tile's taps beyond the staged window; images smaller than
+    the window have none): finite outputs within the format's stated mean error of the binary32
+    path, and the sequence entry bitwise equal to per-frame calls."""
+    w, h = wh
+    spec = synth.SceneSpec(w, h, 8, seed=91, motion="static" if kind == "random" else "orbit",
+                           firefly_frac=0.05)
+    fr = cpu_frames(spec)
+    if kind == "random":
+        for t, f in enumerate(fr):
+            g = torch.Generator().manual_seed(300 + t)
+            f["motion"] = (torch.rand(2, h, w, generator=g) - 0.5) * 12.0
+    ins = [(f["radiance"].cuda(), f["motion"].cuda()) for f in fr]
+    s32 = W.Stream(w, h)
+    s16 = W.Stream(w, h, W.wrls_params_default(state_precision=precision))
+    o32 = torch.empty(3, h, w, device="cuda")
+    per = []
+    errs = []
+    for rad, mot in ins:
+        s32.denoise(rad, mot, o32)
+        o16 = torch.empty(3, h, w, device="cuda")
+        s16.denoise(rad, mot, o16)
+        per.append(o16)
+        errs.append(per_pixel_err(o16.cpu().numpy(), o32.cpu().numpy()))
+    for s in (s32, s16):
+        W.wrls_stream_check(s.handle)
+        s.close()
+    assert all(torch.isfinite(o).all() for o in per)
+    e = np.stack(errs)
+    print("%s %dx%d %s: mean %.3g max %.3g vs binary32" % ("bf16" if precision == 1 else "f16", w, h, kind,
+                                                            e.mean(), e.max()))
+    assert e.mean() <= BOUND_16[precision]["mean"]
+    sq = W.Stream(w, h, W.wrls_params_default(state_precision=precision))
+    seq = [torch.empty(3, h, w, device="cuda") for _ in ins]
+    W.wrls_denoise_sequence(sq.handle, [(rad, None, None, mot, seq[t]) for t, (rad, mot) in enumerate(ins)])
+    W.wrls_stream_check(sq.handle)
+    sq.close()
+    for a, b in zip(per, seq):
+        assert torch.equal(a, b)
