@@ -7,8 +7,12 @@
 
 namespace wrls {
 
+// With a 16-bit state the update is issue-bound and its staged window is half the binary32
+// one: 6 CTAs per SM (40 registers, a small spill) measured 70.6 us per 1080p frame against
+// 74.8 us at 4 CTAs per SM (64 registers), 71.7 us at 5. The binary32 update stays at 4 (its
+// shared memory allows no more).
 template <class SV>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, SV::kScaled ? 6 : 4)
     k_update(const KParams kp, const int W, const int H, const int reset, const int stage_ok,
              const SV prev, const SV next, const __grid_constant__ StageMaps maps,
              const float* __restrict__ rad, const float* __restrict__ mot, int* err) {
