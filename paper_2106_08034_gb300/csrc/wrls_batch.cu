@@ -107,7 +107,7 @@ __device__ __forceinline__ void acquire_tensormap(const CUtensorMap* m) {
 }
 
 template <class SV>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, SV::kScaled ? 6 : 5)  // as k_update
     k_batch_update(const BatchHeader* __restrict__ hdr, const FrameWork* __restrict__ fw, int* counters) {
   extern __shared__ unsigned char dsmem[];
   UpdateSmem<SV>& sm = *reinterpret_cast<UpdateSmem<SV>*>(align128(dsmem));

@@ -102,10 +102,12 @@ __device__ __forceinline__ float2 blend_exponent2(float2 sp, float2 e0, float2 e
 // ---- TMA / mbarrier helpers (inline PTX) ------------------------------------------------
 
 // Staged window of the previous state for one 32 x 8 update tile: kStageH rows x kStageW
-// columns of every plane (covers the tile's bilinear taps plus motion spread and the
-// 16-byte alignment of the box origin).
+// columns of every plane. It covers the tile's bilinear taps (33 x 9) with up to 3 columns for
+// the 16-byte alignment of the box origin, 4 columns and 1 row of motion spread across the
+// tile; a tile whose taps spread further reads them from global memory. 10 rows rather than 12
+// leave the binary32 update 44 KB of shared memory a CTA, 5 CTAs per SM.
 constexpr int kStageW = 40;
-constexpr int kStageH = 12;
+constexpr int kStageH = 10;
 constexpr int kStagePix = kStageW * kStageH;
 // Bounded waits give up after this many SM clocks (about one second) and report
 // WRLS_ERR_TIMEOUT through the stream's error word.

@@ -7,12 +7,13 @@
 
 namespace wrls {
 
-// With a 16-bit state the update is issue-bound and its staged window is half the binary32
-// one: 6 CTAs per SM (40 registers, a small spill) measured 70.6 us per 1080p frame against
-// 74.8 us at 4 CTAs per SM (64 registers), 71.7 us at 5. The binary32 update stays at 4 (its
-// shared memory allows no more).
+// CTAs per SM the update is compiled for (registers a thread <= 65536 / (256 x CTAs)), measured
+// at 1080p: with a 16-bit state (issue-bound, 24 KB of shared memory a CTA) 6 CTAs (40
+// registers, a small spill) took 70.6 us against 74.8 us at 4 (64 registers) and 71.7 at 5; 7
+// (32 registers) spilled and took 87.7. With the binary32 state (44 KB a CTA) 5 CTAs (48
+// registers) took 83.1 us against 88.0 at 4.
 template <class SV>
-__global__ void __launch_bounds__(kTileThreads, SV::kScaled ? 6 : 4)
+__global__ void __launch_bounds__(kTileThreads, SV::kScaled ? 6 : 5)
     k_update(const KParams kp, const int W, const int H, const int reset, const int stage_ok,
              const SV prev, const SV next, const __grid_constant__ StageMaps maps,
              const float* __restrict__ rad, const float* __restrict__ mot, int* err) {
