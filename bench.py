@@ -98,7 +98,7 @@ def parse():
     ap.add_argument("--batched-passes", type=int, default=3)
     ap.add_argument("--seq", action="store_true",
                     help="time only the sequence entry (with --overlap blend CTAs per SM)")
-    ap.add_argument("--overlap", type=int, default=1, help="blend CTAs per SM with --seq")
+    ap.add_argument("--overlap", type=int, default=3, help="blend CTAs per SM with --seq")
     ap.add_argument("--no-seq", action="store_true", help="do not try the sequence entry")
     ap.add_argument("--state", default="f32", choices=["f32", "bf16", "f16"],
                     help="state format of the main leg (the headline workload is f32; the others for profiling)")
@@ -728,14 +728,14 @@ def run_wrls(args):
     pipe_ms = {}
     if not args.seq:
         pipe_ms["frame"] = time_step()
-    seq_choices = [] if args.no_seq else ([args.overlap] if args.seq else [1, 2])
+    seq_choices = [] if args.no_seq else ([args.overlap] if args.seq else [2, 3])
     mode["seq"] = True
     for ov in seq_choices:
         W.wrls_stream_set_overlap(s.handle, ov)
         pipe_ms["seq/%d" % ov] = time_step()
     mode["seq"] = False
     best = min(pipe_ms, key=pipe_ms.get)
-    overlap = 2
+    overlap = 3
     if best.startswith("seq"):
         mode["seq"] = True
         overlap = int(best.split("/")[1])
