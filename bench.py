@@ -104,6 +104,9 @@ def parse():
                     help="state format of the main leg (the headline workload is f32; the others for profiling)")
     ap.add_argument("--blend-config", type=int, default=-1,
                     help="use this blend tile configuration instead of autotuning (profiling captures)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps of the main leg with cudaProfilerStart/Stop, so that "
+                         "ncu --replay-mode app-range measures them as they run (kernels overlapping)")
     return ap.parse_args()
 
 
@@ -749,11 +752,15 @@ def run_wrls(args):
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if args.profile_range:
+        torch.cuda.profiler.start()
     e0.record(cs)
     for _ in range(args.steps):
         step()
     e1.record(cs)
     e1.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     ck = clocks.stop()
     if world > 1:
         dist.barrier()
