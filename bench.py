@@ -718,15 +718,18 @@ def run_wrls(args):
     else:
         blend_times, blend_cfg = W.wrls_stream_autotune(s.handle, out, reps=5)
 
-    def time_step():
+    def time_step():  # one untimed step, then the faster of two timed ones
         step()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(cs)
-        step()
-        b.record(cs)
-        b.synchronize()
-        return a.elapsed_time(b) / T
+        best_ms = float("inf")
+        for _ in range(2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(cs)
+            step()
+            b.record(cs)
+            b.synchronize()
+            best_ms = min(best_ms, a.elapsed_time(b))
+        return best_ms / T
 
     pipe_ms = {}
     if not args.seq:
