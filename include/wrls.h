@@ -285,14 +285,20 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
 wrls_status wrls_stream_set_blend_config(wrls_stream* s, int config);
 
 /*
- * Test hook for the failure path of the bounded device-side waits (not in the paper). With
- * WRLS_DEBUG_WITHHOLD_STAGE_COPY set, the update kernel arms the
- * mbarrier of each tile's state-window copy but does not issue the copy, so the tile's
- * bounded wait runs out (about one second of SM clocks); the kernel then records
- * WRLS_ERR_TIMEOUT in the stream's error word (read by wrls_stream_check) and returns. The
- * frame's output and state are unreliable; the CUDA context stays usable. 0 clears it.
+ * Test hooks (not in the paper); `flags` replaces the previous set, 0 clears them.
+ * WRLS_DEBUG_WITHHOLD_STAGE_COPY: the failure path of the bounded device-side waits. The
+ * update kernel arms the mbarrier of each tile's state-window copy but does not issue the
+ * copy, so the tile's bounded wait runs out (about one second of SM clocks); the kernel then
+ * records WRLS_ERR_TIMEOUT in the stream's error word (read by wrls_stream_check) and
+ * returns. The frame's output and state are unreliable; the CUDA context stays usable.
+ * WRLS_DEBUG_NO_THIRD_COPY: the sequence entries keep two state copies, as when the
+ * allocation of the third fails (the update of frame t+2 then waits for the blend of frame
+ * t). Takes effect if set before the stream's first wrls_denoise_sequence or
+ * wrls_denoise_sequence_host call; outputs are unchanged.
+ * Returns WRLS_ERR_INVALID_ARG for a NULL stream or an unknown flag.
  */
 #define WRLS_DEBUG_WITHHOLD_STAGE_COPY 1u
+#define WRLS_DEBUG_NO_THIRD_COPY 2u
 wrls_status wrls_stream_set_debug(wrls_stream* s, uint32_t flags);
 
 /* Not in the paper: synchronise the stream's CUDA stream and report device-side failures of the frames

@@ -550,7 +550,7 @@ static wrls_status sequence_setup(wrls_stream* s, const char* who) {
     set_error("%s: stream/event creation failed: %s", who, cudaGetErrorString(e));
     return WRLS_ERR_CUDA;
   }
-  add_third_copy(s);
+  if (!s->debug_two_copies) add_third_copy(s);  // on failure the stream keeps two copies
   return WRLS_OK;
 }
 
@@ -838,11 +838,12 @@ wrls_status wrls_stream_autotune(wrls_stream* s, float* out, int reps, float* ti
 }
 
 wrls_status wrls_stream_set_debug(wrls_stream* s, uint32_t flags) {
-  if (!s || (flags & ~WRLS_DEBUG_WITHHOLD_STAGE_COPY)) {
+  if (!s || (flags & ~(WRLS_DEBUG_WITHHOLD_STAGE_COPY | WRLS_DEBUG_NO_THIRD_COPY))) {
     set_error("wrls_stream_set_debug: bad stream or unknown flags 0x%x", flags);
     return WRLS_ERR_INVALID_ARG;
   }
   s->kp.debug_withhold_copy = (flags & WRLS_DEBUG_WITHHOLD_STAGE_COPY) ? 1 : 0;
+  s->debug_two_copies = (flags & WRLS_DEBUG_NO_THIRD_COPY) != 0;
   return WRLS_OK;
 }
 

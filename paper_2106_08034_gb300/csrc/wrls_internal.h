@@ -153,6 +153,7 @@ struct wrls_stream {
   cudaEvent_t ev_b[3] = {nullptr, nullptr, nullptr};  // blend of frame t done, by t % 3: the update of
                                                       // frame t + ncopies, which overwrites its copy, waits
   int overlap_ctas = 3;                // CTAs per SM of a persistent blend that overlaps an update
+  bool debug_two_copies = false;       // WRLS_DEBUG_NO_THIRD_COPY: sequence entries keep two copies
   // kernel tracing
   static constexpr int kTimingCap = 8192;
   cudaEvent_t* tev = nullptr;   // 4 events per recorded frame: update start/end, blend start/end

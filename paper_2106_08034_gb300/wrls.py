@@ -311,10 +311,13 @@ def wrls_stream_autotune(stream: int, out, reps: int = 5):
 
 
 WRLS_DEBUG_WITHHOLD_STAGE_COPY = 1
+WRLS_DEBUG_NO_THIRD_COPY = 2
 
 
 def wrls_stream_set_debug(stream: int, flags: int) -> None:
-    """Test hook: WRLS_DEBUG_WITHHOLD_STAGE_COPY makes the update kernel's bounded wait expire."""
+    """Test hooks: WRLS_DEBUG_WITHHOLD_STAGE_COPY makes the update kernel's bounded wait expire;
+    WRLS_DEBUG_NO_THIRD_COPY (before the first sequence call) keeps the sequence entries on
+    two state copies."""
     _check(lib().wrls_stream_set_debug(stream, int(flags)))
 
 

@@ -33,6 +33,9 @@ def test_header_constants_match_the_binding():
     src = open(os.path.join(ROOT, "include", "wrls.h")).read()
     m = re.search(r"#define\s+WRLS_STATIC_BATCH_MAX\s+(\d+)", src)
     assert m and int(m.group(1)) == W.STATIC_BATCH_MAX
+    for name in ("WRLS_DEBUG_WITHHOLD_STAGE_COPY", "WRLS_DEBUG_NO_THIRD_COPY"):
+        m = re.search(r"#define\s+%s\s+(\d+)u" % name, src)
+        assert m and int(m.group(1)) == getattr(W, name), name
 
 
 def test_every_declared_symbol_is_exported(lib):

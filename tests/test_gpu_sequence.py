@@ -43,9 +43,11 @@ def _per_frame(spec, p, ins, cfg=None):
     return [o.cpu() for o in outs]
 
 
-def _sequence(spec, p, ins, cfg=None, chunk=None, overlap=None, cs=None):
+def _sequence(spec, p, ins, cfg=None, chunk=None, overlap=None, cs=None, debug=0):
     rad, mot, var, feat, _ = ins
     s = W.Stream(spec.width, spec.height, p, cuda_stream=cs)
+    if debug:
+        W.wrls_stream_set_debug(s.handle, debug)
     if overlap is not None:
         W.wrls_stream_set_overlap(s.handle, overlap)
     outs = [torch.empty(3, spec.height, spec.width, device="cuda") for _ in range(spec.frames)]
@@ -73,6 +75,34 @@ def test_sequence_equals_per_frame(prec, cfg):
         got = _sequence(spec, p, ins, cfg, chunk, overlap)
         for t in range(spec.frames):
             assert torch.equal(got[t], ref[t]), (t, chunk, overlap)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sequence_with_two_state_copies_equals_per_frame(prec):
+    """The sequence entries' fallback when the third state copy cannot be allocated
+    (WRLS_DEBUG_NO_THIRD_COPY): the update of frame t+2 then waits for the blend of frame t,
+    which reads the copy it overwrites. Outputs are bitwise those of per-frame calls, for the
+    device entry (default two-wide blend of a 2^19-pixel image, several chunkings) and the host
+    entry."""
+    spec = synth.SceneSpec(1024, 520, 9, seed=68, motion="orbit", firefly_frac=0.05)
+    ins = _inputs(spec)
+    p = W.wrls_params_default(state_precision=prec)
+    ref = _per_frame(spec, p, ins)
+    for chunk, overlap in ((None, None), (4, 2), (1, None)):
+        got = _sequence(spec, p, ins, chunk=chunk, overlap=overlap, debug=W.WRLS_DEBUG_NO_THIRD_COPY)
+        for t in range(spec.frames):
+            assert torch.equal(got[t], ref[t]), (t, chunk, overlap)
+    fr = ins[4]
+    pin = [{k: f[k].pin_memory() for k in ("radiance", "motion")} for f in fr]
+    got = [torch.full((3, spec.height, spec.width), float("nan")).pin_memory() for _ in fr]
+    s = W.Stream(spec.width, spec.height, p)
+    W.wrls_stream_set_debug(s.handle, W.WRLS_DEBUG_NO_THIRD_COPY)
+    W.wrls_denoise_sequence_host(s.handle, [(pin[t]["radiance"], None, None, pin[t]["motion"], got[t])
+                                            for t in range(spec.frames)])
+    W.wrls_stream_check(s.handle)
+    s.close()
+    for t in range(spec.frames):
+        assert torch.equal(got[t], ref[t]), t
 
 
 def test_sequence_extended_path_equals_per_frame():
