@@ -280,21 +280,37 @@ def test_batch_tick_equals_each_stream_alone(precision):
 
 
 def test_full_size_pan_1080p_120_frames():
-    """The bench workload at full size: 1920x1080, 120 frames, pan 1.7 px/frame, 5%
-    fireflies; every pixel of every frame against the oracle."""
+    """The bench workload at full size (1920x1080, 120 frames, pan 1.7 px/frame, 5% fireflies)
+    in the launch configuration bench.py times: one wrls_denoise_sequence call over the 120
+    frames on a non-default CUDA stream, default blend configuration, 3 blend CTAs per SM.
+    Every pixel of every frame against the oracle; per-frame calls give the same bits."""
     spec = synth.pan_1080p_120f()
     sc = synth.Scene(spec)
+    T, H, Wd = spec.frames, spec.height, spec.width
     p = W.wrls_params_default()
-    s = W.Stream(spec.width, spec.height, p)
-    st = O.OracleStream(spec.width, spec.height, oracle_params_from(p))
-    out = torch.empty(3, spec.height, spec.width, device="cuda")
+    rad = torch.empty(T, 3, H, Wd, device="cuda")
+    mot = torch.empty(T, 2, H, Wd, device="cuda")
+    for t in range(T):
+        f = sc.frame(t)
+        rad[t].copy_(f["radiance"])
+        mot[t].copy_(f["motion"])
+    outs = torch.empty(T, 3, H, Wd, device="cuda")
+    seq = W.Stream(Wd, H, p, cuda_stream=torch.cuda.Stream())
+    W.wrls_stream_set_overlap(seq.handle, 3)
+    W.wrls_denoise_sequence(seq.handle, [(rad[t], None, None, mot[t], outs[t]) for t in range(T)])
+    W.wrls_stream_check(seq.handle)  # synchronises the stream's CUDA stream (joined with the blends)
+    seq.close()
+    pf = W.Stream(Wd, H, p)
+    st = O.OracleStream(Wd, H, oracle_params_from(p))
+    out = torch.empty(3, H, Wd, device="cuda")
     worst = worst_c = 0.0
     n_c = 0
-    for t in range(spec.frames):
-        f = sc.frame(t)
-        s.denoise(f["radiance"].cuda(), f["motion"].cuda(), out)
-        ref, _, _ = st.frame(f["radiance"].numpy(), f["motion"].numpy())
-        o = out.cpu().numpy()
+    for t in range(T):
+        pf.denoise(rad[t], mot[t], out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, outs[t]), t
+        ref, _, _ = st.frame(rad[t].cpu().numpy(), mot[t].cpu().numpy())
+        o = outs[t].cpu().numpy()
         e = rel_err(o, ref)
         worst = max(worst, e)
         # the per-channel form, reported beside the per-pixel gate
@@ -302,8 +318,10 @@ def test_full_size_pan_1080p_120_frames():
         worst_c = max(worst_c, float(ec.max()))
         n_c += int((ec.max(axis=0) > REL_TOL).sum())
         assert e <= REL_TOL, (t, e)
+    W.wrls_stream_check(pf.handle)
+    pf.close()
     print("full-size worst rel err: per pixel %.3g; per channel %.3g (%d of %d pixel-frames above %.0e)"
-          % (worst, worst_c, n_c, spec.width * spec.height * spec.frames, REL_TOL))
+          % (worst, worst_c, n_c, Wd * H * T, REL_TOL))
 
 
 def test_blend_configs_bitwise_identical_and_autotune():
