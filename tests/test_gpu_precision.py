@@ -157,6 +157,46 @@ def test_batched_mix_full_size_against_the_oracle(precision):
         assert e.max() <= b["max"]
 
 
+def test_orbit_edit_1080p_120_frames_every_format():
+    """The precision workload at full size (1920x1080, 120 frames, orbit, 5 % fireflies,
+    transfer-function edit at frame 60, light move at frame 90): every pixel of every frame of
+    the binary32, BF16 and FP16 state paths against the oracle, on the same inputs. The binary32
+    state meets the parity bound; the 16-bit states the bounds stated above for sequences with
+    fireflies (the 99.9th percentile as a count of pixel-frames above it)."""
+    spec = synth.orbit_edit_1080p_120f()
+    sc = synth.Scene(spec)
+    fmts = (W.WRLS_STATE_F32, W.WRLS_STATE_BF16, W.WRLS_STATE_F16)
+    streams = {p: W.Stream(spec.width, spec.height, W.wrls_params_default(state_precision=p)) for p in fmts}
+    outs = {p: torch.empty(3, spec.height, spec.width, device="cuda") for p in fmts}
+    st = O.OracleStream(spec.width, spec.height, oracle_params_from(W.wrls_params_default()))
+    worst = {p: 0.0 for p in fmts}
+    total = {p: 0.0 for p in fmts}
+    above = {p: 0 for p in fmts}
+    for t in range(spec.frames):
+        f = sc.frame(t, device="cuda")
+        for p in fmts:
+            streams[p].denoise(f["radiance"], f["motion"], outs[p])
+        ref, _, _ = st.frame(f["radiance"].cpu().numpy(), f["motion"].cpu().numpy())
+        for p in fmts:
+            e = per_pixel_err(outs[p].cpu().numpy(), ref)
+            worst[p] = max(worst[p], float(e.max()))
+            total[p] += float(e.sum())
+            if p != W.WRLS_STATE_F32:
+                above[p] += int((e > BOUND_16_FIREFLIES[p]["p999"]).sum())
+    for s in streams.values():
+        W.wrls_stream_check(s.handle)
+        s.close()
+    n = spec.width * spec.height * spec.frames
+    print("orbit/edit 1080p x 120: " + "; ".join(
+        "state %d max %.3g mean %.3g" % (p, worst[p], total[p] / n) for p in fmts))
+    assert worst[W.WRLS_STATE_F32] <= REL_TOL
+    for p in fmts[1:]:
+        b = BOUND_16_FIREFLIES[p]
+        assert total[p] / n <= b["mean"], p
+        assert above[p] <= 0.001 * n, p
+        assert worst[p] <= b["max"], p
+
+
 @pytest.mark.parametrize("motion,fireflies", [("static", 0.05), ("pan", 0.05), ("static", 0.0)])
 def test_long_run_against_the_oracle(motion, fireflies):
     """1200 frames at 128 x 128 with 5 % x50 fireflies (and a firefly-free static run, where the
