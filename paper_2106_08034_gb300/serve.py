@@ -7,17 +7,26 @@ budget is set) the pixel rate of the admitted sessions plus its own width x heig
 stays within the rate budget -- a fraction of the throughput the GPU sustains, so that
 frames keep their deadline instead of queueing on the device; otherwise it waits in the
 queue until a departure frees room. Admitted sessions keep their state resident on the
-device across frames. A tick takes every session whose next frame is due and denoises all of
-them with one ``wrls_batch_tick``: one CUDA graph launch that holds each session's own
-update and blend kernels on four parallel branches, so that one session's blend runs beside
-another's update. Up to ``depth`` ticks are in flight. A tick starts at once when the GPU has
-nothing in flight; while a tick runs, due frames are coalesced and the next tick starts when
-the oldest of them has waited ``coalesce_s`` (or when no tick is in flight any more), so that
-busy periods run few, large ticks; sessions that arrive while others are on the GPU join the
-next tick and their work overlaps on the device. A frame's latency is the time from its
-release (its due time) to the completion of the tick that denoised it, observed on the host
-by polling the tick's CUDA event. If a session falls more than one frame behind, the older due
-frames are dropped.
+device across frames. A departed session's stream (state and output buffer) is reset and kept
+in a per-resolution pool for the next session of that resolution, so that admission and
+departure make no device allocation or free in the loop (a free waits for the device); pooled
+memory counts against the budget and pooled streams are closed when an admission needs the
+room. A reset stream restarts every pixel on its next frame, as a new one does, so a
+session's output does not depend on whether its stream was pooled.
+
+A tick takes every session whose next frame is due and denoises all of them with one
+``wrls_batch_tick``: one CUDA graph launch that holds each session's own update and blend
+kernels on four parallel branches, so that one session's blend runs beside another's update.
+Up to ``depth`` ticks are in flight; a tick starts as soon as fewer are, so frames that fall
+due while the GPU is busy gather into the next tick and ticks grow with the load (continuous
+batching). With ``coalesce_s`` > 0 a tick that would start while another is in flight waits
+until the oldest due frame has waited that long; measured, that only adds latency (larger
+ticks ran no faster per pixel), so it is off by default. Sessions that arrive while others
+are on the GPU join the next tick and their work overlaps on the device.
+
+A frame's latency is the time from its release (its due time) to the completion of the tick
+that denoised it, observed on the host by polling the tick's CUDA event. If a session falls
+more than one frame behind, the older due frames are dropped.
 
 Inputs come from per-resolution rings of pre-generated frames on the device, read-only and
 shared by sessions of one resolution; session k's n-th processed frame is ring[n % len].
@@ -69,7 +78,7 @@ class Server:
                  params: Optional[W.wrls_params] = None, depth: int = 2, deadline_s: float = 1 / 60,
                  rings: Optional[Dict[Tuple[int, int], Tuple[torch.Tensor, torch.Tensor]]] = None,
                  cuda_stream: Optional[torch.cuda.Stream] = None, rate_budget_px_s: Optional[float] = None,
-                 device="cuda", coalesce_s: float = 0.0):
+                 device="cuda", coalesce_s: float = 0.0, pool_per_resolution: int = 4):
         self.budget = int(hbm_budget_bytes)
         self.rate_budget = None if rate_budget_px_s is None else float(rate_budget_px_s)
         self.rate = 0.0              # pixel rate (px/s) of the admitted sessions
@@ -85,7 +94,11 @@ class Server:
         W.wrls_batch_set_cuda_stream(self.batch, self.cs)
         self.active: Dict[int, Session] = {}
         self.queue: List[Session] = []
-        self.used = 0
+        self.used = 0                # bytes of the active sessions
+        self.pool: Dict[Tuple[int, int], List[Tuple[W.Stream, torch.Tensor]]] = {}
+        self.pooled = 0              # bytes of the pooled streams
+        self.pool_max = int(pool_per_resolution)
+        self.reused = 0              # admissions served from the pool
         self.ticks: List[Tick] = []
         self.latencies: List[float] = []
         self.missed = 0
@@ -114,8 +127,15 @@ class Server:
             rate_ok = self.rate_budget is None or self.rate + rate <= self.rate_budget
             if len(self.active) < self.max_sessions and self.used + need <= self.budget and rate_ok:
                 s.bytes = need
-                s.stream = W.Stream(s.width, s.height, self.params, cuda_stream=self.cs)
-                s.out = torch.empty(3, s.height, s.width, device=self.device)
+                pooled = self.pool.get((s.width, s.height))
+                if pooled:
+                    s.stream, s.out = pooled.pop()
+                    self.pooled -= need
+                    self.reused += 1
+                else:
+                    self._evict(self.budget - self.used - need)
+                    s.stream = W.Stream(s.width, s.height, self.params, cuda_stream=self.cs)
+                    s.out = torch.empty(3, s.height, s.width, device=self.device)
                 s.next_due = max(now, s.arrive)
                 self.active[s.sid] = s
                 self.used += need
@@ -141,9 +161,23 @@ class Server:
         del self.active[sid]
         self.used -= s.bytes
         self.rate -= s.width * s.height * s.fps
-        s.stream.close()
-        s.stream = None
+        pooled = self.pool.setdefault((s.width, s.height), [])
+        if len(pooled) < self.pool_max:
+            s.stream.reset()          # the next session starts from a restart of every pixel
+            pooled.append((s.stream, s.out))
+            self.pooled += s.bytes
+        else:
+            s.stream.close()
+        s.stream, s.out = None, None
         self._admit(now)
+
+    def _evict(self, room: int) -> None:
+        """Close pooled streams, largest first, until they hold at most `room` bytes."""
+        while self.pooled > max(room, 0):
+            key = max((k for k, v in self.pool.items() if v), key=lambda k: k[0] * k[1])
+            stream, _ = self.pool[key].pop()
+            stream.close()
+            self.pooled -= self.session_bytes(*key)
 
     # --- batching ---------------------------------------------------------------------
     def due_frames(self, now: float) -> List[Session]:
@@ -221,6 +255,7 @@ class Server:
         for s in list(self.active.values()):
             s.stream.close()
         self.active.clear()
+        self._evict(0)
         W.wrls_batch_destroy(self.batch)
         self.batch = 0
 
@@ -276,11 +311,14 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
              resolutions=synth.SERVING_RESOLUTIONS, fps_range=(30.0, 60.0), max_sessions: int = 64,
              hbm_budget_bytes: Optional[int] = None, deadline_s: float = 1 / 60, depth: int = 2,
              seed: int = 5, warm_start: bool = True, params: Optional[W.wrls_params] = None,
-             rings=None, rate_budget_mpix_s=None, rate_fraction: float = 0.75,
-             coalesce_s: float = 0.002, capacity_px_s: Optional[float] = None) -> dict:
+             rings=None, rate_budget_mpix_s=None, rate_fraction: float = 0.9,
+             coalesce_s: float = 0.0, capacity_px_s: Optional[float] = None) -> dict:
     """Run the serving loop in real time for `duration_s`. Sessions arrive as a Poisson
     process; with warm_start the run starts from the stationary population (Poisson count
-    with mean arrival_rate * mean lifetime, residual lifetimes uniform).
+    with mean arrival_rate * mean lifetime, residual lifetimes uniform), admitted before the
+    clock starts (their streams are created then), each with its first frame due at a uniform
+    random phase within its frame period after the start (a stationary population's sessions
+    are not in phase).
     rate_budget_mpix_s: None = admission by memory and slots only; "auto" = rate_fraction x
     the throughput calibrate_throughput measures; a number = that budget in Mpix/s."""
     rng = random.Random(seed)
@@ -299,7 +337,7 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
                  rate_budget_px_s=None if rate_budget_mpix_s is None else rate_budget_mpix_s * 1e6)
     t0 = time.perf_counter()
     sid = 0
-    initial = []
+    initial, residual = [], []
     if warm_start:
         mean_pop = arrival_rate * 0.5 * (lifetime[0] + lifetime[1])
         # Poisson(mean_pop) by inversion
@@ -312,8 +350,17 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
         for _ in range(n):
             w, h = rng.choice(list(resolutions))
             life = rng.uniform(*lifetime)
-            initial.append(Session(sid, w, h, rng.uniform(*fps_range), t0, t0 + rng.uniform(0, life)))
+            initial.append(Session(sid, w, h, rng.uniform(*fps_range), t0, math.inf))
+            residual.append(rng.uniform(0, life))
             sid += 1
+    for s in initial:
+        srv.request(s, t0)
+    t0 = time.perf_counter()     # the clock starts once the warm-start population is admitted
+    phase = random.Random(seed + 7919)
+    for s, r in zip(initial, residual):
+        s.arrive, s.depart = t0, t0 + r
+        if s.stream is not None:
+            s.next_due = t0 + phase.uniform(0.0, 1.0 / s.fps)
     arrivals = []
     t = t0
     while True:
@@ -323,8 +370,6 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
         w, h = rng.choice(list(resolutions))
         arrivals.append(Session(sid, w, h, rng.uniform(*fps_range), t, t + rng.uniform(*lifetime)))
         sid += 1
-    for s in initial:
-        srv.request(s, t0)
     pending = list(arrivals)
     end = t0 + duration_s
     rounds = 0
@@ -359,7 +404,7 @@ def simulate(duration_s: float = 15.0, arrival_rate: float = 2.0, lifetime=(10.0
         "mpix_per_gpu_s": round(srv.pixels_done / max(srv.gpu_ms / 1e3, 1e-9) / 1e6, 1),
         "p50_ms": round(pct(0.50), 3) if lat else None, "p99_ms": round(pct(0.99), 3) if lat else None,
         "deadline_ms": round(deadline_s * 1e3, 2),
-        "missed_or_dropped": srv.missed, "admitted": srv.admitted_total,
+        "missed_or_dropped": srv.missed, "admitted": srv.admitted_total, "reused_streams": srv.reused,
         "max_concurrent": srv.max_concurrent, "queued_at_end": len(srv.queue),
         "hbm_budget_gb": round(hbm_budget_bytes / 1e9, 2), "hbm_used_gb_at_end": round(srv.used / 1e9, 3),
         "rate_budget_mpix_s": None if srv.rate_budget is None else round(srv.rate_budget / 1e6, 1),

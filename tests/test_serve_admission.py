@@ -11,9 +11,13 @@ from paper_2106_08034_gb300 import wrls as W
 class _FakeStream:
     def __init__(self, w, h, params=None, cuda_stream=None):
         self.closed = False
+        self.resets = 0
 
     def close(self):
         self.closed = True
+
+    def reset(self):
+        self.resets += 1
 
 
 @pytest.fixture
@@ -82,3 +86,29 @@ def test_tick_coalescing_rule(fake_gpu):
     srv2 = _server(max_sessions=8, depth=2, coalesce_s=0.0)        # no coalescing window
     srv2.ticks.append(serve.Tick(event=None, releases=[], pixels=0))
     assert srv2.should_launch([a], 1.0)
+
+
+def test_departed_streams_are_pooled_and_reused(fake_gpu):
+    """A departed session's stream is reset and kept for the next session of its resolution
+    (no allocation or free in the loop); pooled memory counts against the budget and pooled
+    streams are closed when an admission needs the room; at most `pool_per_resolution` are
+    kept per resolution."""
+    p = W.wrls_params_default(state_precision=W.WRLS_STATE_BF16)
+    b1080 = W.wrls_state_bytes(1920, 1080, p) + 3 * 1920 * 1080 * 4
+    b4k = W.wrls_state_bytes(3840, 2160, p) + 3 * 3840 * 2160 * 4
+    srv = _server(hbm_budget_bytes=b4k + b1080 - 1, max_sessions=8, params=p, pool_per_resolution=1)
+    srv.request(serve.Session(0, 1920, 1080, 60.0, 0.0, 100.0), 0.0)
+    st0 = srv.active[0].stream
+    srv.depart(0, 1.0)
+    assert not st0.closed and st0.resets == 1 and srv.pooled == b1080 and srv.used == 0
+    srv.request(serve.Session(1, 1920, 1080, 30.0, 1.0, 100.0), 1.0)
+    assert srv.active[1].stream is st0 and srv.reused == 1 and srv.pooled == 0 and srv.used == b1080
+    srv.request(serve.Session(2, 1920, 1080, 30.0, 1.0, 100.0), 1.0)
+    st2 = srv.active[2].stream
+    assert st2 is not st0 and srv.used == 2 * b1080
+    srv.depart(1, 2.0)
+    srv.depart(2, 2.0)            # the pool keeps one stream per resolution: this one is closed
+    assert not st0.closed and st2.closed and srv.pooled == b1080
+    # a 4K session fits the budget only without the pooled 1080p stream: it is evicted
+    srv.request(serve.Session(3, 3840, 2160, 30.0, 3.0, 100.0), 3.0)
+    assert 3 in srv.active and st0.closed and srv.pooled == 0 and srv.used == b4k
