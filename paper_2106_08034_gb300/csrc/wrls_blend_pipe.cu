@@ -489,7 +489,17 @@ __global__ void __launch_bounds__(kTW * TH / R, 65536 / 128 / (kTW * TH / R))
     }
     ph ^= 1u;
     const int bx0 = (tile % tiles_x) * TW2, by0 = (tile / tiles_x) * TH;
-    for (int i = threadIdx.x; i < P; i += NT) {
+    if (bx0 - 4 >= 0 && bx0 - 4 + kBlendBoxW2 <= W && by0 - 2 >= 0 && by0 - 2 + G::SH <= H) {
+      // the whole window inside the image (most tiles): -rk of column pairs, no per-pixel tests
+      const float2* z0 = reinterpret_cast<const float2*>(sm + 12 * P);
+      const float2* z1 = reinterpret_cast<const float2*>(sm + 13 * P);
+      const float2* z2 = reinterpret_cast<const float2*>(sm + 14 * P);
+      float2* nrk = reinterpret_cast<float2*>(sm + 15 * P);
+      for (int j = threadIdx.x; j < P / 2; j += NT) {
+        const float2 r = blend_rk2(z0[j], z1[j], z2[j], kp.eps, kp.range_k);
+        nrk[j] = make_float2(-r.x, -r.y);
+      }
+    } else for (int i = threadIdx.x; i < P; i += NT) {
       const int gx = bx0 - 4 + i % kBlendBoxW2, gy = by0 - 2 + i / kBlendBoxW2;
       if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
         sm[15 * P + i] = -blend_rk(sm[12 * P + i], sm[13 * P + i], sm[14 * P + i], kp.eps, kp.range_k);

@@ -83,6 +83,15 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return _
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
+// blend_rk of two pixels: the same operations in the same order per component (the square
+// root and the reciprocal per component), so each component equals blend_rk bit for bit.
+__device__ __forceinline__ float2 blend_rk2(float2 z0, float2 z1, float2 z2, float eps, float range_k) {
+  const float2 q = f2fma(z2, z2, f2fma(z1, z1, f2mul(z0, z0)));
+  const float2 d = f2add(make_float2(sqrtf(q.x), sqrtf(q.y)), make_float2(eps, eps));
+  const float2 r = make_float2(1.0f / d.x, 1.0f / d.y);
+  return f2mul(f2mul(r, r), make_float2(range_k, range_k));
+}
+
 // Cross prediction of one colour channel of pixel i by neighbour k's model (Sec. 5.3):
 // p_i . beta_k,c = b0 + a1 b1 + a2 b2 + a3 b3 with p_i = [1, a1, a2, a3], accumulated in this
 // order by fused multiply-adds in every blend kernel.
