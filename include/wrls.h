@@ -201,9 +201,9 @@ wrls_status wrls_denoise_sequence_host(wrls_stream* s, const struct wrls_frame_i
 
 /* Not in the paper: CTAs per SM of the persistent blend kernels (blend configurations 4-9)
  * when they overlap an update in wrls_denoise_sequence: fewer leave the update room on every SM. 0 = as many
- * as fit; default 3 (measured at 1080p, binary32 state, configuration 9: 123.3 us per frame with
- * 3, 125-126 us with 2, 235 us with 1; 16-bit state, configuration 8, whose CTAs are twice as
- * large: the same with 2 and 3). */
+ * as fit; default 3 (measured at 1080p, binary32 state, configuration 9: 120.7 us per frame with
+ * 3, 123.6 us with 2, about 235 us with 1; 16-bit state, configuration 8, whose CTAs are twice
+ * as large: the same with 2 and 3). */
 wrls_status wrls_stream_set_overlap(wrls_stream* s, int blend_ctas_per_sm);
 
 /* The next frame restarts every pixel (frame-0 behaviour: beta and P at their initial
