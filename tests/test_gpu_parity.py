@@ -23,11 +23,13 @@ def _built():
     W.lib()
 
 
-def run_pair(frames, width, height, params=None, hooks=None, check_z=True, tol=REL_TOL):
+def run_pair(frames, width, height, params=None, hooks=None, check_z=True, tol=REL_TOL, blend_config=None):
     """Denoise the frames with the GPU and with the oracle; assert parity every frame.
     Returns the per-frame max relative errors."""
     p = params if params is not None else W.wrls_params_default()
     s = W.Stream(width, height, p)
+    if blend_config is not None:
+        W.wrls_stream_set_blend_config(s.handle, blend_config)
     st = O.OracleStream(width, height, oracle_params_from(p))
     out = torch.empty(3, height, width, device="cuda")
     zbuf = torch.empty(W.N_STATE, height, width, device="cuda")
