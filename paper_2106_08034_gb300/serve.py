@@ -173,7 +173,7 @@ class Server:
 
     def _evict(self, room: int) -> None:
         """Close pooled streams, largest first, until they hold at most `room` bytes."""
-        while self.pooled > max(room, 0):
+        while self.pooled > max(room, 0) and any(self.pool.values()):
             key = max((k for k, v in self.pool.items() if v), key=lambda k: k[0] * k[1])
             stream, _ = self.pool[key].pop()
             stream.close()
