@@ -455,6 +455,19 @@ __device__ __forceinline__ void bilerp_bottom(float w01, float w11, float q01, f
   if (kNState % 2) st[kNState - 1] = fmaf(w11, d[kNState - 1], fmaf(w01, c[kNState - 1], st[kNState - 1]));
 }
 
+// One tap alone (the others have weight 0): st = w00 a.
+__device__ __forceinline__ void bilerp_top1(float w00, float q00, const float a[kNState], float st[kNState]) {
+#pragma unroll
+  for (int p = 0; p + 1 < kNState; p += 2) {
+    const bool isP = p >= kP && p < kZ;
+    const float2 wa = isP ? make_float2(q00, q00) : make_float2(w00, w00);
+    const float2 v = f2mul(wa, make_float2(a[p], a[p + 1]));
+    st[p] = v.x;
+    st[p + 1] = v.y;
+  }
+  if (kNState % 2) st[kNState - 1] = w00 * a[kNState - 1];
+}
+
 // P-slot weight of a tap: w times the tap's scale (binary32: the weight itself).
 template <class SV>
 __device__ __forceinline__ float scaled_weight(float w, float s) {
@@ -481,8 +494,11 @@ __device__ __forceinline__ void gather_bilinear(const SV& prev, int W, int H, fl
   bilerp_bottom(w01, w11, scaled_weight<SV>(w01, sa), scaled_weight<SV>(w11, sb), a, b, st);
 }
 
-// Bilinear fetch from the staged window whose origin is (X0, Y0).
-template <class SV>
+// Bilinear fetch from the staged window whose origin is (X0, Y0). TAPS = 4, or 2 (the lower
+// row's weights are 0: fy = 0) or 1 (fx = fy = 0): taps of weight exactly 0 are not read. A
+// tap of weight 0 adds fma(0, v, s) = s for a finite v, so the result is that of the four-tap
+// sum (up to the sign of a zero).
+template <class SV, int TAPS = 4>
 __device__ __forceinline__ void gather_bilinear_staged(const unsigned char* stage, int X0, int Y0, int W,
                                                        int H, float qx, float qy, float st[kNState]) {
   const int x0 = (int)floorf(qx), y0 = (int)floorf(qy);
@@ -493,8 +509,13 @@ __device__ __forceinline__ void gather_bilinear_staged(const unsigned char* stag
   const int r0 = (y0 - Y0) * kStageW, r1 = (y1 - Y0) * kStageW;
   float a[kNState], b[kNState], sa, sb;
   SV::load_staged(stage, r0 + x0 - X0, a, sa);
+  if constexpr (TAPS == 1) {
+    bilerp_top1(w00, scaled_weight<SV>(w00, sa), a, st);
+    return;
+  }
   SV::load_staged(stage, r0 + x1 - X0, b, sb);
   bilerp_top(w00, w10, scaled_weight<SV>(w00, sa), scaled_weight<SV>(w10, sb), a, b, st);
+  if constexpr (TAPS == 2) return;
   SV::load_staged(stage, r1 + x0 - X0, a, sa);
   SV::load_staged(stage, r1 + x1 - X0, b, sb);
   bilerp_bottom(w01, w11, scaled_weight<SV>(w01, sa), scaled_weight<SV>(w11, sb), a, b, st);

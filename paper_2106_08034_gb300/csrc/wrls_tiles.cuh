@@ -71,6 +71,11 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint64_t* bar, u
     lo_x = x0; hi_x = min(x0 + 1, W - 1);
     lo_y = y0; hi_y = min(y0 + 1, H - 1);
   }
+  // taps of weight exactly 0, decided per warp (one tile row) so that each branch stays
+  // straight-line code: a warp whose valid pixels all have an integral motion component in y
+  // (and x), as under a static camera or an axis-aligned pan, reads 2 (1) taps instead of 4
+  const bool fy0 = __all_sync(0xffffffffu, !valid || qy == floorf(qy));
+  const bool fx0 = __all_sync(0xffffffffu, !valid || qx == floorf(qx));
   lo_x = __reduce_min_sync(0xffffffffu, lo_x);
   hi_x = __reduce_max_sync(0xffffffffu, hi_x);
   lo_y = __reduce_min_sync(0xffffffffu, lo_y);
@@ -147,7 +152,11 @@ __device__ __forceinline__ bool update_tile(UpdateSmem<SV>& sm, uint64_t* bar, u
   const bool have_box = lo[0] <= hi[0];  // some neighbour (possibly the pixel itself) was present
   float st[kNState];
   if (valid) {
-    if (fits) gather_bilinear_staged<SV>(sm.stage, X0, Y0, W, H, qx, qy, st);
+    if (fits) {
+      if (fy0 && fx0) gather_bilinear_staged<SV, 1>(sm.stage, X0, Y0, W, H, qx, qy, st);
+      else if (fy0) gather_bilinear_staged<SV, 2>(sm.stage, X0, Y0, W, H, qx, qy, st);
+      else gather_bilinear_staged<SV, 4>(sm.stage, X0, Y0, W, H, qx, qy, st);
+    }
     else gather_bilinear(prev, W, H, qx, qy, st);
   }
   update_pixel(kp, valid, st, I, missing, lo, hi, have_box);
