@@ -45,7 +45,7 @@ BYTES_PATH_16 = 136      # + out 12
 # capture is taken again. Writes still held in L2 when the kernel ends are not counted.
 KERNEL_SOURCES = {"k_update<StateF32>": ("wrls_frame.cu", "wrls_tiles.cuh", "wrls_device.cuh")}
 TRAFFIC_CAPTURES = {
-    "k_update<StateF32>": {"bytes": 248871680 + 170766592, "sources_sha256_16": "da00e4aad85706e9",
+    "k_update<StateF32>": {"bytes": 248893696 + 169094656, "sources_sha256_16": "3d05baa4e1b3fd16",
                            "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
                                       "-k regex:k_update -s 8 -c 2, bench.py --frames 8 --steps 1 --state f32"},
 }

@@ -28,8 +28,9 @@ A frame's latency is the time from its release (its due time) to the completion 
 that denoised it, observed on the host by polling the tick's CUDA event. If a session falls
 more than one frame behind, the older due frames are dropped.
 
-Inputs come from per-resolution rings of pre-generated frames on the device, read-only and
-shared by sessions of one resolution; session k's n-th processed frame is ring[n % len].
+Inputs come from per-resolution rings of pre-generated frames on the device (frames 1..K of a
+seeded orbit sequence, all with camera motion), read-only and shared by sessions of one
+resolution; session k's n-th processed frame is ring[n % len].
 """
 from __future__ import annotations
 
@@ -264,11 +265,11 @@ def make_rings(resolutions: Sequence[Tuple[int, int]], frames: int = 4, seed: in
                device="cuda") -> Dict[Tuple[int, int], Tuple[torch.Tensor, torch.Tensor]]:
     rings = {}
     for i, (w, h) in enumerate(resolutions):
-        sc = synth.Scene(synth.SceneSpec(w, h, frames, seed=seed + i, motion="orbit", firefly_frac=0.05))
+        sc = synth.Scene(synth.SceneSpec(w, h, frames + 1, seed=seed + i, motion="orbit", firefly_frac=0.05))
         rad = torch.empty(frames, 3, h, w, device=device)
         mot = torch.empty(frames, 2, h, w, device=device)
-        for t in range(frames):
-            f = sc.frame(t, device=device)
+        for t in range(frames):   # frames 1..K: frame 0 of a sequence has no motion
+            f = sc.frame(t + 1, device=device)
             rad[t].copy_(f["radiance"])
             mot[t].copy_(f["motion"])
         rings[(w, h)] = (rad, mot)
