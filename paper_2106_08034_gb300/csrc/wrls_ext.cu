@@ -49,14 +49,23 @@ __global__ void __launch_bounds__(kExtTW * kExtTH)
   using L = ExtDim<D, F>;
   const KParams& kp = ep.kp;
   const int x = blockIdx.x * kExtTW + threadIdx.x, y = blockIdx.y * kExtTH + threadIdx.y;
-  if (x >= W || y >= H) return;
+  const bool inside = x < W && y < H;
   const size_t npix = (size_t)W * H, j = (size_t)y * W + x;
-  const float I[3] = {__ldg(rad + j), __ldg(rad + npix + j), __ldg(rad + 2 * npix + j)};
-  const bool missing = !finite3(I);
 
   // reprojection q = j + v_j (Table 2), binary32; NaN motion fails every comparison
-  const float qx = (float)x + __ldg(mot + j), qy = (float)y + __ldg(mot + npix + j);
-  const bool valid = !reset && qx >= 0.0f && qx <= (float)(W - 1) && qy >= 0.0f && qy <= (float)(H - 1);
+  float qx = 0.0f, qy = 0.0f;
+  bool valid = false;
+  if (inside) {
+    qx = (float)x + __ldg(mot + j);
+    qy = (float)y + __ldg(mot + npix + j);
+    valid = !reset && qx >= 0.0f && qx <= (float)(W - 1) && qy >= 0.0f && qy <= (float)(H - 1);
+  }
+  // a warp (one tile row) whose valid pixels all have an integral vertical motion component
+  // reads only the upper two taps
+  const bool fy0 = __all_sync(0xffffffffu, !valid || qy == floorf(qy));
+  if (!inside) return;
+  const float I[3] = {__ldg(rad + j), __ldg(rad + npix + j), __ldg(rad + 2 * npix + j)};
+  const bool missing = !finite3(I);
 
   float st[L::kNS];
   if (valid) {
@@ -75,10 +84,18 @@ __global__ void __launch_bounds__(kExtTW * kExtTH)
       const float* s10 = prev + (size_t)y0 * pitch + x1;
       const float* s01 = prev + (size_t)y1 * pitch + x0;
       const float* s11 = prev + (size_t)y1 * pitch + x1;
+      if (fy0) {  // the lower taps have weight exactly 0 (adding 0 * v leaves the sum as it is)
 #pragma unroll
-      for (int p = 0; p < L::kNS; ++p) {
-        const size_t o = p * ps;
-        st[p] = w00 * __ldg(s00 + o) + w10 * __ldg(s10 + o) + (w01 * __ldg(s01 + o) + w11 * __ldg(s11 + o));
+        for (int p = 0; p < L::kNS; ++p) {
+          const size_t o = p * ps;
+          st[p] = w00 * __ldg(s00 + o) + w10 * __ldg(s10 + o);
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < L::kNS; ++p) {
+          const size_t o = p * ps;
+          st[p] = w00 * __ldg(s00 + o) + w10 * __ldg(s10 + o) + (w01 * __ldg(s01 + o) + w11 * __ldg(s11 + o));
+        }
       }
     }
   }
