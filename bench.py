@@ -760,8 +760,8 @@ def run_wrls(args):
             step()
     cs.synchronize()
     # blend tile configuration, then the faster entry (untimed): per-frame calls, or the
-    # sequence entry (blend of frame t beside the update of frame t+1) with 1 or 2 blend CTAs
-    # per SM
+    # sequence entry (blend of frame t beside the update of frame t+1) with 2, 3 or 4 blend
+    # CTAs per SM
     if args.blend_config >= 0:
         W.wrls_stream_set_blend_config(s.handle, args.blend_config)
         blend_times, blend_cfg = [], args.blend_config
@@ -784,7 +784,7 @@ def run_wrls(args):
     pipe_ms = {}
     if not args.seq:
         pipe_ms["frame"] = time_step()
-    seq_choices = [] if args.no_seq else ([args.overlap] if args.seq else [2, 3])
+    seq_choices = [] if args.no_seq else ([args.overlap] if args.seq else [2, 3, 4])
     mode["seq"] = True
     for ov in seq_choices:
         W.wrls_stream_set_overlap(s.handle, ov)
